@@ -1,0 +1,369 @@
+"""FP64 CPU oracle of the NLINV hot path -- TEST INFRASTRUCTURE ONLY.
+
+Plain, slow, obviously-correct NumPy/SciPy complex128 restatement of the
+operators and solver of Schaetz, Voit, Frahm & Uecker, "Accelerated Computing
+in MRI -- Real-Time Imaging Using Non-Linear Inverse Reconstruction" (2017).
+Only the test-suite, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU
+baseline / reference arm may import this module; the product path never
+does, and nothing here is shared with the CUDA path.
+
+Equation numbers follow their order of appearance in the paper:
+  Eq. (1)      NLINV objective  ||F x - y||^2 + alpha ||W (x - x_prev)||^2   (Sec. 2.2)
+  Eqs. (2)-(3) IRGNM update with the change of variables x^ = W x, F^ = F o W^-1
+  Eq. (4)      normal operator DF^H DF : dx -> (sum_j c_j^* t_j, W_b^-H rho^* t_j)
+  Eq. (5)      t_j = F_b^H F_b {c_j drho + rho W_b^-1 dc^_j}
+  Eq. (10)     temporal decomposition h(n, m)                            (Sec. 3.3)
+  Fig. 4       flowchart of the normal operator (W^-1 = iFFT after D_W^-1,
+               W^-H = D_W^-1 after FFT; PSF convolution via pad/FFT/P/iFFT/crop)
+  Fig. 7       Sobolev weight (1 + 880 |k|^2)^16, -0.5 < k < 0.5
+  Sec. 3.2     coil coefficients cropped to G_c = floor(G/4), zero-padded when needed
+
+Conventions (readings of the paper where it is silent; each is listed with
+its reason in the design notes):
+  * grid G = 2N (gamma = 1 in Eq. (8)); image rho on N x N, the FOV sits at
+    rows/cols [0, N) of the G grid (pad writes top-left, crop reads top-left);
+  * unitary 2-D DFT U (norm="ortho"), unshifted frequency order;
+  * D^-1(f) = (1 + a |2f/G|^2)^(-l/2) with a = 220, l = 32 -- identical to the
+    figure's 880 |k|^2 with k = f/G -- applied on the coil grid;
+  * coil coefficients c^_j live on a G_c x G_c grid in unshifted order,
+    frequency f at index f mod G_c (G_c = G means no crop);
+  * x^ = (rho, c^_1..c^_J); inner product Re sum conj(u) v over all parts;
+  * alpha_n = alpha_0 q^n; regulariser x_ref = damping * x_prev;
+  * sampling enters only as the real PSF multiplier P on the G grid
+    (P = mask for Cartesian sampling).
+"""
+from __future__ import annotations
+
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import scipy.fft as sfft
+
+_WORKERS = int(os.environ.get("NLINV_ORACLE_THREADS", os.cpu_count() or 1))
+
+
+def set_workers(n: int) -> None:
+    """Thread count for the oracle's library FFTs."""
+    global _WORKERS
+    _WORKERS = max(1, int(n))
+
+
+def workers() -> int:
+    return _WORKERS
+
+
+# ---------------------------------------------------------------------------
+# geometry
+# ---------------------------------------------------------------------------
+
+@dataclass(frozen=True)
+class Geometry:
+    """Sizes of one reconstruction: image side N, grid G = 2N, J channels,
+    coil grid Gc (Sec. 3.2: Gc = floor(G/4); Gc = G disables the crop), and
+    the Sobolev weight constants (Fig. 7)."""
+    N: int
+    J: int
+    Gc: int | None = None
+    w_a: float = 220.0
+    w_l: float = 32.0
+
+    @property
+    def G(self) -> int:
+        return 2 * self.N
+
+    @property
+    def gc(self) -> int:
+        return self.G // 4 if self.Gc is None else self.Gc
+
+
+def freqs(n: int) -> np.ndarray:
+    """Signed frequency of each index of an unshifted n-point DFT grid."""
+    i = np.arange(n)
+    return np.where(i < (n + 1) // 2, i, i - n)
+
+
+def sobolev_inv_weight(geom: Geometry) -> np.ndarray:
+    """Diagonal D_W^-1 on the Gc x Gc coil grid (Fig. 4, Fig. 7):
+    (1 + a ((2 fx/G)^2 + (2 fy/G)^2))^(-l/2), f the physical frequency."""
+    G, Gc = geom.G, geom.gc
+    f = freqs(Gc).astype(np.float64) * 2.0 / G
+    k2 = f[:, None] ** 2 + f[None, :] ** 2
+    return (1.0 + geom.w_a * k2) ** (-geom.w_l / 2.0)
+
+
+# ---------------------------------------------------------------------------
+# grid helpers: unitary DFT, pad / crop (Fig. 4)
+# ---------------------------------------------------------------------------
+
+def fft2u(x: np.ndarray) -> np.ndarray:
+    """Unitary 2-D DFT U over the last two axes."""
+    return sfft.fft2(x, norm="ortho", workers=_WORKERS)
+
+
+def ifft2u(x: np.ndarray) -> np.ndarray:
+    """U^H = U^-1 over the last two axes."""
+    return sfft.ifft2(x, norm="ortho", workers=_WORKERS)
+
+
+def pad_img(x: np.ndarray, G: int) -> np.ndarray:
+    """Zero-pad an N x N image into the top-left of the G x G grid."""
+    N = x.shape[-1]
+    out = np.zeros(x.shape[:-2] + (G, G), np.complex128)
+    out[..., :N, :N] = x
+    return out
+
+
+def crop_img(z: np.ndarray, N: int) -> np.ndarray:
+    """Top-left N x N of a G x G grid (the FOV)."""
+    return z[..., :N, :N]
+
+
+def pad_coef(c: np.ndarray, G: int) -> np.ndarray:
+    """Place a Gc x Gc unshifted coefficient grid into the G x G grid:
+    frequency f goes to index f mod G, everything else is zero (Sec. 3.2)."""
+    Gc = c.shape[-1]
+    idx = freqs(Gc) % G
+    out = np.zeros(c.shape[:-2] + (G, G), np.complex128)
+    out[..., idx[:, None], idx[None, :]] = c
+    return out
+
+
+def crop_coef(z: np.ndarray, Gc: int) -> np.ndarray:
+    """Keep frequencies of the Gc x Gc coil grid out of a G x G grid."""
+    G = z.shape[-1]
+    idx = freqs(Gc) % G
+    return z[..., idx[:, None], idx[None, :]]
+
+
+# ---------------------------------------------------------------------------
+# the unknown x^ = (rho, c^) and its inner product
+# ---------------------------------------------------------------------------
+
+@dataclass
+class XVec:
+    """x^ = (rho [N,N], chat [J,Gc,Gc]) (Sec. 2.2)."""
+    rho: np.ndarray
+    chat: np.ndarray
+
+    def __add__(self, o):
+        return XVec(self.rho + o.rho, self.chat + o.chat)
+
+    def __sub__(self, o):
+        return XVec(self.rho - o.rho, self.chat - o.chat)
+
+    def scale(self, a):
+        return XVec(a * self.rho, a * self.chat)
+
+    def copy(self):
+        return XVec(self.rho.copy(), self.chat.copy())
+
+    def flat(self) -> np.ndarray:
+        return np.concatenate([self.rho.reshape(-1), self.chat.reshape(-1)])
+
+    @staticmethod
+    def unflat(v: np.ndarray, geom: Geometry) -> "XVec":
+        N, J, Gc = geom.N, geom.J, geom.gc
+        return XVec(v[:N * N].reshape(N, N).copy(),
+                    v[N * N:].reshape(J, Gc, Gc).copy())
+
+    @staticmethod
+    def zeros(geom: Geometry) -> "XVec":
+        return XVec(np.zeros((geom.N, geom.N), np.complex128),
+                    np.zeros((geom.J, geom.gc, geom.gc), np.complex128))
+
+    @staticmethod
+    def initial(geom: Geometry) -> "XVec":
+        """First frame: rho set to unity and coils to zero (Sec. 3.3)."""
+        x = XVec.zeros(geom)
+        x.rho[:] = 1.0
+        return x
+
+
+def dot(u: XVec, v: XVec) -> float:
+    """Real inner product Re <u, v> = Re sum conj(u) v over rho and c^."""
+    return float(np.real(np.vdot(u.rho, v.rho) + np.vdot(u.chat, v.chat)))
+
+
+# ---------------------------------------------------------------------------
+# operators (Sec. 2.2, Eqs. (2)-(5), Fig. 4)
+# ---------------------------------------------------------------------------
+
+def W_inv(chat: np.ndarray, geom: Geometry) -> np.ndarray:
+    """W^-1 on the coil part: D_W^-1, zero-pad to G, inverse FFT, restrict
+    to the FOV.  [J,Gc,Gc] -> [J,N,N]."""
+    z = pad_coef(sobolev_inv_weight(geom) * chat, geom.G)
+    return crop_img(ifft2u(z), geom.N)
+
+
+def W_invH(v: np.ndarray, geom: Geometry) -> np.ndarray:
+    """W^-H, the adjoint of W_inv: pad the FOV image, FFT, keep the coil
+    grid, D_W^-1.  [J,N,N] -> [J,Gc,Gc]."""
+    z = fft2u(pad_img(v, geom.G))
+    return sobolev_inv_weight(geom) * crop_coef(z, geom.gc)
+
+
+def coils(x: XVec, geom: Geometry) -> np.ndarray:
+    """Coil sensitivities c_j = W^-1 c^_j of a point x^."""
+    return W_inv(x.chat, geom)
+
+
+def F_hat(x: XVec, geom: Geometry) -> np.ndarray:
+    """F^(x^)_j = U pad(rho c_j): predicted (unsampled) k-space on the G grid."""
+    return fft2u(pad_img(x.rho[None] * coils(x, geom), geom.G))
+
+
+def DF(x: XVec, dx: XVec, geom: Geometry) -> np.ndarray:
+    """Derivative of F^ at x^ applied to dx: U pad(c_j drho + rho W^-1 dc^_j)."""
+    c = coils(x, geom)
+    dc = W_inv(dx.chat, geom)
+    return fft2u(pad_img(c * dx.rho[None] + x.rho[None] * dc, geom.G))
+
+
+def DFH(x: XVec, z: np.ndarray, geom: Geometry) -> XVec:
+    """Adjoint of DF at x^ (Eq. (4) without the PSF): with t_j = crop U^H z_j,
+    returns (sum_j conj(c_j) t_j, W^-H (conj(rho) t_j))."""
+    c = coils(x, geom)
+    t = crop_img(ifft2u(z), geom.N)
+    return XVec(np.sum(np.conj(c) * t, axis=0),
+                W_invH(np.conj(x.rho)[None] * t, geom))
+
+
+def normal(x: XVec, dx: XVec, P: np.ndarray, alpha: float, geom: Geometry) -> XVec:
+    """(DF^H P DF + alpha I) dx: the operator of Eq. (4)/(5) with the
+    non-uniform transform pair replaced by the PSF multiplier P on the
+    twofold-oversampled grid (Sec. 2.2 footnote), plus the Tikhonov term."""
+    return DFH(x, P[None] * DF(x, dx, geom), geom) + dx.scale(alpha)
+
+
+# ---------------------------------------------------------------------------
+# conjugate gradients (Sec. 2.2: CG on each Newton step's linear system)
+# ---------------------------------------------------------------------------
+
+class CGBreakdown(RuntimeError):
+    pass
+
+
+def cg(apply, b: XVec, iters: int, trace: list | None = None) -> XVec:
+    """Fixed-count conjugate gradients from zero: a = |r|^2 / Re<p,Ap>,
+    beta = |r_new|^2 / |r|^2.  Stops early only when |r|^2 is exactly 0;
+    raises CGBreakdown when Re<p,Ap> <= 0 or is not finite."""
+    x = XVec(np.zeros_like(b.rho), np.zeros_like(b.chat))
+    r = b.copy()
+    p = r.copy()
+    rr = dot(r, r)
+    for _ in range(iters):
+        if rr == 0.0:
+            break
+        q = apply(p)
+        pq = dot(p, q)
+        if not (np.isfinite(pq) and pq > 0.0):
+            raise CGBreakdown(f"Re<p,Ap> = {pq}")
+        a = rr / pq
+        x = x + p.scale(a)
+        r = r - q.scale(a)
+        rr_new = dot(r, r)
+        if trace is not None:
+            trace.append(dict(rr=rr, pq=pq, a=a, rr_new=rr_new))
+        p = r + p.scale(rr_new / rr)
+        rr = rr_new
+    return x
+
+
+# ---------------------------------------------------------------------------
+# IRGNM frame (Eqs. (2)-(3)) and streams
+# ---------------------------------------------------------------------------
+
+@dataclass(frozen=True)
+class Params:
+    newton_steps: int = 7
+    cg_iters: int = 10
+    alpha0: float = 1.0
+    q: float = 0.5
+    damping: float = 1.0
+
+
+def newton_rhs(x: XVec, x_ref: XVec, Y: np.ndarray, P: np.ndarray, alpha: float,
+               geom: Geometry) -> XVec:
+    """Right-hand side of the IRGNM update (Eqs. (2)-(3)):
+    DF^H (Y - P F^(x^_n)) - alpha_n (x^_n - x^_ref)."""
+    resid = Y - P[None] * F_hat(x, geom)
+    return DFH(x, resid, geom) - (x - x_ref).scale(alpha)
+
+
+def nlinv_frame(Y: np.ndarray, P: np.ndarray, x_init: XVec, x_ref: XVec,
+                geom: Geometry, prm: Params = Params(), trace: list | None = None) -> XVec:
+    """One frame of NLINV: M Newton steps from x^_0 = x_init, each solving
+    (DF^H P DF + alpha_n I) delta = rhs by CG and setting x^_{n+1} = x^_n + delta."""
+    x = x_init.copy()
+    for n in range(prm.newton_steps):
+        alpha = prm.alpha0 * prm.q ** n
+        b = newton_rhs(x, x_ref, Y, P, alpha, geom)
+        delta = cg(lambda d: normal(x, d, P, alpha, geom), b, prm.cg_iters,
+                   trace=None if trace is None else trace)
+        x = x + delta
+    return x
+
+
+def image(x: XVec, geom: Geometry) -> np.ndarray:
+    """Coil-combined image rho * sqrt(sum_j |c_j|^2)."""
+    c = coils(x, geom)
+    return x.rho * np.sqrt(np.sum(np.abs(c) ** 2, axis=0))
+
+
+def source_frame(n: int, delay: int, warmup: int) -> int:
+    """Frame whose x^ initialises and regularises frame n under the batched
+    relaxation of the temporal decomposition (Sec. 3.3, Eq. (10) with a fixed
+    offset): in order (n-1) for n <= warmup, n - delay afterwards.  -1 means
+    the initial value (rho = 1, c = 0)."""
+    if n <= warmup:
+        return n - 1
+    return max(n - delay, -1)
+
+
+def nlinv_stream(frames, geom: Geometry, prm: Params = Params(),
+                 delay: int = 1, warmup: int = 0):
+    """Reconstruct a stream of (Y, P) frames in order; frame n starts from
+    and is regularised towards damping * x^ of source_frame(n)."""
+    xs = []
+    init = XVec.initial(geom)
+    for n, (Y, P) in enumerate(frames):
+        s = source_frame(n, delay, warmup)
+        xp = init if s < 0 else xs[s]
+        xs.append(nlinv_frame(Y, P, xp, xp.scale(prm.damping), geom, prm))
+    return xs
+
+
+# ---------------------------------------------------------------------------
+# non-uniform sampling: exact NDFT, PSF and gridded data (Sec. 2.2 footnote)
+# ---------------------------------------------------------------------------
+
+def ndft_adjoint(kx: np.ndarray, ky: np.ndarray, y: np.ndarray, N: int, G: int) -> np.ndarray:
+    """A^H y: (A^H y)(r) = G^-1 sum_s y_s exp(+2 pi i k_s . r) on the N x N FOV,
+    y [..., S] -> [..., N, N]."""
+    r = np.arange(N, dtype=np.float64)
+    ex = np.exp(2j * np.pi * np.outer(kx, r))        # [S, x]
+    ey = np.exp(2j * np.pi * np.outer(ky, r))        # [S, y]
+    return np.einsum("...s,sy,sx->...yx", y, ey, ex, optimize=True) / G
+
+
+def psf_kernel(kx: np.ndarray, ky: np.ndarray, N: int, G: int) -> np.ndarray:
+    """PSF P on the G grid for the Toeplitz form of A^H A:
+    p(d) = G^-2 sum_s exp(2 pi i k_s . d) for d in [-(N-1), N-1]^2, embedded
+    circularly on the G grid (p = 0 at offset +-N), P = G U p.  Real because
+    p is Hermitian; returned as float64 [G, G]."""
+    d = np.arange(-(N - 1), N, dtype=np.float64)
+    ex = np.exp(2j * np.pi * np.outer(kx, d))        # [S, dx]
+    ey = np.exp(2j * np.pi * np.outer(ky, d))        # [S, dy]
+    p = (ey.T @ ex) / (G * G)                          # [dy, dx]
+    emb = np.zeros((G, G), np.complex128)
+    idx = d.astype(int) % G
+    emb[idx[:, None], idx[None, :]] = p
+    P = G * fft2u(emb)
+    return P
+
+
+def grid_data(kx: np.ndarray, ky: np.ndarray, y: np.ndarray, N: int, G: int) -> np.ndarray:
+    """Gridded data on the G grid with crop U^H Y_j = A^H y_j exactly:
+    Y_j = U pad(A^H y_j)."""
+    return fft2u(pad_img(ndft_adjoint(kx, ky, y, N, G), G))
