@@ -1,0 +1,159 @@
+/*
+ * nlinv.h -- C ABI of the GB300 (sm_103a) NLINV hot path.
+ *
+ * NLINV (Schaetz, Voit, Frahm, Uecker 2017, Sec. 2.2) reconstructs an image
+ * rho and J coil sensitivities c_j from multi-channel k-space by minimising
+ *     || F x - y ||^2 + alpha || W (x - x_prev) ||^2                  (Eq. 1)
+ * with the iteratively regularised Gauss-Newton method (IRGNM, Eqs. 2-3)
+ * after the change of variables x^ = W x, F^ = F o W^-1, each Newton step
+ * solved by conjugate gradients on (DF^H DF + alpha_n I) (Eqs. 4-5).  The
+ * non-uniform transform pair is a truncated convolution with the
+ * point-spread function (PSF) on the twofold-oversampled grid (Sec. 2.2
+ * footnote, Fig. 4); W is a Fourier-domain Sobolev weight on the coils only
+ * (Fig. 4, Fig. 7); coil coefficients are stored on a G_c = floor(G/4) grid
+ * (Sec. 3.2).
+ *
+ * Conventions (all entry points):
+ *   - complex data are complex64, interleaved (re, im) float pairs, row-major;
+ *   - N = image side, G = 2N grid side, J channels, Gc coil grid side (even);
+ *   - unitary 2-D DFT U, unshifted frequency order; the field of view is
+ *     rows/cols [0, N) of the G grid;
+ *   - the unknown x^ is ONE contiguous vector of n_x = N*N + J*Gc*Gc complex
+ *     values: rho [N][N] followed by c^ [J][Gc][Gc], the c^ grid holding
+ *     frequency f at index f mod Gc;
+ *   - D_W^-1(f) = (1 + w_a |2f/G|^2)^(-w_l/2) (Fig. 7's (1+880|k|^2)^16 with
+ *     k = f/G for w_a = 220, w_l = 32);
+ *   - the PSF P [U][G][G] is real, unshifted; sampling enters only through
+ *     P (P = 0/1 mask for Cartesian sampling);
+ *   - data Y [J][G][G] are gridded so that crop_N U^H Y_j = A^H y_j.
+ *
+ * Memory and streams: every pointer argument marked "device" is
+ * caller-owned device memory (8-byte aligned for complex data) that must
+ * stay valid until the stream has passed the call.  The plan owns its
+ * workspace, its PSFs and its weight tables.  All compute calls are
+ * asynchronous on `stream` (a cudaStream_t; NULL = legacy default stream).
+ *
+ * Errors: every call returns NLINV_OK (0) or a negative code.  Host-side
+ * validation failures return before anything is enqueued.  Errors detected
+ * on the device (an expired bounded wait, a CG breakdown) are latched in the
+ * plan and returned by nlinv_sync().  No C++ exception crosses this ABI.
+ */
+#ifndef NLINV_H
+#define NLINV_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NLINV_OK 0
+#define NLINV_EINVAL (-1)      /* bad size, null/unaligned pointer, bad turn */
+#define NLINV_ECUDA (-2)       /* a CUDA runtime call failed */
+#define NLINV_ENOMEM (-3)      /* device allocation failed */
+#define NLINV_ETIMEOUT (-4)    /* a bounded device-side wait expired */
+#define NLINV_ENUMERIC (-5)    /* CG breakdown: Re<p, A p> <= 0 or not finite */
+#define NLINV_EUNSUPPORTED (-6)/* grid size without a compiled FFT schedule */
+
+typedef struct nlinv_plan_s* nlinv_plan_t;
+typedef void* nlinv_stream_t; /* cudaStream_t */
+
+typedef struct {
+  int N;              /* image side; grid G = 2N (gamma = 1 in Eq. 8) */
+  int J;              /* receive channels */
+  int Gc;             /* coil grid side, even, <= G; 0 -> floor(G/4) (Sec. 3.2) */
+  int newton_steps;   /* M, 1..32 (Sec. 2.2: 6 to 10) */
+  int cg_iters;       /* fixed CG iterations per Newton step, 0..4096 */
+  int n_turns;        /* U: PSFs held by the plan (Sec. 2.1, Fig. 3) */
+  double alpha0, q;   /* alpha_n = alpha0 * q^n, alpha0 > 0, 0 < q <= 1 */
+  double damping;     /* x_ref = damping * x_prev (1.0 = Eq. 1 literally) */
+  double w_a, w_l;    /* Sobolev weight constants (220, 32) */
+  long long spin_limit; /* polls before a device-side wait gives up; 0 -> default */
+  int exec_mode;      /* 0: one persistent cooperative launch per frame;
+                         1: one launch per phase (unfused comparator) */
+} nlinv_params_t;
+
+/* Fill `p` with the defaults for an N x N image and J channels:
+ * Gc = G/4, 7 Newton steps x 10 CG, alpha0 = 1, q = 1/2, damping 1,
+ * w_a = 220, w_l = 32, one turn, persistent execution. */
+int nlinv_default_params(nlinv_params_t* p, int N, int J);
+
+/* Create a plan (Sec. 2.2, Fig. 4 set-up: twiddles, D_W^-1 table, PSFs,
+ * workspace).  psf: device float [U][G][G] copied into the plan, or NULL
+ * (PSFs then start at zero; set them with nlinv_set_psf / nlinv_psf).
+ * Allocates device memory; synchronises `stream` before returning. */
+int nlinv_plan(nlinv_plan_t* out, const nlinv_params_t* p, const float* psf,
+               nlinv_stream_t stream);
+int nlinv_plan_destroy(nlinv_plan_t plan);
+
+/* n_x, G and Gc of a plan (host values). */
+int nlinv_plan_sizes(nlinv_plan_t plan, long long* nx, int* G, int* Gc);
+
+/* Copy one turn's PSF (device float [G][G]) into the plan. */
+int nlinv_set_psf(nlinv_plan_t plan, int turn, const float* psf, nlinv_stream_t stream);
+
+/* PSF of a trajectory (Sec. 2.2 footnote): P(f) = sum_d p(d) e^{-2 pi i f.d/G},
+ * p(d) = G^-2 sum_s e^{2 pi i k_s.d} for d in [-(N-1), N-1]^2, evaluated as
+ * G^-2 sum_s Dir(kx_s - fx/G) Dir(ky_s - fy/G) with the Dirichlet kernel
+ * Dir(t) = sin((2N-1) pi t) / sin(pi t).
+ * kxy: device double [S][2] (kx, ky) in cycles/pixel.  The result goes into
+ * the plan's slot `turn` and, if P_out != NULL, to device float [G][G]. */
+int nlinv_psf(nlinv_plan_t plan, int turn, int S, const double* kxy, float* P_out,
+              nlinv_stream_t stream);
+
+/* Gridding by the exact adjoint NDFT (the preprocessing stage of Sec. 3.1
+ * in its brute-force form): Y_j = U pad(A^H y_j) with
+ * (A^H y)(r) = G^-1 sum_s y_s e^{+2 pi i k_s.r}.
+ * kxy: device double [S][2]; y: device complex64 [J][S];
+ * Y_out: device complex64 [J][G][G].  Uses the plan's workspace. */
+int nlinv_grid(nlinv_plan_t plan, int S, const double* kxy, const void* y, void* Y_out,
+               nlinv_stream_t stream);
+
+/* DF at x^_n applied to dx (Eq. 5 before the PSF):
+ *   z_j = U pad_N(c_j drho + rho W^-1 dc^_j),  c_j = W^-1 c^_j of x^_n.
+ * xhat, dx: device complex64 [n_x]; z: device complex64 [J][G][G]. */
+int nlinv_apply_DF(nlinv_plan_t plan, const void* xhat, const void* dx, void* z,
+                   nlinv_stream_t stream);
+
+/* The exact adjoint of nlinv_apply_DF (Eq. 4 without the PSF):
+ *   t_j = crop_N U^H z_j;  dx = (sum_j conj(c_j) t_j, W^-H(conj(rho) t_j)).
+ * xhat: device [n_x]; z: device [J][G][G]; dx_out: device [n_x]. */
+int nlinv_apply_DFH(nlinv_plan_t plan, const void* xhat, const void* z, void* dx_out,
+                    nlinv_stream_t stream);
+
+/* The CG operator of one Newton step (Eqs. 2, 4, 5):
+ *   out = (DF^H P_turn DF + alpha I) dx   at x^_n = xhat.
+ * xhat, dx, out: device [n_x]; out must not alias xhat or dx. */
+int nlinv_apply_normal(nlinv_plan_t plan, const void* xhat, const void* dx, int turn,
+                       double alpha, void* out, nlinv_stream_t stream);
+
+/* One NLINV frame (Eqs. 2-3): M Newton steps from x^_0 = x_prev, each
+ *   (DF^H P DF + alpha_n I) delta = DF^H (Y - P F^(x^_n)) - alpha_n (x^_n - x_ref)
+ * solved by cg_iters CG iterations from zero, x^_{n+1} = x^_n + delta,
+ * alpha_n = alpha0 q^n, x_ref = damping * x_prev.
+ * Y: device complex64 [J][G][G]; turn selects the PSF; x_prev: device [n_x]
+ * or NULL (rho = 1, c^ = 0: the first frame of Sec. 3.3); x_out: device
+ * [n_x] (may alias x_prev); rho_out: device [N][N] or NULL; img_out: device
+ * [N][N] rho * sqrt(sum_j |c_j|^2) or NULL. */
+int nlinv_frame(nlinv_plan_t plan, const void* Y, int turn, const void* x_prev,
+                void* x_out, void* rho_out, void* img_out, nlinv_stream_t stream);
+
+/* Bounded device-side wait until *flag == expected (flag: device int),
+ * polling at most spin_limit times; on expiry the plan latches
+ * NLINV_ETIMEOUT, which nlinv_sync() returns.  This is the wait primitive of
+ * the frame dependencies; it also lets a caller check the timeout path. */
+int nlinv_wait_flag(nlinv_plan_t plan, const int* flag, int expected, long long spin_limit,
+                    nlinv_stream_t stream);
+
+/* Wait for `stream`, then return and clear the plan's latched device error
+ * (NLINV_OK, NLINV_ETIMEOUT or NLINV_ENUMERIC) or NLINV_ECUDA. */
+int nlinv_sync(nlinv_plan_t plan, nlinv_stream_t stream);
+
+/* Static description of an error code. */
+const char* nlinv_strerror(int code);
+
+/* Last CUDA error string seen by the library on this thread (or ""). */
+const char* nlinv_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NLINV_H */

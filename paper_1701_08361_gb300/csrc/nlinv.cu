@@ -1,0 +1,785 @@
+// C-ABI implementation of the GB300 NLINV hot path (see include/nlinv.h).
+//
+// Kernels: the fused phases of phases.cuh, launched either one per phase or
+// all inside one persistent cooperative kernel per frame (grid barriers with
+// bounded waits between phases), plus the preprocessing kernels that turn a
+// trajectory into a PSF and raw samples into gridded data.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "nlinv.h"
+#include "phases.cuh"
+
+using namespace nlinv;
+
+namespace {
+
+// ------------------------------------------------------------ errors
+thread_local char g_cuda_err[256] = "";
+
+int cuda_fail(cudaError_t e, const char* what) {
+  std::snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", what, cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? NLINV_ENOMEM : NLINV_ECUDA;
+}
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+#define CKL(what)                                  \
+  do {                                             \
+    cudaError_t e_ = cudaGetLastError();           \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+// ---------------------------------------------------- kernel wrappers
+template <class K>
+__global__ void __launch_bounds__(K::BS) k_coil_y(Ctx C, const float2* src, int upd, int k, float2* hout) {
+  extern __shared__ float2 sm[];
+  __shared__ double sred[32];
+  phase_coil_y<K>(C, sm, src, upd != 0, k, sred, hout);
+}
+
+template <class K>
+__global__ void __launch_bounds__(K::BS) k_row_b(Ctx C, int mode, const float2* hin, const float2* rho,
+                                                 const float2* drho, const float2* img, float2* vout) {
+  extern __shared__ float2 sm[];
+  phase_row_b<K>(C, sm, mode, hin, rho, drho, img, vout);
+}
+
+template <class K>
+__global__ void __launch_bounds__(K::BS) k_col_c(Ctx C, int mode, const float* P, const float2* Yin,
+                                                 float2* zout, float2* vio) {
+  extern __shared__ float2 sm[];
+  phase_col_c<K>(C, sm, mode, P, Yin, zout, vio);
+}
+
+template <class K>
+__global__ void __launch_bounds__(K::BS) k_row_d(Ctx C, const float2* rho, const float2* win, float2* sout,
+                                                 float2* kbout) {
+  extern __shared__ float2 sm[];
+  phase_row_d<K>(C, sm, rho, win, sout, kbout);
+}
+
+template <class K>
+__global__ void __launch_bounds__(K::BS) k_col_e(Ctx C, int mode, float alpha, const float2* kbin,
+                                                 const float2* sin, const float2* pv, float2* out, int slot) {
+  extern __shared__ float2 sm[];
+  __shared__ double sred[32];
+  phase_col_e<K>(C, sm, sred, mode, alpha, kbin, sin, pv, out, slot);
+}
+
+__global__ void k_upd(Ctx C, int k, int last) {
+  __shared__ double sred[32];
+  phase_upd(C, sred, k, last != 0);
+}
+
+__global__ void k_init(Ctx C, const float2* xprev, float damping) { phase_init(C, xprev, damping); }
+
+__global__ void k_final(Ctx C, float2* xout, float2* rho_out, float2* img_out) {
+  phase_final(C, xout, rho_out, img_out);
+}
+
+constexpr int kMaxNewton = 32;
+struct FrameArgs {
+  const float2* Y;
+  const float* P;
+  const float2* xprev;
+  float2* xout;
+  float2* rho_out;
+  float2* img_out;
+  int M, K;
+  float damping;
+  float alpha[kMaxNewton];
+};
+
+// One whole NLINV frame in one cooperative launch: every phase of every
+// Newton step and CG iteration, separated by bounded grid barriers.
+template <class K>
+__global__ void __launch_bounds__(K::BS) k_frame(Ctx C, FrameArgs F) {
+  extern __shared__ float2 sm[];
+  __shared__ double sred[32];
+  const int NN = C.N * C.N;
+#define NLINV_SYNC() \
+  if (!grid_sync(C)) return
+  phase_init(C, F.xprev, F.damping);
+  NLINV_SYNC();
+  for (int n = 0; n < F.M; ++n) {
+    const float alpha = F.alpha[n];
+    // Newton right-hand side: DF^H (Y - P F^(x^_n)) - alpha_n (x^_n - x_ref)
+    phase_coil_y<K>(C, sm, C.xn + NN, false, 0, sred, C.h);
+    NLINV_SYNC();
+    phase_row_b<K>(C, sm, ROW_COIL, C.h, C.xn, nullptr, nullptr, C.v);
+    NLINV_SYNC();
+    phase_col_c<K>(C, sm, COL_RHS, F.P, F.Y, nullptr, C.v);
+    NLINV_SYNC();
+    phase_row_d<K>(C, sm, C.xn, C.v, C.s, C.kb);
+    NLINV_SYNC();
+    phase_col_e<K>(C, sm, sred, E_RHS, alpha, C.kb, C.s, nullptr, C.r, SLOT_RR0);
+    NLINV_SYNC();
+    for (int k = 0; k < F.K; ++k) {
+      phase_coil_y<K>(C, sm, nullptr, true, k, sred, C.h);
+      NLINV_SYNC();
+      phase_row_b<K>(C, sm, ROW_LIN, C.h, C.xn, C.p, nullptr, C.v);
+      NLINV_SYNC();
+      phase_col_c<K>(C, sm, COL_TOEP, F.P, nullptr, nullptr, C.v);
+      NLINV_SYNC();
+      phase_row_d<K>(C, sm, C.xn, C.v, C.s, C.kb);
+      NLINV_SYNC();
+      phase_col_e<K>(C, sm, sred, E_CG, alpha, C.kb, C.s, C.p, C.q, SLOT_PQ);
+      NLINV_SYNC();
+      phase_upd(C, sred, k, k == F.K - 1);
+      NLINV_SYNC();
+    }
+  }
+  phase_coil_y<K>(C, sm, C.xn + NN, false, 0, sred, C.h);
+  NLINV_SYNC();
+  phase_row_b<K>(C, sm, ROW_COILONLY, C.h, nullptr, nullptr, nullptr, nullptr);
+  NLINV_SYNC();
+  phase_final(C, F.xout, F.rho_out, F.img_out);
+#undef NLINV_SYNC
+}
+
+// bounded wait on a device flag (used to test the timeout path)
+__global__ void k_wait_flag(const volatile int* flag, int expected, long long limit, int* err) {
+  if (threadIdx.x != 0) return;
+  long long it = 0;
+  while (*flag != expected) {
+    if (++it > limit) {
+      atomicCAS(err, 0, NLINV_ETIMEOUT);
+      return;
+    }
+    __nanosleep(100);
+  }
+}
+
+// ----------------------------------------------- preprocessing kernels
+// Dirichlet kernel tables Dx[s][f] = Dir(kx_s - f/G), Dy likewise (FP64 math)
+__global__ void k_dirichlet(int N, int G, int S, const double* __restrict__ kxy, float* Dx, float* Dy) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= S * G) return;
+  const int s = idx / G, f = idx - s * G;
+  const double ff = (double)f / G, m = 2.0 * N - 1.0;
+#pragma unroll
+  for (int ax = 0; ax < 2; ++ax) {
+    const double tt = kxy[2 * s + ax] - ff;
+    const double r = tt - rint(tt);
+    const double val = (r == 0.0) ? m : sinpi(m * r) / sinpi(r);
+    (ax ? Dy : Dx)[idx] = (float)val;
+  }
+}
+
+// P[fy][fx] = scale * sum_s Dy[s][fy] Dx[s][fx]   (FP64 accumulation)
+__global__ void k_psf_gemm(int G, int S, const float* __restrict__ Dx, const float* __restrict__ Dy, float* P,
+                           double scale) {
+  __shared__ float ay[16][17], ax[16][17];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int fx = blockIdx.x * 16 + tx, fy = blockIdx.y * 16 + ty;
+  const int fyl = blockIdx.y * 16 + tx;
+  double acc = 0.0;
+  for (int s0 = 0; s0 < S; s0 += 16) {
+    const int s = s0 + ty;
+    ay[ty][tx] = (s < S && fyl < G) ? Dy[(size_t)s * G + fyl] : 0.f;
+    ax[ty][tx] = (s < S && fx < G) ? Dx[(size_t)s * G + fx] : 0.f;
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 16; ++u) acc = fma((double)ay[u][ty], (double)ax[u][tx], acc);
+    __syncthreads();
+  }
+  if (fx < G && fy < G) P[(size_t)fy * G + fx] = (float)(acc * scale);
+}
+
+// E[s][r] = exp(+2 pi i k_s r), phase reduced mod 1 in FP64
+__global__ void k_ndft_tables(int N, int S, const double* __restrict__ kxy, float2* Ex, float2* Ey) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= S * N) return;
+  const int s = idx / N, r = idx - s * N;
+#pragma unroll
+  for (int ax = 0; ax < 2; ++ax) {
+    const double tt = kxy[2 * s + ax] * r;
+    const double fr = tt - rint(tt);
+    double sn, cs;
+    sincospi(2.0 * fr, &sn, &cs);
+    (ax ? Ey : Ex)[idx] = make_float2((float)cs, (float)sn);
+  }
+}
+
+// img[j][y][x] = scale * sum_s y[j][s] Ey[s][y] Ex[s][x]
+__global__ void k_adj_ndft(int N, int S, const float2* __restrict__ yv, const float2* __restrict__ Ex,
+                           const float2* __restrict__ Ey, float2* img, float scale) {
+  __shared__ float2 A[16][17], B[16][17];
+  const int tx = threadIdx.x, ty = threadIdx.y, j = blockIdx.z;
+  const int x = blockIdx.x * 16 + tx, y = blockIdx.y * 16 + ty;
+  const int yl = blockIdx.y * 16 + tx;
+  float2 acc = czero();
+  for (int s0 = 0; s0 < S; s0 += 16) {
+    const int s = s0 + ty;
+    float2 a = czero(), b = czero();
+    if (s < S) {
+      if (yl < N) a = cmul(yv[(size_t)j * S + s], Ey[(size_t)s * N + yl]);
+      if (x < N) b = Ex[(size_t)s * N + x];
+    }
+    A[ty][tx] = a;
+    B[ty][tx] = b;
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const float2 p = A[u][ty], q = B[u][tx];
+      acc.x = fmaf(p.x, q.x, fmaf(-p.y, q.y, acc.x));
+      acc.y = fmaf(p.x, q.y, fmaf(p.y, q.x, acc.y));
+    }
+    __syncthreads();
+  }
+  if (x < N && y < N) img[((size_t)j * N + y) * N + x] = cscale(acc, scale);
+}
+
+// ----------------------------------------------------- size dispatch
+template <class F>
+int dispatch(int G, F&& f) {
+  switch (G) {
+    case 16: return f(Cfg<4, 4>{});
+    case 24: return f(Cfg<4, 6>{});
+    case 40: return f(Cfg<4, 10>{});
+    case 64: return f(Cfg<8, 8>{});
+    case 128: return f(Cfg<8, 16>{});
+    case 256: return f(Cfg<16, 16>{});
+    case 320: return f(Cfg<16, 20>{});
+    case 384: return f(Cfg<16, 24>{});
+    case 512: return f(Cfg<16, 32>{});
+    default: return NLINV_EUNSUPPORTED;
+  }
+}
+
+bool supported_grid(int G) {
+  return dispatch(G, [](auto) { return NLINV_OK; }) == NLINV_OK;
+}
+
+std::mutex g_mu;
+bool g_tw_ready[64] = {};
+
+int ensure_constants(int dev) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (dev < 0 || dev >= 64) return NLINV_EINVAL;
+  if (g_tw_ready[dev]) return NLINV_OK;
+  float2 h[TWL];
+  for (int e = 0; e < TWL; ++e) {
+    const double a = -2.0 * M_PI * (double)e / TWL;
+    h[e] = make_float2((float)std::cos(a), (float)std::sin(a));
+  }
+  CK(cudaMemcpyToSymbol(c_tw, h, sizeof(h)));
+  g_tw_ready[dev] = true;
+  return NLINV_OK;
+}
+
+bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
+
+}  // namespace
+
+// ================================================================== plan
+struct nlinv_plan_s {
+  nlinv_params_t prm;
+  int N, G, Gc, J, U;
+  long long nx;
+  int dev, nsm;
+  void* mem = nullptr;
+  void* prep = nullptr;
+  size_t prep_bytes = 0;
+  Ctx C;
+  float* psf;
+  int coop_grid = 0;
+};
+
+namespace {
+
+size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+int plan_grid(int items, int min_items) {
+  int g = items > min_items ? items : min_items;
+  if (g < 1) g = 1;
+  return g > kMaxPart ? kMaxPart : g;
+}
+
+template <class K>
+int set_smem_attrs() {
+  if (K::SMEM > 48 * 1024) {
+    CK(cudaFuncSetAttribute(k_coil_y<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
+    CK(cudaFuncSetAttribute(k_row_b<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
+    CK(cudaFuncSetAttribute(k_col_c<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
+    CK(cudaFuncSetAttribute(k_row_d<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
+    CK(cudaFuncSetAttribute(k_col_e<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
+    CK(cudaFuncSetAttribute(k_frame<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
+  }
+  return NLINV_OK;
+}
+
+// launch helpers for the one-launch-per-phase path
+template <class K>
+struct Launch {
+  const nlinv_plan_s* pl;
+  cudaStream_t st;
+  int coil_y(const float2* src, int upd, int k, float2* hout) const {
+    const Ctx& C = pl->C;
+    const int items = C.J * ((C.Gc + K::TW - 1) / K::TW);
+    const int g = plan_grid(items, upd ? (C.N * C.N + K::BS - 1) / K::BS : 1);
+    k_coil_y<K><<<g, K::BS, K::SMEM, st>>>(C, src, upd, k, hout);
+    CKL("k_coil_y");
+    return NLINV_OK;
+  }
+  int row_b(int mode, const float2* hin, const float2* rho, const float2* drho, const float2* img,
+            float2* vout) const {
+    const Ctx& C = pl->C;
+    const int g = plan_grid(C.J * ((C.N + K::TW - 1) / K::TW), 1);
+    k_row_b<K><<<g, K::BS, K::SMEM, st>>>(C, mode, hin, rho, drho, img, vout);
+    CKL("k_row_b");
+    return NLINV_OK;
+  }
+  int col_c(int mode, const float* P, const float2* Yin, float2* zout, float2* vio) const {
+    const Ctx& C = pl->C;
+    const int g = plan_grid(C.J * ((C.G + K::TW - 1) / K::TW), 1);
+    k_col_c<K><<<g, K::BS, K::SMEM, st>>>(C, mode, P, Yin, zout, vio);
+    CKL("k_col_c");
+    return NLINV_OK;
+  }
+  int row_d(const float2* rho, const float2* win, float2* sout, float2* kbout) const {
+    const Ctx& C = pl->C;
+    const int g = plan_grid(C.J * ((C.N + K::TW - 1) / K::TW), 1);
+    k_row_d<K><<<g, K::BS, K::SMEM, st>>>(C, rho, win, sout, kbout);
+    CKL("k_row_d");
+    return NLINV_OK;
+  }
+  int col_e(int mode, float alpha, const float2* kbin, const float2* sin, const float2* pv, float2* out,
+            int slot) const {
+    const Ctx& C = pl->C;
+    const int items = C.J * ((C.Gc + K::TW - 1) / K::TW);
+    const int g = plan_grid(items, (C.N * C.N + K::BS - 1) / K::BS);
+    k_col_e<K><<<g, K::BS, K::SMEM, st>>>(C, mode, alpha, kbin, sin, pv, out, slot);
+    CKL("k_col_e");
+    return NLINV_OK;
+  }
+  int upd(int k, int last) const {
+    const Ctx& C = pl->C;
+    const int g = plan_grid((int)((C.nx + 255) / 256), 1);
+    k_upd<<<g, 256, 0, st>>>(C, k, last);
+    CKL("k_upd");
+    return NLINV_OK;
+  }
+  // coil maps c_j = W^-1 c^_j of x^ into the plan's c buffer
+  int coils(const float2* xhat) const {
+    const Ctx& C = pl->C;
+    int rc = coil_y(xhat + (size_t)C.N * C.N, 0, 0, C.h);
+    if (rc) return rc;
+    return row_b(ROW_COILONLY, C.h, nullptr, nullptr, nullptr, nullptr);
+  }
+};
+
+#define RC(x)                 \
+  do {                        \
+    int rc_ = (x);            \
+    if (rc_ != NLINV_OK) return rc_; \
+  } while (0)
+
+int check_plan(const nlinv_plan_s* pl) { return pl ? NLINV_OK : NLINV_EINVAL; }
+
+}  // namespace
+
+extern "C" {
+
+const char* nlinv_strerror(int code) {
+  switch (code) {
+    case NLINV_OK: return "ok";
+    case NLINV_EINVAL: return "invalid argument";
+    case NLINV_ECUDA: return "CUDA runtime error";
+    case NLINV_ENOMEM: return "out of device memory";
+    case NLINV_ETIMEOUT: return "bounded device wait expired";
+    case NLINV_ENUMERIC: return "CG breakdown (Re<p,Ap> <= 0 or not finite)";
+    case NLINV_EUNSUPPORTED: return "unsupported grid size";
+    default: return "unknown error";
+  }
+}
+
+const char* nlinv_last_cuda_error(void) { return g_cuda_err; }
+
+int nlinv_default_params(nlinv_params_t* p, int N, int J) {
+  if (!p || N <= 0 || J <= 0) return NLINV_EINVAL;
+  std::memset(p, 0, sizeof(*p));
+  p->N = N;
+  p->J = J;
+  p->Gc = 0;
+  p->newton_steps = 7;
+  p->cg_iters = 10;
+  p->n_turns = 1;
+  p->alpha0 = 1.0;
+  p->q = 0.5;
+  p->damping = 1.0;
+  p->w_a = 220.0;
+  p->w_l = 32.0;
+  p->spin_limit = 0;
+  p->exec_mode = 0;
+  return NLINV_OK;
+}
+
+int nlinv_plan(nlinv_plan_t* out, const nlinv_params_t* p, const float* psf, nlinv_stream_t stream) {
+  if (!out || !p) return NLINV_EINVAL;
+  *out = nullptr;
+  const int N = p->N, G = 2 * p->N, J = p->J;
+  const int Gc = p->Gc ? p->Gc : G / 4;
+  if (N <= 0 || J <= 0 || J > 4096) return NLINV_EINVAL;
+  if (!supported_grid(G)) return NLINV_EUNSUPPORTED;
+  if (Gc < 2 || Gc > G || (Gc & 1)) return NLINV_EINVAL;
+  if (p->newton_steps < 1 || p->newton_steps > kMaxNewton) return NLINV_EINVAL;
+  if (p->cg_iters < 0 || p->cg_iters > 4096) return NLINV_EINVAL;
+  if (p->n_turns < 1 || p->n_turns > 1024) return NLINV_EINVAL;
+  if (!(p->alpha0 > 0.0) || !(p->q > 0.0) || p->q > 1.0 || !(p->damping >= 0.0)) return NLINV_EINVAL;
+  if (!(p->w_a >= 0.0) || !(p->w_l >= 0.0)) return NLINV_EINVAL;
+  if (p->exec_mode != 0 && p->exec_mode != 1) return NLINV_EINVAL;
+  if (psf && ((uintptr_t)psf & 3u)) return NLINV_EINVAL;
+
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  RC(ensure_constants(dev));
+
+  nlinv_plan_s* pl = new nlinv_plan_s();
+  pl->prm = *p;
+  pl->prm.Gc = Gc;
+  if (pl->prm.spin_limit <= 0) pl->prm.spin_limit = 1LL << 22;
+  pl->N = N;
+  pl->G = G;
+  pl->Gc = Gc;
+  pl->J = J;
+  pl->U = p->n_turns;
+  pl->nx = (long long)N * N + (long long)J * Gc * Gc;
+  pl->dev = dev;
+  cudaError_t e = cudaDeviceGetAttribute(&pl->nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) {
+    delete pl;
+    return cuda_fail(e, "cudaDeviceGetAttribute");
+  }
+
+  // one allocation, carved into the buffers
+  const size_t f2 = sizeof(float2);
+  const size_t nx = (size_t)pl->nx;
+  size_t off[32];
+  size_t tot = 0;
+  int nb = 0;
+  auto take = [&](size_t bytes) {
+    off[nb++] = tot;
+    tot += align_up(bytes);
+  };
+  take(G * f2);                          // 0 tw
+  take((size_t)Gc * Gc * sizeof(float)); // 1 dinv
+  take((size_t)pl->U * G * G * sizeof(float));  // 2 psf
+  take((size_t)J * N * N * f2);          // 3 c
+  take((size_t)J * N * Gc * f2);         // 4 h
+  take((size_t)J * N * G * f2);          // 5 v
+  take((size_t)J * N * N * f2);          // 6 s
+  take((size_t)J * N * Gc * f2);         // 7 kb
+  for (int i = 0; i < 6; ++i) take(nx * f2);  // 8..13 xn xref xcg r p q
+  take((size_t)NSLOT * kMaxPart * sizeof(double));  // 14 part
+  take(NSLOT * sizeof(int));             // 15 pcount
+  take(sizeof(int));                     // 16 err
+  take(2 * sizeof(unsigned));            // 17 bar
+  e = cudaMalloc(&pl->mem, tot);
+  if (e != cudaSuccess) {
+    delete pl;
+    return cuda_fail(e, "cudaMalloc(plan)");
+  }
+  char* base = (char*)pl->mem;
+  Ctx& C = pl->C;
+  C.N = N;
+  C.G = G;
+  C.Gc = Gc;
+  C.J = J;
+  C.nx = (int)nx;
+  C.U = pl->U;
+  C.inv_G = (float)(1.0 / G);
+  C.inv_G2 = (float)(1.0 / ((double)G * G));
+  C.tw = (const float2*)(base + off[0]);
+  C.dinv = (const float*)(base + off[1]);
+  pl->psf = (float*)(base + off[2]);
+  C.psf = pl->psf;
+  C.c = (float2*)(base + off[3]);
+  C.h = (float2*)(base + off[4]);
+  C.v = (float2*)(base + off[5]);
+  C.s = (float2*)(base + off[6]);
+  C.kb = (float2*)(base + off[7]);
+  C.xn = (float2*)(base + off[8]);
+  C.xref = (float2*)(base + off[9]);
+  C.xcg = (float2*)(base + off[10]);
+  C.r = (float2*)(base + off[11]);
+  C.p = (float2*)(base + off[12]);
+  C.q = (float2*)(base + off[13]);
+  C.part = (double*)(base + off[14]);
+  C.pcount = (int*)(base + off[15]);
+  C.err = (int*)(base + off[16]);
+  C.bar = (unsigned*)(base + off[17]);
+  C.spin_limit = pl->prm.spin_limit;
+
+  // host tables in FP64, rounded once
+  std::vector<float2> tw(G);
+  for (int k = 0; k < G; ++k) {
+    const double a = -2.0 * M_PI * (double)k / G;
+    tw[k] = make_float2((float)std::cos(a), (float)std::sin(a));
+  }
+  std::vector<float> dinv((size_t)Gc * Gc);
+  for (int iy = 0; iy < Gc; ++iy) {
+    const int fy = iy < (Gc + 1) / 2 ? iy : iy - Gc;
+    for (int ix = 0; ix < Gc; ++ix) {
+      const int fx = ix < (Gc + 1) / 2 ? ix : ix - Gc;
+      const double ky = 2.0 * fy / G, kx = 2.0 * fx / G;
+      dinv[(size_t)iy * Gc + ix] = (float)std::pow(1.0 + p->w_a * (kx * kx + ky * ky), -p->w_l / 2.0);
+    }
+  }
+  int rc = NLINV_OK;
+  auto fail = [&](int code) {
+    cudaFree(pl->mem);
+    delete pl;
+    return code;
+  };
+  if ((e = cudaMemsetAsync(pl->mem, 0, tot, st)) != cudaSuccess) return fail(cuda_fail(e, "memset"));
+  if ((e = cudaMemcpyAsync((void*)C.tw, tw.data(), G * f2, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return fail(cuda_fail(e, "tw"));
+  if ((e = cudaMemcpyAsync((void*)C.dinv, dinv.data(), dinv.size() * sizeof(float), cudaMemcpyHostToDevice,
+                           st)) != cudaSuccess)
+    return fail(cuda_fail(e, "dinv"));
+  if (psf) {
+    if ((e = cudaMemcpyAsync(pl->psf, psf, (size_t)pl->U * G * G * sizeof(float), cudaMemcpyDeviceToDevice,
+                             st)) != cudaSuccess)
+      return fail(cuda_fail(e, "psf"));
+  }
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(cuda_fail(e, "sync"));
+
+  rc = dispatch(G, [&](auto k) -> int {
+    using K = decltype(k);
+    RC(set_smem_attrs<K>());
+    int nbk = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nbk, k_frame<K>, K::BS, K::SMEM));
+    int g = nbk * pl->nsm;
+    if (g > kMaxPart) g = kMaxPart;
+    pl->coop_grid = g;
+    return g > 0 ? NLINV_OK : NLINV_ECUDA;
+  });
+  if (rc != NLINV_OK) return fail(rc);
+  *out = pl;
+  return NLINV_OK;
+}
+
+int nlinv_plan_destroy(nlinv_plan_t pl) {
+  if (!pl) return NLINV_EINVAL;
+  cudaFree(pl->prep);
+  cudaError_t e = cudaFree(pl->mem);
+  delete pl;
+  return e == cudaSuccess ? NLINV_OK : cuda_fail(e, "cudaFree");
+}
+
+int nlinv_plan_sizes(nlinv_plan_t pl, long long* nx, int* G, int* Gc) {
+  RC(check_plan(pl));
+  if (nx) *nx = pl->nx;
+  if (G) *G = pl->G;
+  if (Gc) *Gc = pl->Gc;
+  return NLINV_OK;
+}
+
+int nlinv_set_psf(nlinv_plan_t pl, int turn, const float* psf, nlinv_stream_t stream) {
+  RC(check_plan(pl));
+  if (!psf || turn < 0 || turn >= pl->U || ((uintptr_t)psf & 3u)) return NLINV_EINVAL;
+  const size_t bytes = (size_t)pl->G * pl->G * sizeof(float);
+  CK(cudaMemcpyAsync(pl->psf + (size_t)turn * pl->G * pl->G, psf, bytes, cudaMemcpyDeviceToDevice,
+                     (cudaStream_t)stream));
+  return NLINV_OK;
+}
+
+static int ensure_prep(nlinv_plan_s* pl, size_t bytes) {
+  if (pl->prep_bytes >= bytes) return NLINV_OK;
+  if (pl->prep) {
+    CK(cudaFree(pl->prep));
+    pl->prep = nullptr;
+    pl->prep_bytes = 0;
+  }
+  CK(cudaMalloc(&pl->prep, bytes));
+  pl->prep_bytes = bytes;
+  return NLINV_OK;
+}
+
+int nlinv_psf(nlinv_plan_t pl, int turn, int S, const double* kxy, float* P_out, nlinv_stream_t stream) {
+  RC(check_plan(pl));
+  if (turn < 0 || turn >= pl->U || S <= 0 || !kxy || ((uintptr_t)kxy & 7u)) return NLINV_EINVAL;
+  if (P_out && ((uintptr_t)P_out & 3u)) return NLINV_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int G = pl->G;
+  RC(ensure_prep(pl, (size_t)2 * S * G * sizeof(float)));
+  float* Dx = (float*)pl->prep;
+  float* Dy = Dx + (size_t)S * G;
+  const int tot = S * G;
+  k_dirichlet<<<(tot + 255) / 256, 256, 0, st>>>(pl->N, G, S, kxy, Dx, Dy);
+  CKL("k_dirichlet");
+  float* P = pl->psf + (size_t)turn * G * G;
+  k_psf_gemm<<<dim3((G + 15) / 16, (G + 15) / 16), dim3(16, 16), 0, st>>>(G, S, Dx, Dy, P,
+                                                                         1.0 / ((double)G * G));
+  CKL("k_psf_gemm");
+  if (P_out) CK(cudaMemcpyAsync(P_out, P, (size_t)G * G * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  return NLINV_OK;
+}
+
+int nlinv_grid(nlinv_plan_t pl, int S, const double* kxy, const void* y, void* Y_out, nlinv_stream_t stream) {
+  RC(check_plan(pl));
+  if (S <= 0 || !kxy || !y || !Y_out || ((uintptr_t)kxy & 7u) || !aligned8(y) || !aligned8(Y_out))
+    return NLINV_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int N = pl->N, J = pl->J;
+  RC(ensure_prep(pl, (size_t)2 * S * N * sizeof(float2)));
+  float2* Ex = (float2*)pl->prep;
+  float2* Ey = Ex + (size_t)S * N;
+  k_ndft_tables<<<(S * N + 255) / 256, 256, 0, st>>>(N, S, kxy, Ex, Ey);
+  CKL("k_ndft_tables");
+  k_adj_ndft<<<dim3((N + 15) / 16, (N + 15) / 16, J), dim3(16, 16), 0, st>>>(
+      N, S, (const float2*)y, Ex, Ey, pl->C.s, (float)(1.0 / pl->G));
+  CKL("k_adj_ndft");
+  return dispatch(pl->G, [&](auto k) -> int {
+    using K = decltype(k);
+    Launch<K> L{pl, st};
+    RC(L.row_b(ROW_IMG, nullptr, nullptr, nullptr, pl->C.s, pl->C.v));
+    return L.col_c(COL_FWD, nullptr, nullptr, (float2*)Y_out, pl->C.v);
+  });
+}
+
+int nlinv_apply_DF(nlinv_plan_t pl, const void* xhat, const void* dx, void* z, nlinv_stream_t stream) {
+  RC(check_plan(pl));
+  if (!xhat || !dx || !z || !aligned8(xhat) || !aligned8(dx) || !aligned8(z)) return NLINV_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const float2* xh = (const float2*)xhat;
+  const float2* d = (const float2*)dx;
+  const size_t NN = (size_t)pl->N * pl->N;
+  return dispatch(pl->G, [&](auto k) -> int {
+    using K = decltype(k);
+    Launch<K> L{pl, st};
+    RC(L.coils(xh));
+    RC(L.coil_y(d + NN, 0, 0, pl->C.h));
+    RC(L.row_b(ROW_LIN, pl->C.h, xh, d, nullptr, pl->C.v));
+    return L.col_c(COL_FWD, nullptr, nullptr, (float2*)z, pl->C.v);
+  });
+}
+
+int nlinv_apply_DFH(nlinv_plan_t pl, const void* xhat, const void* z, void* dx_out, nlinv_stream_t stream) {
+  RC(check_plan(pl));
+  if (!xhat || !z || !dx_out || !aligned8(xhat) || !aligned8(z) || !aligned8(dx_out)) return NLINV_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const float2* xh = (const float2*)xhat;
+  return dispatch(pl->G, [&](auto k) -> int {
+    using K = decltype(k);
+    Launch<K> L{pl, st};
+    RC(L.coils(xh));
+    RC(L.col_c(COL_INV, nullptr, (const float2*)z, nullptr, pl->C.v));
+    RC(L.row_d(xh, pl->C.v, pl->C.s, pl->C.kb));
+    return L.col_e(E_DFH, 0.f, pl->C.kb, pl->C.s, nullptr, (float2*)dx_out, SLOT_PQ);
+  });
+}
+
+int nlinv_apply_normal(nlinv_plan_t pl, const void* xhat, const void* dx, int turn, double alpha, void* out,
+                       nlinv_stream_t stream) {
+  RC(check_plan(pl));
+  if (!xhat || !dx || !out || !aligned8(xhat) || !aligned8(dx) || !aligned8(out)) return NLINV_EINVAL;
+  if (turn < 0 || turn >= pl->U || !(alpha >= 0.0)) return NLINV_EINVAL;
+  if (out == xhat || out == dx) return NLINV_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const float2* xh = (const float2*)xhat;
+  const float2* d = (const float2*)dx;
+  const size_t NN = (size_t)pl->N * pl->N;
+  const float* P = pl->psf + (size_t)turn * pl->G * pl->G;
+  return dispatch(pl->G, [&](auto k) -> int {
+    using K = decltype(k);
+    Launch<K> L{pl, st};
+    RC(L.coils(xh));
+    RC(L.coil_y(d + NN, 0, 0, pl->C.h));
+    RC(L.row_b(ROW_LIN, pl->C.h, xh, d, nullptr, pl->C.v));
+    RC(L.col_c(COL_TOEP, P, nullptr, nullptr, pl->C.v));
+    RC(L.row_d(xh, pl->C.v, pl->C.s, pl->C.kb));
+    return L.col_e(E_NORMAL, (float)alpha, pl->C.kb, pl->C.s, d, (float2*)out, SLOT_PQ);
+  });
+}
+
+int nlinv_frame(nlinv_plan_t pl, const void* Y, int turn, const void* x_prev, void* x_out, void* rho_out,
+                void* img_out, nlinv_stream_t stream) {
+  RC(check_plan(pl));
+  if (!Y || !x_out || !aligned8(Y) || !aligned8(x_out)) return NLINV_EINVAL;
+  if ((x_prev && !aligned8(x_prev)) || (rho_out && !aligned8(rho_out)) || (img_out && !aligned8(img_out)))
+    return NLINV_EINVAL;
+  if (turn < 0 || turn >= pl->U) return NLINV_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const nlinv_params_t& p = pl->prm;
+  FrameArgs F;
+  std::memset(&F, 0, sizeof(F));
+  F.Y = (const float2*)Y;
+  F.P = pl->psf + (size_t)turn * pl->G * pl->G;
+  F.xprev = (const float2*)x_prev;
+  F.xout = (float2*)x_out;
+  F.rho_out = (float2*)rho_out;
+  F.img_out = (float2*)img_out;
+  F.M = p.newton_steps;
+  F.K = p.cg_iters;
+  F.damping = (float)p.damping;
+  for (int n = 0; n < F.M; ++n) F.alpha[n] = (float)(p.alpha0 * std::pow(p.q, n));
+  Ctx C = pl->C;
+  const int NN = pl->N * pl->N;
+  return dispatch(pl->G, [&](auto k) -> int {
+    using K = decltype(k);
+    if (p.exec_mode == 0) {
+      CK(cudaMemsetAsync(C.bar, 0, 2 * sizeof(unsigned), st));
+      void* args[] = {(void*)&C, (void*)&F};
+      CK(cudaLaunchCooperativeKernel((const void*)k_frame<K>, dim3(pl->coop_grid), dim3(K::BS), args,
+                                     (size_t)K::SMEM, st));
+      return NLINV_OK;
+    }
+    Launch<K> L{pl, st};
+    const int ge = plan_grid((int)((C.nx + 255) / 256), 1);
+    k_init<<<ge, 256, 0, st>>>(C, F.xprev, F.damping);
+    CKL("k_init");
+    for (int n = 0; n < F.M; ++n) {
+      const float alpha = F.alpha[n];
+      RC(L.coil_y(C.xn + NN, 0, 0, C.h));
+      RC(L.row_b(ROW_COIL, C.h, C.xn, nullptr, nullptr, C.v));
+      RC(L.col_c(COL_RHS, F.P, F.Y, nullptr, C.v));
+      RC(L.row_d(C.xn, C.v, C.s, C.kb));
+      RC(L.col_e(E_RHS, alpha, C.kb, C.s, nullptr, C.r, SLOT_RR0));
+      for (int kk = 0; kk < F.K; ++kk) {
+        RC(L.coil_y(nullptr, 1, kk, C.h));
+        RC(L.row_b(ROW_LIN, C.h, C.xn, C.p, nullptr, C.v));
+        RC(L.col_c(COL_TOEP, F.P, nullptr, nullptr, C.v));
+        RC(L.row_d(C.xn, C.v, C.s, C.kb));
+        RC(L.col_e(E_CG, alpha, C.kb, C.s, C.p, C.q, SLOT_PQ));
+        RC(L.upd(kk, kk == F.K - 1));
+      }
+    }
+    RC(L.coils(C.xn));
+    k_final<<<ge, 256, 0, st>>>(C, F.xout, F.rho_out, F.img_out);
+    CKL("k_final");
+    return NLINV_OK;
+  });
+}
+
+int nlinv_sync(nlinv_plan_t pl, nlinv_stream_t stream) {
+  RC(check_plan(pl));
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  int h = 0;
+  CK(cudaMemcpy(&h, pl->C.err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h != 0) CK(cudaMemset(pl->C.err, 0, sizeof(int)));
+  return h;
+}
+
+int nlinv_wait_flag(nlinv_plan_t pl, const int* flag, int expected, long long spin_limit, nlinv_stream_t stream) {
+  RC(check_plan(pl));
+  if (!flag || spin_limit <= 0 || ((uintptr_t)flag & 3u)) return NLINV_EINVAL;
+  k_wait_flag<<<1, 32, 0, (cudaStream_t)stream>>>(flag, expected, spin_limit, pl->C.err);
+  CKL("k_wait_flag");
+  return NLINV_OK;
+}
+
+}  // extern "C"

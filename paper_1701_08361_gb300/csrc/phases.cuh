@@ -1,0 +1,654 @@
+// Device phases of the NLINV hot path (Schaetz et al. 2017, Sec. 2.2,
+// Eqs. (2)-(5), Fig. 4) on one GB300.
+//
+// One application of the normal operator  DF^H P DF + alpha I  (Eq. (4)-(5)
+// with the non-uniform pair replaced by the PSF multiplier P on the twofold
+// grid) is five passes over per-channel data; each pass is one fused kernel
+// phase and every pass keeps its 1-D FFTs in registers (see fft.cuh):
+//
+//   A  coil_y : W^-1 along y.  c^_j columns (G_c nonzero of G) -> N rows.
+//               In CG it first forms p = r + beta p (the CG direction update).
+//   B  row_b  : W^-1 along x, then u_j = c_j drho + rho dc_j, then the
+//               forward FFT of the zero-padded row (N nonzero of G).
+//   C  col_c  : along y: FFT (N nonzero of G), x P / G^2, inverse FFT, keep
+//               N rows -- the whole PSF convolution of a column in one go.
+//   D  row_d  : inverse FFT along x, keep N: t_j.  s_j = conj(c_j) t_j is
+//               stored for the channel sum; conj(rho) t_j is FFT'd along x and
+//               cropped to the G_c coil band.
+//   E  col_e  : FFT along y, crop to G_c, x D_W^-1: the W^-H part; plus the
+//               channel sum  sum_j s_j  for the rho part; plus the Tikhonov
+//               term and the CG inner product Re<p, q> (FP64 partials).
+//   F  upd    : x += a p, r -= a q, |r|^2 (FP64 partials).
+//
+// Data layouts (complex64 interleaved, row-major):
+//   x^ vector   : rho [N][N] followed by c^ [J][Gc][Gc]        (n_x elements)
+//   c  (coils)  : [J][N][N]      h  : [J][N][Gc]   (after the y pass of W^-1)
+//   v  (rows)   : [J][N][G]      s  : [J][N][N]    kb : [J][N][Gc]
+//   P           : [U][G][G] real  D_W^-1 : [Gc][Gc] real
+// The FOV occupies rows/cols [0, N) of the G grid; the c^ grid holds
+// frequency f at index f mod Gc and at index f mod G of the G grid.
+//
+// Buffers written by one phase and read by another are read with ld.global.cg
+// (L2, not L1) because the persistent kernel runs every phase in one launch.
+#pragma once
+#include "fft.cuh"
+
+namespace nlinv {
+
+constexpr int kMaxPart = 4096;     // max CTAs that deposit an FP64 partial
+enum { SLOT_PQ = 0, SLOT_RR0 = 1, SLOT_RR1 = 2, NSLOT = 4 };
+enum { DEV_ETIMEOUT = -4, DEV_ENUMERIC = -5 };
+
+enum RowMode { ROW_COIL = 0, ROW_COILONLY = 1, ROW_LIN = 2, ROW_IMG = 3 };
+enum ColMode { COL_TOEP = 0, COL_RHS = 1, COL_FWD = 2, COL_INV = 3 };
+enum EMode { E_CG = 0, E_RHS = 1, E_DFH = 2, E_NORMAL = 3 };
+
+struct Ctx {
+  int N, G, Gc, J, nx, U;
+  float inv_G, inv_G2;
+  const float2* tw;     // [G] exp(-2 pi i e / G)
+  const float* dinv;    // [Gc][Gc]
+  const float* psf;     // [U][G][G]
+  float2 *c, *h, *v, *s, *kb;
+  float2 *xn, *xref, *xcg, *r, *p, *q;
+  double* part;         // [NSLOT][kMaxPart]
+  int* pcount;          // [NSLOT]
+  int* err;             // latched device error
+  unsigned* bar;        // grid barrier {count, generation}
+  long long spin_limit;
+};
+
+template <int G1_, int G2_> struct Cfg {
+  static constexpr int G1 = G1_, G2 = G2_;
+  static constexpr int G = G1 * G2;
+  static constexpr int MX = G1 > G2 ? G1 : G2;
+  static constexpr int TW = 16;             // columns per tile / rows per group
+  static constexpr int BS = TW * MX;        // threads per CTA
+  static constexpr int RS = G + MX;         // smem stride of one row (float2)
+  static constexpr int SMEM = TW * RS * 8;  // dynamic smem bytes
+  static_assert(G1 % 2 == 0 && G2 % 2 == 0, "G1, G2 must be even");
+};
+
+__device__ __forceinline__ float2 ldcg(const float2* p) { return __ldcg(p); }
+
+// index of grid position pos in the G_c coil band, -1 outside (Gc even)
+__device__ __forceinline__ int coef_index(int pos, int G, int Gc) {
+  const int h = Gc >> 1;
+  if (pos < h) return pos;
+  if (pos >= G - h) return pos - G + Gc;
+  return -1;
+}
+
+// -------------------------------------------------------- reductions
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;   // valid in lane 0
+}
+
+// deterministic block sum of v, stored as this CTA's partial of `slot`
+__device__ __forceinline__ void block_partial(const Ctx& C, double v, int slot, double* sred) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sred[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    const int nw = blockDim.x >> 5;
+    double a = (l < nw) ? sred[l] : 0.0;
+    a = warp_sum(a);
+    if (l == 0) {
+      C.part[slot * kMaxPart + blockIdx.x] = a;
+      if (blockIdx.x == 0) C.pcount[slot] = gridDim.x;
+    }
+  }
+  __syncthreads();
+}
+
+// sum of all partials of `slot` in fixed order (every CTA computes it)
+__device__ __forceinline__ double slot_total(const Ctx& C, int slot, double* sred) {
+  if (threadIdx.x < 32) {
+    const int n = __ldcg(C.pcount + slot);
+    double a = 0.0;
+    for (int i = threadIdx.x; i < n; i += 32) a += __ldcg(C.part + slot * kMaxPart + i);
+    a = warp_sum(a);
+    if (threadIdx.x == 0) sred[0] = a;
+  }
+  __syncthreads();
+  const double t = sred[0];
+  __syncthreads();
+  return t;
+}
+
+__device__ __forceinline__ void raise_err(const Ctx& C, int code) { atomicCAS(C.err, 0, code); }
+
+// ------------------------------------------------ A: W^-1 along y (coil)
+// src: c^ coefficients [J][Gc][Gc].  upd: the CG direction is first updated
+// in place, p = r + beta p (k > 0) or p = r (k == 0), and used as the source.
+template <class K>
+__device__ void phase_coil_y(const Ctx& C, float2* sm, const float2* src, bool upd, int k,
+                             double* sred, float2* hout) {
+  constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW;
+  const int N = C.N, Gc = C.Gc, J = C.J, NN = N * N;
+  const int t = threadIdx.x;
+  float beta = 0.f;
+  if (upd && k > 0) {
+    const double rr1 = slot_total(C, (k & 1) ? SLOT_RR1 : SLOT_RR0, sred);
+    const double rr0 = slot_total(C, (k & 1) ? SLOT_RR0 : SLOT_RR1, sred);
+    beta = (rr0 > 0.0) ? (float)(rr1 / rr0) : 0.f;
+  }
+  const float2* r_c = C.r + NN;
+  float2* p_c = C.p + NN;
+  const int tiles = (Gc + TW - 1) / TW;
+  const int items = J * tiles;
+  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+    const int j = it / tiles;
+    const int fx = (it - j * tiles) * TW + (t % TW);
+    const bool colok = fx < Gc;
+    {  // stage 1: thread (n1, c), inverse DFT over n2
+      const int n1 = t / TW;
+      if (n1 < G1) {
+        float2 a[G2];
+#pragma unroll
+        for (int n2 = 0; n2 < G2; ++n2) {
+          const int iy = coef_index(n1 + G1 * n2, G, Gc);
+          float2 val = czero();
+          if (colok && iy >= 0) {
+            const size_t e = ((size_t)j * Gc + iy) * Gc + fx;
+            if (upd) {
+              const float2 rv = ldcg(r_c + e);
+              val = (k == 0) ? rv : cfma(ldcg(p_c + e), beta, rv);
+              p_c[e] = val;
+            } else {
+              val = ldcg(src + e);
+            }
+            val = cscale(val, __ldg(C.dinv + iy * Gc + fx));
+          }
+          a[n2] = val;
+        }
+        dft<G2, true>(a);
+#pragma unroll
+        for (int k2 = 0; k2 < G2; ++k2) {
+          float2 x = a[k2];
+          if (k2) x = cmul(x, twg<true>(C.tw, n1 * k2));
+          sm[(k2 * G1 + n1) * TW + (t % TW)] = x;
+        }
+      }
+    }
+    __syncthreads();
+    {  // stage 2: thread (k2, c), inverse DFT over n1, keep y < N
+      const int k2 = t / TW, cc = t % TW;
+      if (k2 < G2 && colok) {
+        float2 b[G1];
+#pragma unroll
+        for (int n1 = 0; n1 < G1; ++n1) b[n1] = sm[(k2 * G1 + n1) * TW + cc];
+        dft<G1, true>(b);
+#pragma unroll
+        for (int k1 = 0; k1 < G1 / 2; ++k1) {
+          const int y = k2 + G2 * k1;
+          hout[((size_t)j * N + y) * Gc + fx] = cscale(b[k1], C.inv_G);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (upd) {  // rho part of the direction update
+    for (int e = blockIdx.x * blockDim.x + t; e < NN; e += gridDim.x * blockDim.x) {
+      const float2 rv = ldcg(C.r + e);
+      C.p[e] = (k == 0) ? rv : cfma(ldcg(C.p + e), beta, rv);
+    }
+  }
+}
+
+// ------------------------------------- B: W^-1 along x, product, row FFT
+// mode ROW_COIL    : c = W^-1 c^ stored, u = rho c
+//      ROW_COILONLY: c stored, nothing else
+//      ROW_LIN     : u = c drho + rho dc
+//      ROW_IMG     : u = img (no coil part)
+template <class K>
+__device__ void phase_row_b(const Ctx& C, float2* sm, int mode, const float2* hin,
+                            const float2* rho, const float2* drho, const float2* img,
+                            float2* vout) {
+  constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW, RS = K::RS;
+  const int N = C.N, Gc = C.Gc, J = C.J;
+  const int t = threadIdx.x;
+  const int groups = (N + TW - 1) / TW;
+  const int items = J * groups;
+  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+    const int j = it / groups;
+    const int y0 = (it - j * groups) * TW;
+    if (mode != ROW_IMG) {  // stage 1: thread (row, n1): inverse DFT over n2
+      const int rr = t / G1, n1 = t % G1, y = y0 + rr;
+      if (rr < TW && y < N) {
+        float2 a[G2];
+#pragma unroll
+        for (int n2 = 0; n2 < G2; ++n2) {
+          const int ix = coef_index(n1 + G1 * n2, G, Gc);
+          a[n2] = (ix >= 0) ? ldcg(hin + ((size_t)j * N + y) * Gc + ix) : czero();
+        }
+        dft<G2, true>(a);
+#pragma unroll
+        for (int k2 = 0; k2 < G2; ++k2) {
+          float2 x = a[k2];
+          if (k2) x = cmul(x, twg<true>(C.tw, n1 * k2));
+          sm[rr * RS + k2 * (G1 + 1) + n1] = x;
+        }
+      }
+      __syncthreads();
+    }
+    // stage 2: thread (row, k2): inverse DFT over n1 -> x = k2 + G2 k1,
+    // product, forward DFT over k1 (x = k2 + G2 k1 is the input index)
+    const int rr = t / G2, k2 = t % G2, y = y0 + rr;
+    const bool ok = rr < TW && y < N;
+    float2 u[G1];
+    if (ok) {
+      float2 b[G1];
+      if (mode != ROW_IMG) {
+#pragma unroll
+        for (int n1 = 0; n1 < G1; ++n1) b[n1] = sm[rr * RS + k2 * (G1 + 1) + n1];
+        dft<G1, true>(b);
+      }
+#pragma unroll
+      for (int k1 = 0; k1 < G1; ++k1) {
+        u[k1] = czero();
+        if (k1 < G1 / 2) {
+          const int x = k2 + G2 * k1;
+          const size_t ic = ((size_t)j * N + y) * N + x;
+          const int ir = y * N + x;
+          if (mode == ROW_COIL) {
+            C.c[ic] = b[k1];
+            u[k1] = cmul(ldcg(rho + ir), b[k1]);
+          } else if (mode == ROW_COILONLY) {
+            C.c[ic] = b[k1];
+          } else if (mode == ROW_LIN) {
+            u[k1] = cadd(cmul(ldcg(C.c + ic), ldcg(drho + ir)), cmul(ldcg(rho + ir), b[k1]));
+          } else {
+            u[k1] = ldcg(img + ic);
+          }
+        }
+      }
+      if (mode != ROW_COILONLY) {
+        dft<G1, false>(u);
+#pragma unroll
+        for (int kb = 1; kb < G1; ++kb) u[kb] = cmul(u[kb], twg<false>(C.tw, k2 * kb));
+      }
+    }
+    if (mode == ROW_COILONLY) {
+      __syncthreads();
+      continue;
+    }
+    __syncthreads();
+    if (ok) {
+#pragma unroll
+      for (int kb = 0; kb < G1; ++kb) sm[rr * RS + kb * (G2 + 1) + k2] = u[kb];
+    }
+    __syncthreads();
+    {  // stage 3: thread (row, kb): forward DFT over k2 -> kb + G1 ka
+      const int r3 = t / G1, kb = t % G1, y3 = y0 + r3;
+      if (r3 < TW && y3 < N) {
+        float2 d[G2];
+#pragma unroll
+        for (int a2 = 0; a2 < G2; ++a2) d[a2] = sm[r3 * RS + kb * (G2 + 1) + a2];
+        dft<G2, false>(d);
+        float2* dst = vout + ((size_t)j * N + y3) * G;
+#pragma unroll
+        for (int ka = 0; ka < G2; ++ka) dst[kb + G1 * ka] = d[ka];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------ C: column pass (PSF convolution)
+// COL_TOEP: FFT_y, x P / G^2, iFFT_y, keep N rows (in place in v)
+// COL_RHS : FFT_y, z = (Y - P X / G) / G, iFFT_y, keep N rows
+// COL_FWD : FFT_y, zout = X / G (full G rows), stop
+// COL_INV : X = Yin / G (full G rows given), iFFT_y, keep N rows
+template <class K>
+__device__ void phase_col_c(const Ctx& C, float2* sm, int mode, const float* P,
+                            const float2* Yin, float2* zout, float2* vio) {
+  constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW;
+  const int N = C.N, J = C.J;
+  const int t = threadIdx.x;
+  constexpr int tiles = (G + TW - 1) / TW;
+  const int items = J * tiles;
+  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+    const int j = it / tiles;
+    const int x = (it - j * tiles) * TW + (t % TW);
+    const bool colok = x < G;
+    if (mode != COL_INV) {  // stage 1: thread (n1, c): forward DFT over n2 (y = n1 + G1 n2 < N)
+      const int n1 = t / TW;
+      if (n1 < G1 && colok) {
+        float2 a[G2];
+#pragma unroll
+        for (int n2 = 0; n2 < G2; ++n2)
+          a[n2] = (n2 < G2 / 2) ? ldcg(vio + ((size_t)j * N + n1 + G1 * n2) * G + x) : czero();
+        dft<G2, false>(a);
+#pragma unroll
+        for (int k2 = 0; k2 < G2; ++k2) {
+          float2 v = a[k2];
+          if (k2) v = cmul(v, twg<false>(C.tw, n1 * k2));
+          sm[(k2 * G1 + n1) * TW + (t % TW)] = v;
+        }
+      }
+      __syncthreads();
+    }
+    // stage 2: thread (k2, c): forward DFT over n1 -> k = k2 + G2 k1; the
+    // pointwise step; inverse DFT over k1 (k = k2 + G2 k1 is the input index)
+    const int k2 = t / TW, cc = t % TW;
+    const bool ok = k2 < G2 && colok;
+    float2 b[G1];
+    if (ok) {
+      if (mode == COL_INV) {
+#pragma unroll
+        for (int k1 = 0; k1 < G1; ++k1)
+          b[k1] = cscale(ldcg(Yin + ((size_t)j * G + k2 + G2 * k1) * G + x), C.inv_G);
+      } else {
+#pragma unroll
+        for (int n1 = 0; n1 < G1; ++n1) b[n1] = sm[(k2 * G1 + n1) * TW + cc];
+        dft<G1, false>(b);
+#pragma unroll
+        for (int k1 = 0; k1 < G1; ++k1) {
+          const size_t kk = (size_t)(k2 + G2 * k1) * G + x;
+          if (mode == COL_TOEP) {
+            b[k1] = cscale(b[k1], __ldg(P + kk) * C.inv_G2);
+          } else if (mode == COL_RHS) {
+            const float2 yv = ldcg(Yin + (size_t)j * G * G + kk);
+            const float pk = __ldg(P + kk) * C.inv_G;
+            b[k1] = cscale(make_float2(fmaf(-pk, b[k1].x, yv.x), fmaf(-pk, b[k1].y, yv.y)), C.inv_G);
+          } else {  // COL_FWD
+            zout[(size_t)j * G * G + kk] = cscale(b[k1], C.inv_G);
+          }
+        }
+      }
+      if (mode != COL_FWD) {
+        dft<G1, true>(b);
+#pragma unroll
+        for (int m1 = 1; m1 < G1; ++m1) b[m1] = cmul(b[m1], twg<true>(C.tw, k2 * m1));
+      }
+    }
+    if (mode == COL_FWD) {
+      __syncthreads();
+      continue;
+    }
+    __syncthreads();
+    if (ok) {
+#pragma unroll
+      for (int m1 = 0; m1 < G1; ++m1) sm[(m1 * G2 + k2) * TW + cc] = b[m1];
+    }
+    __syncthreads();
+    {  // stage 3: thread (m1, c): inverse DFT over k2 -> y = m1 + G1 m2, keep y < N
+      const int m1 = t / TW;
+      if (m1 < G1 && colok) {
+        float2 d[G2];
+#pragma unroll
+        for (int a2 = 0; a2 < G2; ++a2) d[a2] = sm[(m1 * G2 + a2) * TW + (t % TW)];
+        dft<G2, true>(d);
+#pragma unroll
+        for (int m2 = 0; m2 < G2 / 2; ++m2) vio[((size_t)j * N + m1 + G1 * m2) * G + x] = d[m2];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------- D: row iFFT, channel products, W^-H along x
+template <class K>
+__device__ void phase_row_d(const Ctx& C, float2* sm, const float2* rho, const float2* win,
+                            float2* sout, float2* kbout) {
+  constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW, RS = K::RS;
+  const int N = C.N, Gc = C.Gc, J = C.J;
+  const int t = threadIdx.x;
+  const int groups = (N + TW - 1) / TW;
+  const int items = J * groups;
+  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+    const int j = it / groups;
+    const int y0 = (it - j * groups) * TW;
+    {  // stage 1: thread (row, n1): inverse DFT over n2
+      const int rr = t / G1, n1 = t % G1, y = y0 + rr;
+      if (rr < TW && y < N) {
+        float2 a[G2];
+        const float2* src = win + ((size_t)j * N + y) * G;
+#pragma unroll
+        for (int n2 = 0; n2 < G2; ++n2) a[n2] = ldcg(src + n1 + G1 * n2);
+        dft<G2, true>(a);
+#pragma unroll
+        for (int k2 = 0; k2 < G2; ++k2) {
+          float2 x = a[k2];
+          if (k2) x = cmul(x, twg<true>(C.tw, n1 * k2));
+          sm[rr * RS + k2 * (G1 + 1) + n1] = x;
+        }
+      }
+    }
+    __syncthreads();
+    // stage 2: thread (row, k2): inverse DFT over n1 -> t_j at x = k2 + G2 k1
+    const int rr = t / G2, k2 = t % G2, y = y0 + rr;
+    const bool ok = rr < TW && y < N;
+    float2 g[G1];
+    if (ok) {
+      float2 b[G1];
+#pragma unroll
+      for (int n1 = 0; n1 < G1; ++n1) b[n1] = sm[rr * RS + k2 * (G1 + 1) + n1];
+      dft<G1, true>(b);
+#pragma unroll
+      for (int k1 = 0; k1 < G1; ++k1) {
+        g[k1] = czero();
+        if (k1 < G1 / 2) {
+          const int x = k2 + G2 * k1;
+          const size_t ic = ((size_t)j * N + y) * N + x;
+          sout[ic] = cconjmul(ldcg(C.c + ic), b[k1]);
+          g[k1] = cconjmul(ldcg(rho + y * N + x), b[k1]);
+        }
+      }
+      dft<G1, false>(g);
+#pragma unroll
+      for (int kb = 1; kb < G1; ++kb) g[kb] = cmul(g[kb], twg<false>(C.tw, k2 * kb));
+    }
+    __syncthreads();
+    if (ok) {
+#pragma unroll
+      for (int kb = 0; kb < G1; ++kb) sm[rr * RS + kb * (G2 + 1) + k2] = g[kb];
+    }
+    __syncthreads();
+    {  // stage 3: thread (row, kb): forward DFT over k2 -> kb + G1 ka, crop to G_c
+      const int r3 = t / G1, kb = t % G1, y3 = y0 + r3;
+      if (r3 < TW && y3 < N) {
+        float2 d[G2];
+#pragma unroll
+        for (int a2 = 0; a2 < G2; ++a2) d[a2] = sm[r3 * RS + kb * (G2 + 1) + a2];
+        dft<G2, false>(d);
+        float2* dst = kbout + ((size_t)j * N + y3) * Gc;
+#pragma unroll
+        for (int ka = 0; ka < G2; ++ka) {
+          const int ix = coef_index(kb + G1 * ka, G, Gc);
+          if (ix >= 0) dst[ix] = d[ka];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ----------------- E: W^-H along y, D_W^-1, channel sum, Tikhonov, Re<p,q>
+// E_CG    : out = q = A p (+ alpha p), partial Re<p, q>      (p = pv)
+// E_RHS   : out = r = DF^H(...) - alpha (x_n - x_ref), partial |r|^2
+// E_DFH   : out = DF^H z
+// E_NORMAL: out = (DF^H P DF + alpha) dx                      (dx = pv)
+template <class K>
+__device__ void phase_col_e(const Ctx& C, float2* sm, double* sred, int mode, float alpha,
+                            const float2* kbin, const float2* sin, const float2* pv,
+                            float2* out, int slot) {
+  constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW;
+  const int N = C.N, Gc = C.Gc, J = C.J, NN = N * N;
+  const int t = threadIdx.x;
+  const int tiles = (Gc + TW - 1) / TW;
+  const int items = J * tiles;
+  double acc = 0.0;
+  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+    const int j = it / tiles;
+    const int fx = (it - j * tiles) * TW + (t % TW);
+    const bool colok = fx < Gc;
+    {  // stage 1: thread (n1, c): forward DFT over n2 (rows y < N)
+      const int n1 = t / TW;
+      if (n1 < G1) {
+        float2 a[G2];
+#pragma unroll
+        for (int n2 = 0; n2 < G2; ++n2)
+          a[n2] = (colok && n2 < G2 / 2) ? ldcg(kbin + ((size_t)j * N + n1 + G1 * n2) * Gc + fx)
+                                         : czero();
+        dft<G2, false>(a);
+#pragma unroll
+        for (int k2 = 0; k2 < G2; ++k2) {
+          float2 v = a[k2];
+          if (k2) v = cmul(v, twg<false>(C.tw, n1 * k2));
+          sm[(k2 * G1 + n1) * TW + (t % TW)] = v;
+        }
+      }
+    }
+    __syncthreads();
+    {  // stage 2: thread (k2, c): forward DFT over n1, crop rows to G_c
+      const int k2 = t / TW, cc = t % TW;
+      if (k2 < G2 && colok) {
+        float2 b[G1];
+#pragma unroll
+        for (int n1 = 0; n1 < G1; ++n1) b[n1] = sm[(k2 * G1 + n1) * TW + cc];
+        dft<G1, false>(b);
+#pragma unroll
+        for (int k1 = 0; k1 < G1; ++k1) {
+          const int iy = coef_index(k2 + G2 * k1, G, Gc);
+          if (iy < 0) continue;
+          const size_t e = (size_t)NN + ((size_t)j * Gc + iy) * Gc + fx;
+          const float2 val = cscale(b[k1], C.inv_G * __ldg(C.dinv + iy * Gc + fx));
+          if (mode == E_CG) {
+            const float2 p = ldcg(pv + e);
+            const float2 qv = cfma(p, alpha, val);
+            out[e] = qv;
+            acc += (double)p.x * qv.x + (double)p.y * qv.y;
+          } else if (mode == E_RHS) {
+            const float2 d = csub(ldcg(C.xn + e), ldcg(C.xref + e));
+            const float2 bv = cfma(d, -alpha, val);
+            out[e] = bv;
+            acc += (double)bv.x * bv.x + (double)bv.y * bv.y;
+          } else if (mode == E_DFH) {
+            out[e] = val;
+          } else {
+            out[e] = cfma(ldcg(pv + e), alpha, val);
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // rho part: channel sum of s_j = conj(c_j) t_j
+  for (int e = blockIdx.x * blockDim.x + t; e < NN; e += gridDim.x * blockDim.x) {
+    float2 sv = czero();
+    for (int j = 0; j < J; ++j) sv = cadd(sv, ldcg(sin + (size_t)j * NN + e));
+    if (mode == E_CG) {
+      const float2 p = ldcg(pv + e);
+      const float2 qv = cfma(p, alpha, sv);
+      out[e] = qv;
+      acc += (double)p.x * qv.x + (double)p.y * qv.y;
+    } else if (mode == E_RHS) {
+      const float2 d = csub(ldcg(C.xn + e), ldcg(C.xref + e));
+      const float2 bv = cfma(d, -alpha, sv);
+      out[e] = bv;
+      acc += (double)bv.x * bv.x + (double)bv.y * bv.y;
+    } else if (mode == E_DFH) {
+      out[e] = sv;
+    } else {
+      out[e] = cfma(ldcg(pv + e), alpha, sv);
+    }
+  }
+  if (mode == E_CG || mode == E_RHS) block_partial(C, acc, slot, sred);
+}
+
+// -------------------------------------------------- F: CG vector update
+// a = |r_k|^2 / Re<p, A p>; x += a p; r -= a q; partial |r_{k+1}|^2.
+// On the last iteration the Newton update x^_{n+1} = x^_n + x is applied.
+__device__ __forceinline__ void phase_upd(const Ctx& C, double* sred, int k, bool last) {
+  const double rr = slot_total(C, (k & 1) ? SLOT_RR1 : SLOT_RR0, sred);
+  const double pq = slot_total(C, SLOT_PQ, sred);
+  float a = 0.f;
+  if (rr > 0.0) {
+    if (pq > 0.0 && isfinite(pq)) {
+      a = (float)(rr / pq);
+    } else if (blockIdx.x == 0 && threadIdx.x == 0) {
+      raise_err(C, DEV_ENUMERIC);
+    }
+  }
+  double acc = 0.0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < C.nx; e += gridDim.x * blockDim.x) {
+    const float2 p = ldcg(C.p + e);
+    float2 xv = cscale(p, a);
+    if (k > 0) xv = cadd(xv, ldcg(C.xcg + e));
+    const float2 rv = cfma(ldcg(C.q + e), -a, ldcg(C.r + e));
+    C.r[e] = rv;
+    acc += (double)rv.x * rv.x + (double)rv.y * rv.y;
+    if (last) C.xn[e] = cadd(ldcg(C.xn + e), xv);
+    else C.xcg[e] = xv;
+  }
+  block_partial(C, acc, (k & 1) ? SLOT_RR0 : SLOT_RR1, sred);
+}
+
+// x^_0 = x_prev (or rho = 1, c^ = 0), x_ref = damping * x_prev
+__device__ __forceinline__ void phase_init(const Ctx& C, const float2* xprev, float damping) {
+  const int NN = C.N * C.N;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < C.nx; e += gridDim.x * blockDim.x) {
+    float2 v = xprev ? ldcg(xprev + e) : make_float2(e < NN ? 1.f : 0.f, 0.f);
+    C.xn[e] = v;
+    C.xref[e] = cscale(v, damping);
+  }
+}
+
+// outputs: x^ copy, rho, rho * sqrt(sum_j |c_j|^2)
+__device__ __forceinline__ void phase_final(const Ctx& C, float2* xout, float2* rho_out, float2* img_out) {
+  const int NN = C.N * C.N;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < C.nx; e += gridDim.x * blockDim.x) {
+    const float2 v = ldcg(C.xn + e);
+    if (xout) xout[e] = v;
+    if (e < NN) {
+      if (rho_out) rho_out[e] = v;
+      if (img_out) {
+        float ss = 0.f;
+        for (int j = 0; j < C.J; ++j) {
+          const float2 cv = ldcg(C.c + (size_t)j * NN + e);
+          ss = fmaf(cv.x, cv.x, fmaf(cv.y, cv.y, ss));
+        }
+        img_out[e] = cscale(v, sqrtf(ss));
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------- grid barrier
+// Sense-free generation barrier for the cooperative persistent kernel.
+// Every wait is bounded by spin_limit polls; on expiry the error word is set
+// and all CTAs leave at their next barrier.
+__device__ __forceinline__ bool grid_sync(const Ctx& C) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = C.bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    const unsigned prev = atomicAdd(C.bar, 1u);
+    if (prev == gridDim.x - 1) {
+      atomicExch(C.bar, 0u);
+      __threadfence();
+      atomicAdd(C.bar + 1, 1u);
+    } else {
+      long long it = 0;
+      while (*gen == g) {
+        if (*(volatile int*)C.err != 0) break;
+        if (++it > C.spin_limit) {
+          raise_err(C, DEV_ETIMEOUT);
+          break;
+        }
+        __nanosleep(20);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *(volatile int*)C.err == 0;
+}
+
+}  // namespace nlinv

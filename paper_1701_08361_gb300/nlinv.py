@@ -1,0 +1,226 @@
+"""Thin ctypes binding of the C ABI in include/nlinv.h.
+
+Every function here has the C entry point's name and only marshals
+arguments: torch tensors become device pointers, the current torch CUDA
+stream becomes the cudaStream_t, return codes become NlinvError.  All
+computation runs in libnlinv.so; if the library is missing this module
+raises on first use.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnlinv.so")
+
+NLINV_OK = 0
+NLINV_EINVAL = -1
+NLINV_ECUDA = -2
+NLINV_ENOMEM = -3
+NLINV_ETIMEOUT = -4
+NLINV_ENUMERIC = -5
+NLINV_EUNSUPPORTED = -6
+
+
+class NlinvError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        msg = f"{where}: {nlinv_strerror(code)} ({code})"
+        if code == NLINV_ECUDA:
+            msg += f" [{_lib().nlinv_last_cuda_error().decode()}]"
+        super().__init__(msg)
+
+
+class nlinv_params_t(ctypes.Structure):
+    _fields_ = [
+        ("N", ctypes.c_int), ("J", ctypes.c_int), ("Gc", ctypes.c_int),
+        ("newton_steps", ctypes.c_int), ("cg_iters", ctypes.c_int), ("n_turns", ctypes.c_int),
+        ("alpha0", ctypes.c_double), ("q", ctypes.c_double), ("damping", ctypes.c_double),
+        ("w_a", ctypes.c_double), ("w_l", ctypes.c_double),
+        ("spin_limit", ctypes.c_longlong), ("exec_mode", ctypes.c_int),
+    ]
+
+
+_L = None
+_VP = ctypes.c_void_p
+_I = ctypes.c_int
+
+_SIGS = {
+    "nlinv_default_params": (_I, [ctypes.POINTER(nlinv_params_t), _I, _I]),
+    "nlinv_plan": (_I, [ctypes.POINTER(_VP), ctypes.POINTER(nlinv_params_t), _VP, _VP]),
+    "nlinv_plan_destroy": (_I, [_VP]),
+    "nlinv_plan_sizes": (_I, [_VP, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_I),
+                              ctypes.POINTER(_I)]),
+    "nlinv_set_psf": (_I, [_VP, _I, _VP, _VP]),
+    "nlinv_psf": (_I, [_VP, _I, _I, _VP, _VP, _VP]),
+    "nlinv_grid": (_I, [_VP, _I, _VP, _VP, _VP, _VP]),
+    "nlinv_apply_DF": (_I, [_VP, _VP, _VP, _VP, _VP]),
+    "nlinv_apply_DFH": (_I, [_VP, _VP, _VP, _VP, _VP]),
+    "nlinv_apply_normal": (_I, [_VP, _VP, _VP, _I, ctypes.c_double, _VP, _VP]),
+    "nlinv_frame": (_I, [_VP, _VP, _I, _VP, _VP, _VP, _VP, _VP]),
+    "nlinv_wait_flag": (_I, [_VP, _VP, _I, ctypes.c_longlong, _VP]),
+    "nlinv_sync": (_I, [_VP, _VP]),
+    "nlinv_strerror": (ctypes.c_char_p, [_I]),
+    "nlinv_last_cuda_error": (ctypes.c_char_p, []),
+}
+
+
+def _lib():
+    global _L
+    if _L is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _L = lib
+    return _L
+
+
+def library():
+    """The loaded ctypes library (loads it on first call)."""
+    return _lib()
+
+
+def _check(rc: int, where: str):
+    if rc != NLINV_OK:
+        raise NlinvError(rc, where)
+
+
+def _stream(stream):
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _ptr(t, dtype=torch.complex64, numel=None, name="tensor"):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    return t.data_ptr()
+
+
+def nlinv_strerror(code: int) -> str:
+    return _lib().nlinv_strerror(code).decode()
+
+
+def nlinv_default_params(N: int, J: int) -> nlinv_params_t:
+    p = nlinv_params_t()
+    _check(_lib().nlinv_default_params(ctypes.byref(p), N, J), "nlinv_default_params")
+    return p
+
+
+class Plan:
+    """Owning handle of an nlinv_plan_t with the plan's sizes."""
+
+    def __init__(self, handle, params: nlinv_params_t):
+        self.handle = handle
+        self.params = params
+        nx, G, Gc = ctypes.c_longlong(), ctypes.c_int(), ctypes.c_int()
+        _check(_lib().nlinv_plan_sizes(handle, ctypes.byref(nx), ctypes.byref(G),
+                                       ctypes.byref(Gc)), "nlinv_plan_sizes")
+        self.nx, self.G, self.Gc = nx.value, G.value, Gc.value
+        self.N, self.J = params.N, params.J
+
+    def close(self):
+        if self.handle:
+            _lib().nlinv_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def nlinv_plan(params: nlinv_params_t, psf=None, stream=None) -> Plan:
+    h = _VP()
+    G = 2 * params.N
+    ptr = _ptr(psf, torch.float32, params.n_turns * G * G, "psf") if psf is not None else None
+    _check(_lib().nlinv_plan(ctypes.byref(h), ctypes.byref(params), ptr, _stream(stream)),
+           "nlinv_plan")
+    return Plan(h, params)
+
+
+def nlinv_plan_destroy(plan: Plan):
+    plan.close()
+
+
+def nlinv_set_psf(plan: Plan, turn: int, psf, stream=None):
+    _check(_lib().nlinv_set_psf(plan.handle, turn, _ptr(psf, torch.float32, plan.G * plan.G, "psf"),
+                                _stream(stream)), "nlinv_set_psf")
+
+
+def nlinv_psf(plan: Plan, turn: int, kxy, P_out=None, stream=None):
+    S = kxy.shape[0]
+    _check(_lib().nlinv_psf(plan.handle, turn, S, _ptr(kxy, torch.float64, 2 * S, "kxy"),
+                            _ptr(P_out, torch.float32, plan.G * plan.G, "P_out"),
+                            _stream(stream)), "nlinv_psf")
+
+
+def nlinv_grid(plan: Plan, kxy, y, Y_out, stream=None):
+    S = kxy.shape[0]
+    _check(_lib().nlinv_grid(plan.handle, S, _ptr(kxy, torch.float64, 2 * S, "kxy"),
+                             _ptr(y, numel=plan.J * S, name="y"),
+                             _ptr(Y_out, numel=plan.J * plan.G * plan.G, name="Y_out"),
+                             _stream(stream)), "nlinv_grid")
+
+
+def nlinv_apply_DF(plan: Plan, xhat, dx, z, stream=None):
+    _check(_lib().nlinv_apply_DF(plan.handle, _ptr(xhat, numel=plan.nx, name="xhat"),
+                                 _ptr(dx, numel=plan.nx, name="dx"),
+                                 _ptr(z, numel=plan.J * plan.G * plan.G, name="z"),
+                                 _stream(stream)), "nlinv_apply_DF")
+
+
+def nlinv_apply_DFH(plan: Plan, xhat, z, dx_out, stream=None):
+    _check(_lib().nlinv_apply_DFH(plan.handle, _ptr(xhat, numel=plan.nx, name="xhat"),
+                                  _ptr(z, numel=plan.J * plan.G * plan.G, name="z"),
+                                  _ptr(dx_out, numel=plan.nx, name="dx_out"),
+                                  _stream(stream)), "nlinv_apply_DFH")
+
+
+def nlinv_apply_normal(plan: Plan, xhat, dx, turn: int, alpha: float, out, stream=None):
+    _check(_lib().nlinv_apply_normal(plan.handle, _ptr(xhat, numel=plan.nx, name="xhat"),
+                                     _ptr(dx, numel=plan.nx, name="dx"), turn, float(alpha),
+                                     _ptr(out, numel=plan.nx, name="out"), _stream(stream)),
+           "nlinv_apply_normal")
+
+
+def nlinv_frame(plan: Plan, Y, turn: int, x_prev, x_out, rho_out=None, img_out=None, stream=None):
+    NN = plan.N * plan.N
+    _check(_lib().nlinv_frame(plan.handle, _ptr(Y, numel=plan.J * plan.G * plan.G, name="Y"), turn,
+                              _ptr(x_prev, numel=plan.nx, name="x_prev"),
+                              _ptr(x_out, numel=plan.nx, name="x_out"),
+                              _ptr(rho_out, numel=NN, name="rho_out"),
+                              _ptr(img_out, numel=NN, name="img_out"),
+                              _stream(stream)), "nlinv_frame")
+
+
+def nlinv_wait_flag(plan: Plan, flag, expected: int, spin_limit: int, stream=None):
+    _check(_lib().nlinv_wait_flag(plan.handle, _ptr(flag, torch.int32, 1, "flag"), expected,
+                                  spin_limit, _stream(stream)), "nlinv_wait_flag")
+
+
+def nlinv_sync(plan: Plan, stream=None) -> int:
+    """Synchronise the stream; return the plan's latched device error code
+    (0 if none) without raising, so callers can test for it."""
+    return _lib().nlinv_sync(plan.handle, _stream(stream))
