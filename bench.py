@@ -1,0 +1,479 @@
+"""Benchmark of the GB300 NLINV hot path on the real-time radial stream.
+
+Workload (one step = F consecutive frames of one stream, carried on from the
+previous step): image side N = 160 on the G = 320 grid, J = 10 channels, 13
+radial spokes per frame rotating over U = 5 turns, 7 Newton steps x 10 CG,
+regularisation to the previous frame, a moving ellipse phantom with fixed
+coil maps and sigma = 1e-3 noise; synthetic data, gridded and PSF'd on the
+device before timing.  Frames of one stream depend on each other, so the
+frame rate is 1 / per-frame latency.
+
+Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth as S  # noqa: E402
+
+CFG = dict(N=160, J=10, K=13, U=5, M=7, CG=10, sigma=1e-3, seed=1702)
+METRIC = "NLINV frames/s (320^2 grid, 10 ch, radial 13 spokes, 7x10)"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def flops_per_frame(N, G, Gc, J, M, K):
+    """Algorithmic FP32 flops of one frame: (K + 1) operator applications per
+    Newton step; per channel and application (4N + 2G + 2Gc) length-G
+    transforms at 5 G log2 G flops plus the pointwise work."""
+    per_ch = (4 * N + 2 * G + 2 * Gc) * 5.0 * G * math.log2(G) + 28 * N * N + 2 * G * G + 4 * Gc * Gc
+    return M * (K + 1) * J * per_ch
+
+
+def bytes_per_frame(N, G, Gc, J, M, K):
+    """Algorithmic HBM bytes of one frame with FFT intermediates on chip:
+    per CG iteration the CG vectors (10 n_x), the coil maps (J N^2), rho
+    (N^2) and the PSF (4 G^2 bytes)."""
+    nx = N * N + J * Gc * Gc
+    per_it = 8 * (10 * nx + J * N * N + N * N) + 4 * G * G
+    return M * (K + 1) * per_it
+
+
+def make_raw_frames(nframes, seed):
+    N, J, K, U = CFG["N"], CFG["J"], CFG["K"], CFG["U"]
+    coils = S.coil_maps(N, J, seed)
+    out = []
+    for n in range(nframes):
+        kx, ky, y, _, _ = S.radial_frame(N, J, K, U, n, seed, CFG["sigma"], coils=coils)
+        out.append((kx, ky, y))
+    return out
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.seek(0)
+        rows = [l.strip().split(", ") for l in self.f if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_init(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier_max(x, world):
+    """Barrier, then the maximum of x over ranks."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ----------------------------------------------------------------- ours
+def run_ours(args):
+    import torch
+    from paper_1701_08361_gb300 import nlinv as L
+
+    world, rank, local = dist_init(args)
+    N, J, U = CFG["N"], CFG["J"], CFG["U"]
+    G = 2 * N
+    F = args.frames_per_step
+    seed = CFG["seed"] + 1000 * rank          # independent replica stream per rank
+    raw = make_raw_frames(F, seed)
+    p = L.nlinv_default_params(N, J)
+    p.n_turns = U
+    p.newton_steps, p.cg_iters = CFG["M"], CFG["CG"]
+    p.exec_mode = args.exec_mode
+    plan = L.nlinv_plan(p)
+    Gc = plan.Gc
+    dev = torch.device("cuda")
+    Yall = torch.empty((F, J * G * G), dtype=torch.complex64, device=dev)
+    for n, (kx, ky, y) in enumerate(raw):
+        kxy = torch.tensor(np.stack([kx, ky], 1), dtype=torch.float64, device=dev)
+        if n < U:
+            L.nlinv_psf(plan, n % U, kxy)
+        L.nlinv_grid(plan, kxy, torch.tensor(y, dtype=torch.complex64, device=dev), Yall[n])
+    assert L.nlinv_sync(plan) == 0
+    x = torch.empty(plan.nx, dtype=torch.complex64, device=dev)
+    imgs = torch.empty((F, N * N), dtype=torch.complex64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    st = torch.cuda.current_stream()
+    state = {"first": True, "frame": 0}
+
+    def step(evs=None, Ysrc=None):
+        for n in range(F):
+            if evs is not None:
+                evs[n][0].record(st)
+            L.nlinv_frame(plan, Ysrc[n] if Ysrc is not None else Yall[n], state["frame"] % U,
+                          None if state["first"] else x, x, None, imgs[n])
+            if evs is not None:
+                evs[n][1].record(st)
+            state["first"] = False
+            state["frame"] += 1
+
+    for _ in range(args.warmup):
+        step()
+    rc = L.nlinv_sync(plan)
+    if rc != 0:
+        raise RuntimeError(L.nlinv_strerror(rc))
+
+    clocks = Clocks(local)
+    K = args.steps
+    ev_frames = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(F)]
+                 for _ in range(K)]
+    ev_step = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K)]
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    for s in range(K):
+        flush.fill_(float(s))
+        ev_step[s][0].record(st)
+        step(ev_frames[s])
+        ev_step[s][1].record(st)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    rc = L.nlinv_sync(plan)
+    if rc != 0:
+        raise RuntimeError(L.nlinv_strerror(rc))
+    t_steps = [ev_step[s][0].elapsed_time(ev_step[s][1]) for s in range(K)]
+    t_frames = [ev_frames[s][n][0].elapsed_time(ev_frames[s][n][1]) for s in range(K) for n in range(F)]
+    total_ms = barrier_max(sum(t_steps), world)
+    frames = K * F * world
+    value = frames / (total_ms / 1e3)
+    lat = sorted(t_frames)
+
+    # end to end: pinned host Y in, images out, copies inside the timed region
+    Yh = Yall.cpu().pin_memory()
+    imgs_h = torch.empty(imgs.shape, dtype=imgs.dtype).pin_memory()
+    Ydev = torch.empty_like(Yall)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for s in range(K):
+        Ydev.copy_(Yh, non_blocking=True)
+        step(None, Ydev)
+        imgs_h.copy_(imgs, non_blocking=True)
+    e1.record(st)
+    torch.cuda.synchronize()
+    e2e_ms = barrier_max(e0.elapsed_time(e1), world)
+    rc = L.nlinv_sync(plan)
+    if rc != 0:
+        raise RuntimeError(L.nlinv_strerror(rc))
+
+    pk, pk_src = peaks()
+    fl = flops_per_frame(N, G, Gc, J, CFG["M"], CFG["CG"])
+    by = bytes_per_frame(N, G, Gc, J, CFG["M"], CFG["CG"])
+    mean_frame_s = statistics.mean(t_frames) / 1e3
+    fp32_peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12   # TFLOP/s
+    achieved = fl / mean_frame_s / 1e12
+    hbm = by / mean_frame_s / 1e9
+
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": "frames/s", "n_gpus": world,
+        "steps": K, "warmup": args.warmup, "ms_per_step": round(total_ms / K, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
+        "data": "synthetic",
+        "config": {"workload": "real-time radial stream: N=160, G=320, J=10, 13 spokes x 5 turns, "
+                               "7 Newton x 10 CG, moving phantom, sigma=1e-3",
+                   "frames_per_step": F, "exec_mode": ["persistent", "per-phase"][args.exec_mode],
+                   "l2": "inputs larger than L2 (%.0f MB of gridded data per step) and L2 flushed "
+                         "between steps" % (Yall.numel() * 8 / 1e6),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "latency_ms": {"p50": round(statistics.median(lat), 4), "min": round(lat[0], 4)},
+        "roofline": {"bound": "alu", "achieved": round(achieved, 3),
+                     "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
+                     "frac": round(achieved / fp32_peak, 4), "traffic": None,
+                     "kernel": "k_frame (persistent, one launch per frame)",
+                     "peak_source": "FP32: 152 SMs x 128 lanes x 2 flop x sm_max_mhz (%s)" % pk_src},
+        "hbm": {"achieved_gbs": round(hbm, 1), "peak_gbs": pk["hbm_gbs"],
+                "frac": round(hbm / pk["hbm_gbs"], 4), "peak_source": pk_src},
+        "e2e": {"value": round(frames / (e2e_ms / 1e3), 2), "unit": "frames/s",
+                "h2d_bytes_per_step": int(Yall.numel() * 8),
+                "d2h_bytes_per_step": int(imgs.numel() * 8)},
+        "gpu_launches": K * F * (1 if args.exec_mode == 0 else -1),
+        "clocks": clk,
+    }
+    if args.exec_mode == 1:
+        M, C = CFG["M"], CFG["CG"]
+        out["gpu_launches"] = K * F * (1 + M * (5 + 6 * C) + 2 + 1)
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.cpu_frames)
+    if rank == 0 and args.plain_loop:
+        out["plain_gpu_loop"] = plain_gpu_loop(raw, args)
+    plan.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------- CPU oracle baseline
+def oracle_frames(nframes, seed):
+    import oracle as O
+    N, J, U = CFG["N"], CFG["J"], CFG["U"]
+    G = 2 * N
+    raw = make_raw_frames(nframes, seed)
+    frames = [(O.grid_data(kx, ky, y, N, G), O.psf_kernel(kx, ky, N, G).real) for kx, ky, y in raw]
+    return frames
+
+
+def cpu_baseline(nframes):
+    """The FP64 oracle as it stands, timed on the host cores over a bounded
+    sample of the stream (the first `nframes` frames)."""
+    import oracle as O
+    N, J = CFG["N"], CFG["J"]
+    frames = oracle_frames(nframes, CFG["seed"])
+    g = O.Geometry(N=N, J=J)
+    prm = O.Params(newton_steps=CFG["M"], cg_iters=CFG["CG"])
+    t0 = time.perf_counter()
+    O.nlinv_stream(frames, g, prm)
+    dt = time.perf_counter() - t0
+    return {"value": round(nframes / dt, 4), "unit": "frames/s", "cores": O.workers(),
+            "kind": "oracle",
+            "sample": f"first {nframes} frames of the stream (FP64 NumPy/SciPy, "
+                      f"scipy.fft workers={O.workers()})"}
+
+
+# -------------------------------------- plain per-frame GPU loop (cuFFT)
+def plain_gpu_loop(raw, args):
+    """The same algorithm as plain eager torch ops (torch.fft = cuFFT, FP32,
+    no fusion), one frame at a time: the comparator the metric names."""
+    import torch
+    N, J, U = CFG["N"], CFG["J"], CFG["U"]
+    G = 2 * N
+    from paper_1701_08361_gb300 import nlinv as L
+    p = L.nlinv_default_params(N, J)
+    p.n_turns = U
+    plan = L.nlinv_plan(p)
+    Gc = plan.Gc
+    dev = torch.device("cuda")
+    Ys, Ps = [], []
+    for n, (kx, ky, y) in enumerate(raw):
+        kxy = torch.tensor(np.stack([kx, ky], 1), dtype=torch.float64, device=dev)
+        Yd = torch.empty(J * G * G, dtype=torch.complex64, device=dev)
+        L.nlinv_grid(plan, kxy, torch.tensor(y, dtype=torch.complex64, device=dev), Yd)
+        Ys.append(Yd.view(J, G, G))
+        if n < U:
+            Pd = torch.empty(G * G, dtype=torch.float32, device=dev)
+            L.nlinv_psf(plan, n, kxy, Pd)
+            Ps.append(Pd.view(G, G))
+    L.nlinv_sync(plan)
+    plan.close()
+    i = torch.arange(Gc, device=dev)
+    f = torch.where(i < (Gc + 1) // 2, i, i - Gc)
+    idx = f % G
+    k2 = (2.0 * f / G).double()
+    D = ((1 + 220.0 * (k2[:, None] ** 2 + k2[None, :] ** 2)) ** -16).float()
+
+    def Winv(ch):
+        z = torch.zeros((J, G, G), dtype=torch.complex64, device=dev)
+        z[:, idx[:, None], idx[None, :]] = D * ch
+        return torch.fft.ifft2(z, norm="ortho")[:, :N, :N]
+
+    def WinvH(v):
+        z = torch.zeros((J, G, G), dtype=torch.complex64, device=dev)
+        z[:, :N, :N] = v
+        return D * torch.fft.fft2(z, norm="ortho")[:, idx[:, None], idx[None, :]]
+
+    def pad(v):
+        z = torch.zeros((J, G, G), dtype=torch.complex64, device=dev)
+        z[:, :N, :N] = v
+        return z
+
+    def frame(Y, P, rho0, ch0, rhor, chr_):
+        rho, ch = rho0.clone(), ch0.clone()
+        for n in range(CFG["M"]):
+            al = 0.5 ** n
+            c = Winv(ch)
+            Fx = torch.fft.fft2(pad(rho * c), norm="ortho")
+            t = torch.fft.ifft2(Y - P * Fx, norm="ortho")[:, :N, :N]
+            br = (c.conj() * t).sum(0) - al * (rho - rhor)
+            bc = WinvH(rho.conj() * t) - al * (ch - chr_)
+            xr, xc = torch.zeros_like(br), torch.zeros_like(bc)
+            rr_, rc_ = br.clone(), bc.clone()
+            pr, pc = rr_.clone(), rc_.clone()
+            rr = (rr_.abs() ** 2).sum().double() + (rc_.abs() ** 2).sum().double()
+            for _ in range(CFG["CG"]):
+                u = c * pr + rho * Winv(pc)
+                tt = torch.fft.ifft2(P * torch.fft.fft2(pad(u), norm="ortho"), norm="ortho")[:, :N, :N]
+                qr = (c.conj() * tt).sum(0) + al * pr
+                qc = WinvH(rho.conj() * tt) + al * pc
+                pq = (pr.conj() * qr).real.sum().double() + (pc.conj() * qc).real.sum().double()
+                a = (rr / pq).float()
+                xr, xc = xr + a * pr, xc + a * pc
+                rr_, rc_ = rr_ - a * qr, rc_ - a * qc
+                rn = (rr_.abs() ** 2).sum().double() + (rc_.abs() ** 2).sum().double()
+                b = (rn / rr).float()
+                pr, pc = rr_ + b * pr, rc_ + b * pc
+                rr = rn
+            rho, ch = rho + xr, ch + xc
+        return rho, ch
+
+    rho = torch.ones((N, N), dtype=torch.complex64, device=dev)
+    ch = torch.zeros((J, Gc, Gc), dtype=torch.complex64, device=dev)
+    st = torch.cuda.current_stream()
+    for n in range(min(3, len(Ys))):
+        rho, ch = frame(Ys[n], Ps[n % U], rho, ch, rho, ch)
+    torch.cuda.synchronize()
+    nf = min(len(Ys), args.plain_frames)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for n in range(nf):
+        rho, ch = frame(Ys[n], Ps[n % U], rho, ch, rho, ch)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    return {"value": round(nf / (ms / 1e3), 2), "unit": "frames/s",
+            "kind": "plain torch.fft/cuFFT eager loop, FP32, one frame at a time",
+            "frames": nf}
+
+
+# ------------------------------------------------------- reference arm
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    N, J = CFG["N"], CFG["J"]
+    g = O.Geometry(N=N, J=J)
+    prm = O.Params(newton_steps=CFG["M"], cg_iters=CFG["CG"])
+    nf = args.warmup + args.steps
+    frames = oracle_frames(nf, CFG["seed"])
+    init = O.XVec.initial(g)
+    x = init
+    times = []
+    for s in range(nf):
+        Y, P = frames[s]
+        t0 = time.perf_counter()
+        x = O.nlinv_frame(Y, P, x, x, g, prm)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = len(times) / tot
+    out = {
+        "metric": METRIC, "value": round(value, 4), "unit": "frames/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * tot / len(times), 2),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+        "data": "synthetic", "impl": "reference",
+        "config": {"workload": "real-time radial stream: N=160, G=320, J=10, 13 spokes x 5 turns, "
+                               "7 Newton x 10 CG, moving phantom, sigma=1e-3",
+                   "frames_per_step": 1},
+        "cpu_baseline": {"value": round(value, 4), "unit": "frames/s", "cores": O.workers(),
+                         "kind": "oracle",
+                         "sample": "one frame of the stream per step (FP64 NumPy/SciPy oracle)"},
+        "e2e": {"value": round(value, 4), "unit": "frames/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--frames-per-step", type=int, default=25)
+    ap.add_argument("--exec-mode", type=int, default=0, choices=[0, 1])
+    ap.add_argument("--cpu-frames", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--plain-loop", type=int, default=1)
+    ap.add_argument("--plain-frames", type=int, default=10)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

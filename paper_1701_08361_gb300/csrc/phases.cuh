@@ -71,6 +71,11 @@ template <int G1_, int G2_> struct Cfg {
 
 __device__ __forceinline__ float2 ldcg(const float2* p) { return __ldcg(p); }
 
+// y + s x with the CG step scalar s kept in FP64 and one rounding to FP32
+__device__ __forceinline__ float2 axpy64(float2 x, double s, float2 y) {
+  return make_float2((float)fma(s, (double)x.x, (double)y.x), (float)fma(s, (double)x.y, (double)y.y));
+}
+
 // index of grid position pos in the G_c coil band, -1 outside (Gc even)
 __device__ __forceinline__ int coef_index(int pos, int G, int Gc) {
   const int h = Gc >> 1;
@@ -130,11 +135,11 @@ __device__ void phase_coil_y(const Ctx& C, float2* sm, const float2* src, bool u
   constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW;
   const int N = C.N, Gc = C.Gc, J = C.J, NN = N * N;
   const int t = threadIdx.x;
-  float beta = 0.f;
+  double beta = 0.0;
   if (upd && k > 0) {
     const double rr1 = slot_total(C, (k & 1) ? SLOT_RR1 : SLOT_RR0, sred);
     const double rr0 = slot_total(C, (k & 1) ? SLOT_RR0 : SLOT_RR1, sred);
-    beta = (rr0 > 0.0) ? (float)(rr1 / rr0) : 0.f;
+    beta = (rr0 > 0.0) ? rr1 / rr0 : 0.0;
   }
   const float2* r_c = C.r + NN;
   float2* p_c = C.p + NN;
@@ -156,7 +161,7 @@ __device__ void phase_coil_y(const Ctx& C, float2* sm, const float2* src, bool u
             const size_t e = ((size_t)j * Gc + iy) * Gc + fx;
             if (upd) {
               const float2 rv = ldcg(r_c + e);
-              val = (k == 0) ? rv : cfma(ldcg(p_c + e), beta, rv);
+              val = (k == 0) ? rv : axpy64(ldcg(p_c + e), beta, rv);
               p_c[e] = val;
             } else {
               val = ldcg(src + e);
@@ -194,7 +199,7 @@ __device__ void phase_coil_y(const Ctx& C, float2* sm, const float2* src, bool u
   if (upd) {  // rho part of the direction update
     for (int e = blockIdx.x * blockDim.x + t; e < NN; e += gridDim.x * blockDim.x) {
       const float2 rv = ldcg(C.r + e);
-      C.p[e] = (k == 0) ? rv : cfma(ldcg(C.p + e), beta, rv);
+      C.p[e] = (k == 0) ? rv : axpy64(ldcg(C.p + e), beta, rv);
     }
   }
 }
@@ -562,15 +567,15 @@ __device__ void phase_col_e(const Ctx& C, float2* sm, double* sred, int mode, fl
 }
 
 // -------------------------------------------------- F: CG vector update
-// a = |r_k|^2 / Re<p, A p>; x += a p; r -= a q; partial |r_{k+1}|^2.
+// a = |r_k|^2 / Re<p, A p> (FP64); x += a p; r -= a q; partial |r_{k+1}|^2.
 // On the last iteration the Newton update x^_{n+1} = x^_n + x is applied.
 __device__ __forceinline__ void phase_upd(const Ctx& C, double* sred, int k, bool last) {
   const double rr = slot_total(C, (k & 1) ? SLOT_RR1 : SLOT_RR0, sred);
   const double pq = slot_total(C, SLOT_PQ, sred);
-  float a = 0.f;
+  double a = 0.0;
   if (rr > 0.0) {
     if (pq > 0.0 && isfinite(pq)) {
-      a = (float)(rr / pq);
+      a = rr / pq;
     } else if (blockIdx.x == 0 && threadIdx.x == 0) {
       raise_err(C, DEV_ENUMERIC);
     }
@@ -578,9 +583,8 @@ __device__ __forceinline__ void phase_upd(const Ctx& C, double* sred, int k, boo
   double acc = 0.0;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < C.nx; e += gridDim.x * blockDim.x) {
     const float2 p = ldcg(C.p + e);
-    float2 xv = cscale(p, a);
-    if (k > 0) xv = cadd(xv, ldcg(C.xcg + e));
-    const float2 rv = cfma(ldcg(C.q + e), -a, ldcg(C.r + e));
+    const float2 xv = axpy64(p, a, k > 0 ? ldcg(C.xcg + e) : czero());
+    const float2 rv = axpy64(ldcg(C.q + e), -a, ldcg(C.r + e));
     C.r[e] = rv;
     acc += (double)rv.x * rv.x + (double)rv.y * rv.y;
     if (last) C.xn[e] = cadd(ldcg(C.xn + e), xv);

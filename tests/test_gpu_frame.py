@@ -50,11 +50,11 @@ def test_cartesian_frame_C1(exec_mode):
 
 
 def test_radial_stream_with_device_psf_and_gridding():
-    """Radial frames (K=9 spokes, U=5 turns) whose PSFs and gridded data are
+    """Radial frames (K=13 spokes, U=5 turns) whose PSFs and gridded data are
     computed by the library from the trajectory and raw samples; 3 frames
     chained with damping 0.9."""
     from paper_1701_08361_gb300 import nlinv as L
-    N, J, K, U = 32, 4, 9, 5
+    N, J, K, U = 64, 4, 13, 5
     g = O.Geometry(N=N, J=J)
     prm = O.Params(damping=0.9)
     plan = make_plan(N, J, turns=U, damping=0.9)
