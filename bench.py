@@ -43,6 +43,31 @@ def peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def source_hash() -> str:
+    import hashlib
+    import glob
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1701_08361_gb300", "csrc", "*"))):
+        h.update(os.path.basename(f).encode())
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(name="k_frame_c2_stream.md"):
+    """DRAM read+write bytes per launch from the committed ncu summary, or
+    None when the kernel sources changed since that capture."""
+    p = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(p):
+        return None
+    txt = open(p).read()
+    import re
+    m = re.search(r"kernel-source-sha256-16:\s*([0-9a-f]+)", txt)
+    t = re.search(r"traffic \(read \+ write\) per launch[^|]*\|\s*([0-9.]+) MB", txt)
+    if not m or not t or m.group(1) != source_hash():
+        return None
+    return float(t.group(1)) * 1e6
+
+
 def flops_per_frame(N, G, Gc, J, M, K):
     """Algorithmic FP32 flops of one frame: (K + 1) operator applications per
     Newton step; per channel and application (4N + 2G + 2Gc) length-G
@@ -266,7 +291,7 @@ def run_ours(args):
         "latency_ms": {"p50": round(statistics.median(lat), 4), "min": round(lat[0], 4)},
         "roofline": {"bound": "alu", "achieved": round(achieved, 3),
                      "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
-                     "frac": round(achieved / fp32_peak, 4), "traffic": None,
+                     "frac": round(achieved / fp32_peak, 4), "traffic": profiled_traffic(),
                      "kernel": "k_frame (persistent, one launch per frame)",
                      "peak_source": "FP32: 152 SMs x 128 lanes x 2 flop x sm_max_mhz (%s)" % pk_src},
         "hbm": {"achieved_gbs": round(hbm, 1), "peak_gbs": pk["hbm_gbs"],
