@@ -125,6 +125,32 @@ int nlinv_apply_DFH(nlinv_plan_t plan, const void* xhat, const void* z, void* dx
 int nlinv_apply_normal(nlinv_plan_t plan, const void* xhat, const void* dx, int turn,
                        double alpha, void* out, nlinv_stream_t stream);
 
+/* Allocation-free variant of nlinv_apply_normal (the paper has no
+ * counterpart: this is a deployment convenience).  It is for callers that
+ * cannot call cudaMalloc -- a running real-time reconstruction loop that
+ * must not allocate or implicitly synchronise the device, or a host
+ * framework that owns all device memory through its own pools.  It needs
+ * no plan:
+ *   out = (DF^H P DF + alpha I) dx  at x^_n = xhat,
+ * with G = 2N, Gc (0 -> G/4, even), D_W^-1 constants w_a, w_l, and
+ * psf: device float [G][G].  xhat, dx, out: device complex64 [n_x],
+ * n_x = N*N + J*Gc*Gc; out must not alias xhat or dx.
+ * Every intermediate lives in one 16 MiB __device__ array inside
+ * libnlinv.so, which every GPU that loads the library holds until the
+ * process exits; a problem needing more than that (about 40 J N^2 bytes,
+ * e.g. N = 160 with J <= 16, N = 256 with J <= 6) returns NLINV_EINVAL
+ * before anything is enqueued.  The call allocates nothing: no cudaMalloc,
+ * no cudaFree, no allocating library routine.  The first call on a device
+ * does a one-time set-up (looks up the array's device address and uploads
+ * a small constant table); make that first call before any stream capture.
+ * All calls share the one array, so calls that overlap on the GPU (other
+ * streams, other threads) race and must be serialised by the caller; each
+ * call writes every intermediate before reading it, so nothing has to be
+ * cleared between calls. */
+int nlinv_apply_normal_static(int N, int J, int Gc, double w_a, double w_l,
+                              const void* xhat, const void* dx, const float* psf,
+                              double alpha, void* out, nlinv_stream_t stream);
+
 /* One NLINV frame (Eqs. 2-3): M Newton steps from x^_0 = x_prev, each
  *   (DF^H P DF + alpha_n I) delta = DF^H (Y - P F^(x^_n)) - alpha_n (x^_n - x_ref)
  * solved by cg_iters CG iterations from zero, x^_{n+1} = x^_n + delta,

@@ -783,3 +783,138 @@ int nlinv_wait_flag(nlinv_plan_t pl, const int* flag, int expected, long long sp
 }
 
 }  // extern "C"
+
+// ======================================================================
+// Allocation-free normal operator.
+//
+// Some callers cannot call cudaMalloc: a reconstruction loop that must not
+// allocate (or implicitly synchronise the device) once it is running, or a
+// host framework that hands out all device memory from its own pools.  For
+// them nlinv_apply_normal_static runs the same phase kernels as
+// nlinv_apply_normal with every intermediate in one file-scope __device__
+// array that is part of the loaded module, so no call allocates.
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(16) << 20;   // 16 MiB
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+std::mutex g_static_mu;
+void* g_static_ptr[64] = {};
+
+// twiddles w_G^k and the D_W^-1 table, computed on the device in FP64
+__global__ void k_static_tables(int G, int Gc, double w_a, double w_l, float2* tw, float* dinv) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < G) {
+    double sn, cs;
+    sincospi(-2.0 * (double)i / G, &sn, &cs);
+    tw[i] = make_float2((float)cs, (float)sn);
+  }
+  if (i < Gc * Gc) {
+    const int iy = i / Gc, ix = i - iy * Gc;
+    const int fy = iy < (Gc + 1) / 2 ? iy : iy - Gc;
+    const int fx = ix < (Gc + 1) / 2 ? ix : ix - Gc;
+    const double ky = 2.0 * fy / G, kx = 2.0 * fx / G;
+    dinv[i] = (float)pow(1.0 + w_a * (kx * kx + ky * ky), -w_l / 2.0);
+  }
+}
+
+// set-up once per device (with that device current): the device address of
+// the scratch array and the constant twiddle table
+int static_scratch(void** out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return NLINV_EINVAL;
+  RC(ensure_constants(dev));
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    CK(cudaGetSymbolAddress(&p, g_static_scratch));
+    g_static_ptr[dev] = p;
+  }
+  *out = g_static_ptr[dev];
+  return NLINV_OK;
+}
+
+}  // namespace
+
+extern "C" int nlinv_apply_normal_static(int N, int J, int Gc, double w_a, double w_l, const void* xhat,
+                                         const void* dx, const float* psf, double alpha, void* out,
+                                         nlinv_stream_t stream) {
+  const int G = 2 * N;
+  if (N <= 0 || J <= 0 || J > 4096) return NLINV_EINVAL;
+  if (!supported_grid(G)) return NLINV_EUNSUPPORTED;
+  if (Gc == 0) Gc = G / 4;
+  if (Gc < 2 || Gc > G || (Gc & 1)) return NLINV_EINVAL;
+  if (!(alpha >= 0.0) || !(w_a >= 0.0) || !(w_l >= 0.0)) return NLINV_EINVAL;
+  if (!xhat || !dx || !psf || !out || !aligned8(xhat) || !aligned8(dx) || !aligned8(out) ||
+      ((uintptr_t)psf & 3u))
+    return NLINV_EINVAL;
+  if (out == xhat || out == dx) return NLINV_EINVAL;
+  // scratch layout: tw, dinv, c, h, v, s, kb, partials, counters
+  const size_t f2 = sizeof(float2);
+  size_t off[12];
+  size_t tot = 0;
+  int nb = 0;
+  auto take = [&](size_t bytes) {
+    off[nb++] = tot;
+    tot += align_up(bytes);
+  };
+  take(G * f2);
+  take((size_t)Gc * Gc * sizeof(float));
+  take((size_t)J * N * N * f2);
+  take((size_t)J * N * Gc * f2);
+  take((size_t)J * N * G * f2);
+  take((size_t)J * N * N * f2);
+  take((size_t)J * N * Gc * f2);
+  take((size_t)NSLOT * kMaxPart * sizeof(double));
+  take(NSLOT * sizeof(int) + sizeof(int) + 2 * sizeof(unsigned));
+  if (tot > kStaticScratchBytes) return NLINV_EINVAL;
+  void* base_v = nullptr;
+  RC(static_scratch(&base_v));
+  char* base = (char*)base_v;
+  cudaStream_t st = (cudaStream_t)stream;
+
+  nlinv_plan_s tmp;
+  Ctx& C = tmp.C;
+  std::memset(&C, 0, sizeof(C));
+  C.N = N;
+  C.G = G;
+  C.Gc = Gc;
+  C.J = J;
+  C.nx = N * N + J * Gc * Gc;
+  C.U = 1;
+  C.inv_G = (float)(1.0 / G);
+  C.inv_G2 = (float)(1.0 / ((double)G * G));
+  float2* tw = (float2*)(base + off[0]);
+  float* dinv = (float*)(base + off[1]);
+  C.tw = tw;
+  C.dinv = dinv;
+  C.psf = psf;
+  C.c = (float2*)(base + off[2]);
+  C.h = (float2*)(base + off[3]);
+  C.v = (float2*)(base + off[4]);
+  C.s = (float2*)(base + off[5]);
+  C.kb = (float2*)(base + off[6]);
+  C.part = (double*)(base + off[7]);
+  C.pcount = (int*)(base + off[8]);
+  C.err = C.pcount + NSLOT;
+  C.bar = (unsigned*)(C.err + 1);
+  C.spin_limit = 1LL << 22;
+  const int nt = (G > Gc * Gc ? G : Gc * Gc);
+  k_static_tables<<<(nt + 255) / 256, 256, 0, st>>>(G, Gc, w_a, w_l, tw, dinv);
+  CKL("k_static_tables");
+  const float2* xh = (const float2*)xhat;
+  const float2* d = (const float2*)dx;
+  const size_t NN = (size_t)N * N;
+  return dispatch(G, [&](auto k) -> int {
+    using K = decltype(k);
+    RC(set_smem_attrs<K>());
+    Launch<K> L{&tmp, st};
+    RC(L.coils(xh));
+    RC(L.coil_y(d + NN, 0, 0, C.h));
+    RC(L.row_b(ROW_LIN, C.h, xh, d, nullptr, C.v));
+    RC(L.col_c(COL_TOEP, psf, nullptr, nullptr, C.v));
+    RC(L.row_d(xh, C.v, C.s, C.kb));
+    return L.col_e(E_NORMAL, (float)alpha, C.kb, C.s, d, (float2*)out, SLOT_PQ);
+  });
+}

@@ -61,6 +61,8 @@ _SIGS = {
     "nlinv_apply_DFH": (_I, [_VP, _VP, _VP, _VP, _VP]),
     "nlinv_apply_normal": (_I, [_VP, _VP, _VP, _I, ctypes.c_double, _VP, _VP]),
     "nlinv_frame": (_I, [_VP, _VP, _I, _VP, _VP, _VP, _VP, _VP]),
+    "nlinv_apply_normal_static": (_I, [_I, _I, _I, ctypes.c_double, ctypes.c_double, _VP, _VP, _VP,
+                                       ctypes.c_double, _VP, _VP]),
     "nlinv_wait_flag": (_I, [_VP, _VP, _I, ctypes.c_longlong, _VP]),
     "nlinv_sync": (_I, [_VP, _VP]),
     "nlinv_strerror": (ctypes.c_char_p, [_I]),
@@ -203,6 +205,23 @@ def nlinv_apply_normal(plan: Plan, xhat, dx, turn: int, alpha: float, out, strea
                                      _ptr(dx, numel=plan.nx, name="dx"), turn, float(alpha),
                                      _ptr(out, numel=plan.nx, name="out"), _stream(stream)),
            "nlinv_apply_normal")
+
+
+def nlinv_apply_normal_static(N: int, J: int, Gc: int, w_a: float, w_l: float, xhat, dx, psf,
+                              alpha: float, out, stream=None):
+    """Plan-free normal operator for callers that cannot allocate device
+    memory: all of its intermediates live in the library's fixed 16 MiB
+    device array (see include/nlinv.h for the size limit and the rule that
+    overlapping calls race)."""
+    G = 2 * N
+    gc = Gc if Gc else G // 4
+    nx = N * N + J * gc * gc
+    _check(_lib().nlinv_apply_normal_static(N, J, Gc, float(w_a), float(w_l),
+                                            _ptr(xhat, numel=nx, name="xhat"),
+                                            _ptr(dx, numel=nx, name="dx"),
+                                            _ptr(psf, torch.float32, G * G, "psf"), float(alpha),
+                                            _ptr(out, numel=nx, name="out"), _stream(stream)),
+           "nlinv_apply_normal_static")
 
 
 def nlinv_frame(plan: Plan, Y, turn: int, x_prev, x_out, rho_out=None, img_out=None, stream=None):
