@@ -42,10 +42,17 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 // ---------------------------------------------------- kernel wrappers
 template <class K>
-__global__ void __launch_bounds__(K::BS) k_coil_y(Ctx C, const float2* src, int upd, int k, float2* hout) {
+__global__ void __launch_bounds__(K::BS) k_coil_y(Ctx C, const float2* src, float2* hout) {
+  extern __shared__ float2 sm[];
+  phase_coil_y<K>(C, sm, src, hout);
+}
+
+template <class K>
+__global__ void __launch_bounds__(K::BS) k_row_cg(Ctx C, int k, const float2* p_old, float2* p_new,
+                                                  float2* vout) {
   extern __shared__ float2 sm[];
   __shared__ double sred[32];
-  phase_coil_y<K>(C, sm, src, upd != 0, k, sred, hout);
+  phase_row_cg<K>(C, sm, sred, k, p_old, p_new, vout);
 }
 
 template <class K>
@@ -70,16 +77,19 @@ __global__ void __launch_bounds__(K::BS) k_row_d(Ctx C, const float2* rho, const
 }
 
 template <class K>
-__global__ void __launch_bounds__(K::BS) k_col_e(Ctx C, int mode, float alpha, const float2* kbin,
-                                                 const float2* sin, const float2* pv, float2* out, int slot) {
+__global__ void __launch_bounds__(K::BS) k_col_e(Ctx C, int mode, float alpha, int k, const float2* kbin,
+                                                 const float2* sin, const float2* p_old, float2* p_new,
+                                                 float2* out, float2* hout, int slot) {
   extern __shared__ float2 sm[];
   __shared__ double sred[32];
-  phase_col_e<K>(C, sm, sred, mode, alpha, kbin, sin, pv, out, slot);
+  phase_col_e<K>(C, sm, sred, mode, alpha, k, kbin, sin, p_old, p_new, out, hout, slot);
 }
 
-__global__ void k_upd(Ctx C, int k, int last) {
+template <class K>
+__global__ void __launch_bounds__(K::BS) k_upd(Ctx C, int k, int last, const float2* p) {
+  extern __shared__ float2 sm[];
   __shared__ double sred[32];
-  phase_upd(C, sred, k, last != 0);
+  phase_upd<K>(C, sm, sred, k, last != 0, p);
 }
 
 __global__ void k_init(Ctx C, const float2* xprev, float damping) { phase_init(C, xprev, damping); }
@@ -104,18 +114,19 @@ struct FrameArgs {
 // One whole NLINV frame in one cooperative launch: every phase of every
 // Newton step and CG iteration, separated by bounded grid barriers.
 template <class K>
-__global__ void __launch_bounds__(K::BS) k_frame(Ctx C, FrameArgs F) {
+__global__ void __launch_bounds__(K::BS, K::MINB) k_frame(Ctx C, FrameArgs F) {
   extern __shared__ float2 sm[];
   __shared__ double sred[32];
   const int NN = C.N * C.N;
+  unsigned epoch = 0;
 #define NLINV_SYNC() \
-  if (!grid_sync(C)) return
+  if (!grid_sync(C, epoch)) return
   phase_init(C, F.xprev, F.damping);
   NLINV_SYNC();
   for (int n = 0; n < F.M; ++n) {
     const float alpha = F.alpha[n];
     // Newton right-hand side: DF^H (Y - P F^(x^_n)) - alpha_n (x^_n - x_ref)
-    phase_coil_y<K>(C, sm, C.xn + NN, false, 0, sred, C.h);
+    phase_coil_y<K>(C, sm, C.xn + NN, C.h);
     NLINV_SYNC();
     phase_row_b<K>(C, sm, ROW_COIL, C.h, C.xn, nullptr, nullptr, C.v);
     NLINV_SYNC();
@@ -123,24 +134,24 @@ __global__ void __launch_bounds__(K::BS) k_frame(Ctx C, FrameArgs F) {
     NLINV_SYNC();
     phase_row_d<K>(C, sm, C.xn, C.v, C.s, C.kb);
     NLINV_SYNC();
-    phase_col_e<K>(C, sm, sred, E_RHS, alpha, C.kb, C.s, nullptr, C.r, SLOT_RR0);
+    phase_col_e<K>(C, sm, sred, E_RHS, alpha, 0, C.kb, C.s, nullptr, nullptr, C.r, C.Hr, SLOT_RR0);
     NLINV_SYNC();
     for (int k = 0; k < F.K; ++k) {
-      phase_coil_y<K>(C, sm, nullptr, true, k, sred, C.h);
-      NLINV_SYNC();
-      phase_row_b<K>(C, sm, ROW_LIN, C.h, C.xn, C.p, nullptr, C.v);
+      float2* pk = C.pb[k & 1];
+      const float2* pm = C.pb[(k + 1) & 1];
+      phase_row_cg<K>(C, sm, sred, k, pm, pk, C.v);
       NLINV_SYNC();
       phase_col_c<K>(C, sm, COL_TOEP, F.P, nullptr, nullptr, C.v);
       NLINV_SYNC();
       phase_row_d<K>(C, sm, C.xn, C.v, C.s, C.kb);
       NLINV_SYNC();
-      phase_col_e<K>(C, sm, sred, E_CG, alpha, C.kb, C.s, C.p, C.q, SLOT_PQ);
+      phase_col_e<K>(C, sm, sred, E_CG, alpha, k, C.kb, C.s, pm, pk, C.q, nullptr, SLOT_PQ);
       NLINV_SYNC();
-      phase_upd(C, sred, k, k == F.K - 1);
+      phase_upd<K>(C, sm, sred, k, k == F.K - 1, pk);
       NLINV_SYNC();
     }
   }
-  phase_coil_y<K>(C, sm, C.xn + NN, false, 0, sred, C.h);
+  phase_coil_y<K>(C, sm, C.xn + NN, C.h);
   NLINV_SYNC();
   phase_row_b<K>(C, sm, ROW_COILONLY, C.h, nullptr, nullptr, nullptr, nullptr);
   NLINV_SYNC();
@@ -315,6 +326,8 @@ int set_smem_attrs() {
     CK(cudaFuncSetAttribute(k_col_c<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(k_row_d<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(k_col_e<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
+    CK(cudaFuncSetAttribute(k_row_cg<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
+    CK(cudaFuncSetAttribute(k_upd<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(k_frame<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
   }
   return NLINV_OK;
@@ -325,12 +338,18 @@ template <class K>
 struct Launch {
   const nlinv_plan_s* pl;
   cudaStream_t st;
-  int coil_y(const float2* src, int upd, int k, float2* hout) const {
+  int coil_y(const float2* src, float2* hout) const {
     const Ctx& C = pl->C;
-    const int items = C.J * ((C.Gc + K::TW - 1) / K::TW);
-    const int g = plan_grid(items, upd ? (C.N * C.N + K::BS - 1) / K::BS : 1);
-    k_coil_y<K><<<g, K::BS, K::SMEM, st>>>(C, src, upd, k, hout);
+    const int g = plan_grid(C.J * ((C.Gc + K::TW - 1) / K::TW), 1);
+    k_coil_y<K><<<g, K::BS, K::SMEM, st>>>(C, src, hout);
     CKL("k_coil_y");
+    return NLINV_OK;
+  }
+  int row_cg(int k, const float2* p_old, float2* p_new, float2* vout) const {
+    const Ctx& C = pl->C;
+    const int g = plan_grid(C.J * ((C.N + K::TW - 1) / K::TW), 1);
+    k_row_cg<K><<<g, K::BS, K::SMEM, st>>>(C, k, p_old, p_new, vout);
+    CKL("k_row_cg");
     return NLINV_OK;
   }
   int row_b(int mode, const float2* hin, const float2* rho, const float2* drho, const float2* img,
@@ -355,26 +374,27 @@ struct Launch {
     CKL("k_row_d");
     return NLINV_OK;
   }
-  int col_e(int mode, float alpha, const float2* kbin, const float2* sin, const float2* pv, float2* out,
-            int slot) const {
+  int col_e(int mode, float alpha, int k, const float2* kbin, const float2* sin, const float2* p_old,
+            float2* p_new, float2* out, float2* hout, int slot) const {
     const Ctx& C = pl->C;
     const int items = C.J * ((C.Gc + K::TW - 1) / K::TW);
     const int g = plan_grid(items, (C.N * C.N + K::BS - 1) / K::BS);
-    k_col_e<K><<<g, K::BS, K::SMEM, st>>>(C, mode, alpha, kbin, sin, pv, out, slot);
+    k_col_e<K><<<g, K::BS, K::SMEM, st>>>(C, mode, alpha, k, kbin, sin, p_old, p_new, out, hout, slot);
     CKL("k_col_e");
     return NLINV_OK;
   }
-  int upd(int k, int last) const {
+  int upd(int k, int last, const float2* p) const {
     const Ctx& C = pl->C;
-    const int g = plan_grid((int)((C.nx + 255) / 256), 1);
-    k_upd<<<g, 256, 0, st>>>(C, k, last);
+    const int items = C.J * ((C.Gc + K::TW - 1) / K::TW);
+    const int g = plan_grid(items, (C.N * C.N + K::BS - 1) / K::BS);
+    k_upd<K><<<g, K::BS, K::SMEM, st>>>(C, k, last, p);
     CKL("k_upd");
     return NLINV_OK;
   }
   // coil maps c_j = W^-1 c^_j of x^ into the plan's c buffer
   int coils(const float2* xhat) const {
     const Ctx& C = pl->C;
-    int rc = coil_y(xhat + (size_t)C.N * C.N, 0, 0, C.h);
+    int rc = coil_y(xhat + (size_t)C.N * C.N, C.h);
     if (rc) return rc;
     return row_b(ROW_COILONLY, C.h, nullptr, nullptr, nullptr, nullptr);
   }
@@ -467,7 +487,7 @@ int nlinv_plan(nlinv_plan_t* out, const nlinv_params_t* p, const float* psf, nli
   // one allocation, carved into the buffers
   const size_t f2 = sizeof(float2);
   const size_t nx = (size_t)pl->nx;
-  size_t off[32];
+  size_t off[40];
   size_t tot = 0;
   int nb = 0;
   auto take = [&](size_t bytes) {
@@ -482,11 +502,12 @@ int nlinv_plan(nlinv_plan_t* out, const nlinv_params_t* p, const float* psf, nli
   take((size_t)J * N * G * f2);          // 5 v
   take((size_t)J * N * N * f2);          // 6 s
   take((size_t)J * N * Gc * f2);         // 7 kb
-  for (int i = 0; i < 6; ++i) take(nx * f2);  // 8..13 xn xref xcg r p q
-  take((size_t)NSLOT * kMaxPart * sizeof(double));  // 14 part
-  take(NSLOT * sizeof(int));             // 15 pcount
-  take(sizeof(int));                     // 16 err
-  take(2 * sizeof(unsigned));            // 17 bar
+  for (int i = 0; i < 7; ++i) take(nx * f2);  // 8..14 xn xref xcg r q p0 p1
+  take((size_t)NSLOT * kMaxPart * sizeof(double));  // 15 part
+  take(NSLOT * (sizeof(double) + sizeof(unsigned)));  // 16 tot, cnt
+  take(sizeof(int));                     // 17 err
+  take(2 * sizeof(unsigned));            // 18 bar
+  for (int i = 0; i < 2; ++i) take((size_t)J * N * Gc * f2);  // 19..20 Hr Hp
   e = cudaMalloc(&pl->mem, tot);
   if (e != cudaSuccess) {
     delete pl;
@@ -515,12 +536,16 @@ int nlinv_plan(nlinv_plan_t* out, const nlinv_params_t* p, const float* psf, nli
   C.xref = (float2*)(base + off[9]);
   C.xcg = (float2*)(base + off[10]);
   C.r = (float2*)(base + off[11]);
-  C.p = (float2*)(base + off[12]);
-  C.q = (float2*)(base + off[13]);
-  C.part = (double*)(base + off[14]);
-  C.pcount = (int*)(base + off[15]);
-  C.err = (int*)(base + off[16]);
-  C.bar = (unsigned*)(base + off[17]);
+  C.q = (float2*)(base + off[12]);
+  C.pb[0] = (float2*)(base + off[13]);
+  C.pb[1] = (float2*)(base + off[14]);
+  C.part = (double*)(base + off[15]);
+  C.tot = (double*)(base + off[16]);
+  C.cnt = (unsigned*)(C.tot + NSLOT);
+  C.err = (int*)(base + off[17]);
+  C.bar = (unsigned*)(base + off[18]);
+  C.Hr = (float2*)(base + off[19]);
+  C.Hp = (float2*)(base + off[20]);
   C.spin_limit = pl->prm.spin_limit;
 
   // host tables in FP64, rounded once
@@ -662,7 +687,7 @@ int nlinv_apply_DF(nlinv_plan_t pl, const void* xhat, const void* dx, void* z, n
     using K = decltype(k);
     Launch<K> L{pl, st};
     RC(L.coils(xh));
-    RC(L.coil_y(d + NN, 0, 0, pl->C.h));
+    RC(L.coil_y(d + NN, pl->C.h));
     RC(L.row_b(ROW_LIN, pl->C.h, xh, d, nullptr, pl->C.v));
     return L.col_c(COL_FWD, nullptr, nullptr, (float2*)z, pl->C.v);
   });
@@ -679,7 +704,7 @@ int nlinv_apply_DFH(nlinv_plan_t pl, const void* xhat, const void* z, void* dx_o
     RC(L.coils(xh));
     RC(L.col_c(COL_INV, nullptr, (const float2*)z, nullptr, pl->C.v));
     RC(L.row_d(xh, pl->C.v, pl->C.s, pl->C.kb));
-    return L.col_e(E_DFH, 0.f, pl->C.kb, pl->C.s, nullptr, (float2*)dx_out, SLOT_PQ);
+    return L.col_e(E_DFH, 0.f, 0, pl->C.kb, pl->C.s, nullptr, nullptr, (float2*)dx_out, nullptr, SLOT_PQ);
   });
 }
 
@@ -698,11 +723,12 @@ int nlinv_apply_normal(nlinv_plan_t pl, const void* xhat, const void* dx, int tu
     using K = decltype(k);
     Launch<K> L{pl, st};
     RC(L.coils(xh));
-    RC(L.coil_y(d + NN, 0, 0, pl->C.h));
+    RC(L.coil_y(d + NN, pl->C.h));
     RC(L.row_b(ROW_LIN, pl->C.h, xh, d, nullptr, pl->C.v));
     RC(L.col_c(COL_TOEP, P, nullptr, nullptr, pl->C.v));
     RC(L.row_d(xh, pl->C.v, pl->C.s, pl->C.kb));
-    return L.col_e(E_NORMAL, (float)alpha, pl->C.kb, pl->C.s, d, (float2*)out, SLOT_PQ);
+    return L.col_e(E_NORMAL, (float)alpha, 0, pl->C.kb, pl->C.s, nullptr, (float2*)d, (float2*)out, nullptr,
+                   SLOT_PQ);
   });
 }
 
@@ -744,18 +770,19 @@ int nlinv_frame(nlinv_plan_t pl, const void* Y, int turn, const void* x_prev, vo
     CKL("k_init");
     for (int n = 0; n < F.M; ++n) {
       const float alpha = F.alpha[n];
-      RC(L.coil_y(C.xn + NN, 0, 0, C.h));
+      RC(L.coil_y(C.xn + NN, C.h));
       RC(L.row_b(ROW_COIL, C.h, C.xn, nullptr, nullptr, C.v));
       RC(L.col_c(COL_RHS, F.P, F.Y, nullptr, C.v));
       RC(L.row_d(C.xn, C.v, C.s, C.kb));
-      RC(L.col_e(E_RHS, alpha, C.kb, C.s, nullptr, C.r, SLOT_RR0));
+      RC(L.col_e(E_RHS, alpha, 0, C.kb, C.s, nullptr, nullptr, C.r, C.Hr, SLOT_RR0));
       for (int kk = 0; kk < F.K; ++kk) {
-        RC(L.coil_y(nullptr, 1, kk, C.h));
-        RC(L.row_b(ROW_LIN, C.h, C.xn, C.p, nullptr, C.v));
+        float2* pk = C.pb[kk & 1];
+        const float2* pm = C.pb[(kk + 1) & 1];
+        RC(L.row_cg(kk, pm, pk, C.v));
         RC(L.col_c(COL_TOEP, F.P, nullptr, nullptr, C.v));
         RC(L.row_d(C.xn, C.v, C.s, C.kb));
-        RC(L.col_e(E_CG, alpha, C.kb, C.s, C.p, C.q, SLOT_PQ));
-        RC(L.upd(kk, kk == F.K - 1));
+        RC(L.col_e(E_CG, alpha, kk, C.kb, C.s, pm, pk, C.q, nullptr, SLOT_PQ));
+        RC(L.upd(kk, kk == F.K - 1, pk));
       }
     }
     RC(L.coils(C.xn));
@@ -867,7 +894,7 @@ extern "C" int nlinv_apply_normal_static(int N, int J, int Gc, double w_a, doubl
   take((size_t)J * N * N * f2);
   take((size_t)J * N * Gc * f2);
   take((size_t)NSLOT * kMaxPart * sizeof(double));
-  take(NSLOT * sizeof(int) + sizeof(int) + 2 * sizeof(unsigned));
+  take(NSLOT * (sizeof(double) + sizeof(unsigned)) + sizeof(int) + 2 * sizeof(unsigned));
   if (tot > kStaticScratchBytes) return NLINV_EINVAL;
   void* base_v = nullptr;
   RC(static_scratch(&base_v));
@@ -896,8 +923,9 @@ extern "C" int nlinv_apply_normal_static(int N, int J, int Gc, double w_a, doubl
   C.s = (float2*)(base + off[5]);
   C.kb = (float2*)(base + off[6]);
   C.part = (double*)(base + off[7]);
-  C.pcount = (int*)(base + off[8]);
-  C.err = C.pcount + NSLOT;
+  C.tot = (double*)(base + off[8]);
+  C.cnt = (unsigned*)(C.tot + NSLOT);
+  C.err = (int*)(C.cnt + NSLOT);
   C.bar = (unsigned*)(C.err + 1);
   C.spin_limit = 1LL << 22;
   const int nt = (G > Gc * Gc ? G : Gc * Gc);
@@ -911,10 +939,10 @@ extern "C" int nlinv_apply_normal_static(int N, int J, int Gc, double w_a, doubl
     RC(set_smem_attrs<K>());
     Launch<K> L{&tmp, st};
     RC(L.coils(xh));
-    RC(L.coil_y(d + NN, 0, 0, C.h));
+    RC(L.coil_y(d + NN, C.h));
     RC(L.row_b(ROW_LIN, C.h, xh, d, nullptr, C.v));
     RC(L.col_c(COL_TOEP, psf, nullptr, nullptr, C.v));
     RC(L.row_d(xh, C.v, C.s, C.kb));
-    return L.col_e(E_NORMAL, (float)alpha, C.kb, C.s, d, (float2*)out, SLOT_PQ);
+    return L.col_e(E_NORMAL, (float)alpha, 0, C.kb, C.s, nullptr, (float2*)d, (float2*)out, nullptr, SLOT_PQ);
   });
 }

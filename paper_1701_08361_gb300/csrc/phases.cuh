@@ -33,6 +33,21 @@
 #pragma once
 #include "fft.cuh"
 
+#ifndef NLINV_TW
+#define NLINV_TW 16
+#endif
+// phases are inlined into the persistent kernel unless NLINV_NOINLINE_PHASES
+// is defined (separate functions get their own register allocation but cost
+// more than they save here)
+#ifdef NLINV_NOINLINE_PHASES
+#define NLINV_PHASE __noinline__
+#else
+#define NLINV_PHASE __forceinline__
+#endif
+#ifndef NLINV_BAR_SLEEP_NS
+#define NLINV_BAR_SLEEP_NS 0
+#endif
+
 namespace nlinv {
 
 constexpr int kMaxPart = 4096;     // max CTAs that deposit an FP64 partial
@@ -50,9 +65,12 @@ struct Ctx {
   const float* dinv;    // [Gc][Gc]
   const float* psf;     // [U][G][G]
   float2 *c, *h, *v, *s, *kb;
-  float2 *xn, *xref, *xcg, *r, *p, *q;
-  double* part;         // [NSLOT][kMaxPart]
-  int* pcount;          // [NSLOT]
+  float2 *xn, *xref, *xcg, *r, *q;
+  float2* pb[2];        // CG direction p_k lives in pb[k & 1]
+  float2 *Hr, *Hp;      // y pass of W^-1 applied to r, p: [J][N][Gc]
+  double* part;         // [NSLOT][kMaxPart] per-CTA partials
+  double* tot;          // [NSLOT] totals, written by the last CTA of the producer
+  unsigned* cnt;        // [NSLOT] arrival counters of the producer (self-resetting)
   int* err;             // latched device error
   unsigned* bar;        // grid barrier {count, generation}
   long long spin_limit;
@@ -62,18 +80,29 @@ template <int G1_, int G2_> struct Cfg {
   static constexpr int G1 = G1_, G2 = G2_;
   static constexpr int G = G1 * G2;
   static constexpr int MX = G1 > G2 ? G1 : G2;
-  static constexpr int TW = 16;             // columns per tile / rows per group
+  static constexpr int TW = NLINV_TW;       // columns per tile / rows per group
   static constexpr int BS = TW * MX;        // threads per CTA
   static constexpr int RS = G + MX;         // smem stride of one row (float2)
   static constexpr int SMEM = TW * RS * 8;  // dynamic smem bytes
+  // CTAs per SM the persistent kernel is compiled for (caps registers)
+  static constexpr int MINB = BS <= 256 ? 2 : 1;
   static_assert(G1 % 2 == 0 && G2 % 2 == 0, "G1, G2 must be even");
 };
 
 __device__ __forceinline__ float2 ldcg(const float2* p) { return __ldcg(p); }
 
-// y + s x with the CG step scalar s kept in FP64 and one rounding to FP32
-__device__ __forceinline__ float2 axpy64(float2 x, double s, float2 y) {
-  return make_float2((float)fma(s, (double)x.x, (double)y.x), (float)fma(s, (double)x.y, (double)y.y));
+// A CG scalar (computed in FP64) as an unevaluated float pair hi + lo, so
+// that y + s x keeps s to ~48 bits at the cost of two FP32 FMAs (FP64
+// arithmetic runs at a small fraction of the FP32 rate on this part).
+struct Scal2 {
+  float hi, lo;
+};
+__device__ __forceinline__ Scal2 split(double s) {
+  const float hi = (float)s;
+  return Scal2{hi, (float)(s - (double)hi)};
+}
+__device__ __forceinline__ float2 axpy2(float2 x, Scal2 s, float2 y) {
+  return make_float2(fmaf(s.hi, x.x, fmaf(s.lo, x.x, y.x)), fmaf(s.hi, x.y, fmaf(s.lo, x.y, y.y)));
 }
 
 // index of grid position pos in the G_c coil band, -1 outside (Gc even)
@@ -91,58 +120,52 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;   // valid in lane 0
 }
 
-// deterministic block sum of v, stored as this CTA's partial of `slot`
+// Deterministic reduction of one FP64 scalar over the whole grid: each CTA
+// sums its threads (fixed warp trees) into part[slot][blockIdx]; the last CTA
+// to arrive adds the partials in index order and publishes tot[slot].  A
+// later phase (after a grid barrier or in a later kernel) reads the total
+// with a single load.
 __device__ __forceinline__ void block_partial(const Ctx& C, double v, int slot, double* sred) {
+  __shared__ int s_last;
   v = warp_sum(v);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   if (l == 0) sred[w] = v;
   __syncthreads();
-  if (w == 0) {
+  if (threadIdx.x == 0) {
     const int nw = blockDim.x >> 5;
-    double a = (l < nw) ? sred[l] : 0.0;
+    double a = 0.0;
+    for (int i = 0; i < nw; ++i) a += sred[i];
+    C.part[slot * kMaxPart + blockIdx.x] = a;
+    __threadfence();
+    s_last = (atomicAdd(C.cnt + slot, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (s_last && w == 0) {
+    __threadfence();
+    double a = 0.0;
+    for (int i = l; i < (int)gridDim.x; i += 32) a += __ldcg(C.part + slot * kMaxPart + i);
     a = warp_sum(a);
     if (l == 0) {
-      C.part[slot * kMaxPart + blockIdx.x] = a;
-      if (blockIdx.x == 0) C.pcount[slot] = gridDim.x;
+      C.tot[slot] = a;
+      C.cnt[slot] = 0u;
     }
   }
   __syncthreads();
 }
 
-// sum of all partials of `slot` in fixed order (every CTA computes it)
-__device__ __forceinline__ double slot_total(const Ctx& C, int slot, double* sred) {
-  if (threadIdx.x < 32) {
-    const int n = __ldcg(C.pcount + slot);
-    double a = 0.0;
-    for (int i = threadIdx.x; i < n; i += 32) a += __ldcg(C.part + slot * kMaxPart + i);
-    a = warp_sum(a);
-    if (threadIdx.x == 0) sred[0] = a;
-  }
-  __syncthreads();
-  const double t = sred[0];
-  __syncthreads();
-  return t;
-}
+// the published total of `slot`
+__device__ __forceinline__ double slot_total(const Ctx& C, int slot) { return __ldcg(C.tot + slot); }
 
 __device__ __forceinline__ void raise_err(const Ctx& C, int code) { atomicCAS(C.err, 0, code); }
 
 // ------------------------------------------------ A: W^-1 along y (coil)
-// src: c^ coefficients [J][Gc][Gc].  upd: the CG direction is first updated
-// in place, p = r + beta p (k > 0) or p = r (k == 0), and used as the source.
+// H(src): D_W^-1, then the inverse DFT along y of each c^ column (G_c
+// nonzero of G), keeping rows y < N, scaled by 1/G.  src: [J][Gc][Gc].
 template <class K>
-__device__ void phase_coil_y(const Ctx& C, float2* sm, const float2* src, bool upd, int k,
-                             double* sred, float2* hout) {
+__device__ NLINV_PHASE void phase_coil_y(const Ctx& C, float2* sm, const float2* src, float2* hout) {
   constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW;
-  const int N = C.N, Gc = C.Gc, J = C.J, NN = N * N;
+  const int N = C.N, Gc = C.Gc, J = C.J;
   const int t = threadIdx.x;
-  double beta = 0.0;
-  if (upd && k > 0) {
-    const double rr1 = slot_total(C, (k & 1) ? SLOT_RR1 : SLOT_RR0, sred);
-    const double rr0 = slot_total(C, (k & 1) ? SLOT_RR0 : SLOT_RR1, sred);
-    beta = (rr0 > 0.0) ? rr1 / rr0 : 0.0;
-  }
-  const float2* r_c = C.r + NN;
-  float2* p_c = C.p + NN;
   const int tiles = (Gc + TW - 1) / TW;
   const int items = J * tiles;
   for (int it = blockIdx.x; it < items; it += gridDim.x) {
@@ -157,17 +180,8 @@ __device__ void phase_coil_y(const Ctx& C, float2* sm, const float2* src, bool u
         for (int n2 = 0; n2 < G2; ++n2) {
           const int iy = coef_index(n1 + G1 * n2, G, Gc);
           float2 val = czero();
-          if (colok && iy >= 0) {
-            const size_t e = ((size_t)j * Gc + iy) * Gc + fx;
-            if (upd) {
-              const float2 rv = ldcg(r_c + e);
-              val = (k == 0) ? rv : axpy64(ldcg(p_c + e), beta, rv);
-              p_c[e] = val;
-            } else {
-              val = ldcg(src + e);
-            }
-            val = cscale(val, __ldg(C.dinv + iy * Gc + fx));
-          }
+          if (colok && iy >= 0)
+            val = cscale(ldcg(src + ((size_t)j * Gc + iy) * Gc + fx), __ldg(C.dinv + iy * Gc + fx));
           a[n2] = val;
         }
         dft<G2, true>(a);
@@ -196,12 +210,11 @@ __device__ void phase_coil_y(const Ctx& C, float2* sm, const float2* src, bool u
     }
     __syncthreads();
   }
-  if (upd) {  // rho part of the direction update
-    for (int e = blockIdx.x * blockDim.x + t; e < NN; e += gridDim.x * blockDim.x) {
-      const float2 rv = ldcg(C.r + e);
-      C.p[e] = (k == 0) ? rv : axpy64(ldcg(C.p + e), beta, rv);
-    }
-  }
+}
+
+// CG step length a = |r|^2 / Re<p, A p> (0 when |r|^2 = 0 or on breakdown)
+__device__ __forceinline__ double cg_step(double rr, double pq) {
+  return (rr > 0.0 && pq > 0.0 && isfinite(pq)) ? rr / pq : 0.0;
 }
 
 // ------------------------------------- B: W^-1 along x, product, row FFT
@@ -210,7 +223,7 @@ __device__ void phase_coil_y(const Ctx& C, float2* sm, const float2* src, bool u
 //      ROW_LIN     : u = c drho + rho dc
 //      ROW_IMG     : u = img (no coil part)
 template <class K>
-__device__ void phase_row_b(const Ctx& C, float2* sm, int mode, const float2* hin,
+__device__ NLINV_PHASE void phase_row_b(const Ctx& C, float2* sm, int mode, const float2* hin,
                             const float2* rho, const float2* drho, const float2* img,
                             float2* vout) {
   constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW, RS = K::RS;
@@ -303,13 +316,115 @@ __device__ void phase_row_b(const Ctx& C, float2* sm, int mode, const float2* hi
   }
 }
 
+// --------------------------- B in a CG iteration: direction update fused in
+// The y pass of W^-1 (H) of the CG direction is not recomputed: H r_k comes
+// exactly from the update phase (which transforms the rounded r_k), and
+//   H p_k = H r_k + beta_k H p_{k-1},  H p_0 = H r_0,
+// an addition without cancellation.  (Recurring H r_k = H r_{k-1} - a H q
+// instead would cancel catastrophically when |r| drops sharply and drift
+// away from r.)  p_rho,k = r_rho,k + beta_k p_rho,k-1 is formed on the fly
+// (channel 0 stores it into p_new).  Then as ROW_LIN:
+//   u = c p_rho + rho (x pass of W^-1 of H p), forward row FFT.
+template <class K>
+__device__ NLINV_PHASE void phase_row_cg(const Ctx& C, float2* sm, double* sred, int k, const float2* p_old,
+                             float2* p_new, float2* vout) {
+  constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW, RS = K::RS;
+  const int N = C.N, Gc = C.Gc, J = C.J;
+  const int t = threadIdx.x;
+  double beta64 = 0.0;
+  if (k > 0) {
+    const double rr_k = slot_total(C, (k & 1) ? SLOT_RR1 : SLOT_RR0);
+    const double rr_m = slot_total(C, (k & 1) ? SLOT_RR0 : SLOT_RR1);
+    beta64 = (rr_m > 0.0) ? rr_k / rr_m : 0.0;
+  }
+  const Scal2 beta = split(beta64);
+  const int groups = (N + TW - 1) / TW;
+  const int items = J * groups;
+  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+    const int j = it / groups;
+    const int y0 = (it - j * groups) * TW;
+    {  // stage 1: thread (row, n1): direction update of H p, inverse DFT over n2
+      const int rr = t / G1, n1 = t % G1, y = y0 + rr;
+      if (rr < TW && y < N) {
+        float2 av[G2];
+#pragma unroll
+        for (int n2 = 0; n2 < G2; ++n2) {
+          const int ix = coef_index(n1 + G1 * n2, G, Gc);
+          float2 hp = czero();
+          if (ix >= 0) {
+            const size_t e = ((size_t)j * N + y) * Gc + ix;
+            const float2 hr = ldcg(C.Hr + e);
+            hp = (k == 0) ? hr : axpy2(ldcg(C.Hp + e), beta, hr);
+            C.Hp[e] = hp;
+          }
+          av[n2] = hp;
+        }
+        dft<G2, true>(av);
+#pragma unroll
+        for (int k2 = 0; k2 < G2; ++k2) {
+          float2 x = av[k2];
+          if (k2) x = cmul(x, twg<true>(C.tw, n1 * k2));
+          sm[rr * RS + k2 * (G1 + 1) + n1] = x;
+        }
+      }
+    }
+    __syncthreads();
+    // stage 2: thread (row, k2): inverse DFT over n1 -> dc at x = k2 + G2 k1;
+    // u = c p_rho + rho dc; forward DFT over k1
+    const int rr = t / G2, k2 = t % G2, y = y0 + rr;
+    const bool ok = rr < TW && y < N;
+    float2 u[G1];
+    if (ok) {
+      float2 b[G1];
+#pragma unroll
+      for (int n1 = 0; n1 < G1; ++n1) b[n1] = sm[rr * RS + k2 * (G1 + 1) + n1];
+      dft<G1, true>(b);
+#pragma unroll
+      for (int k1 = 0; k1 < G1; ++k1) {
+        u[k1] = czero();
+        if (k1 < G1 / 2) {
+          const int x = k2 + G2 * k1;
+          const size_t ic = ((size_t)j * N + y) * N + x;
+          const int ir = y * N + x;
+          const float2 rv = ldcg(C.r + ir);
+          const float2 pr = (k == 0) ? rv : axpy2(ldcg(p_old + ir), beta, rv);
+          if (j == 0) p_new[ir] = pr;
+          u[k1] = cadd(cmul(ldcg(C.c + ic), pr), cmul(ldcg(C.xn + ir), b[k1]));
+        }
+      }
+      dft<G1, false>(u);
+#pragma unroll
+      for (int kb = 1; kb < G1; ++kb) u[kb] = cmul(u[kb], twg<false>(C.tw, k2 * kb));
+    }
+    __syncthreads();
+    if (ok) {
+#pragma unroll
+      for (int kb = 0; kb < G1; ++kb) sm[rr * RS + kb * (G2 + 1) + k2] = u[kb];
+    }
+    __syncthreads();
+    {  // stage 3: thread (row, kb): forward DFT over k2 -> kb + G1 ka
+      const int r3 = t / G1, kb = t % G1, y3 = y0 + r3;
+      if (r3 < TW && y3 < N) {
+        float2 d[G2];
+#pragma unroll
+        for (int a2 = 0; a2 < G2; ++a2) d[a2] = sm[r3 * RS + kb * (G2 + 1) + a2];
+        dft<G2, false>(d);
+        float2* dst = vout + ((size_t)j * N + y3) * G;
+#pragma unroll
+        for (int ka = 0; ka < G2; ++ka) dst[kb + G1 * ka] = d[ka];
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------ C: column pass (PSF convolution)
 // COL_TOEP: FFT_y, x P / G^2, iFFT_y, keep N rows (in place in v)
 // COL_RHS : FFT_y, z = (Y - P X / G) / G, iFFT_y, keep N rows
 // COL_FWD : FFT_y, zout = X / G (full G rows), stop
 // COL_INV : X = Yin / G (full G rows given), iFFT_y, keep N rows
 template <class K>
-__device__ void phase_col_c(const Ctx& C, float2* sm, int mode, const float* P,
+__device__ NLINV_PHASE void phase_col_c(const Ctx& C, float2* sm, int mode, const float* P,
                             const float2* Yin, float2* zout, float2* vio) {
   constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW;
   const int N = C.N, J = C.J;
@@ -398,7 +513,7 @@ __device__ void phase_col_c(const Ctx& C, float2* sm, int mode, const float* P,
 
 // ------------------------------- D: row iFFT, channel products, W^-H along x
 template <class K>
-__device__ void phase_row_d(const Ctx& C, float2* sm, const float2* rho, const float2* win,
+__device__ NLINV_PHASE void phase_row_d(const Ctx& C, float2* sm, const float2* rho, const float2* win,
                             float2* sout, float2* kbout) {
   constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW, RS = K::RS;
   const int N = C.N, Gc = C.Gc, J = C.J;
@@ -474,20 +589,31 @@ __device__ void phase_row_d(const Ctx& C, float2* sm, const float2* rho, const f
 }
 
 // ----------------- E: W^-H along y, D_W^-1, channel sum, Tikhonov, Re<p,q>
-// E_CG    : out = q = A p (+ alpha p), partial Re<p, q>      (p = pv)
-// E_RHS   : out = r = DF^H(...) - alpha (x_n - x_ref), partial |r|^2
+// E_CG    : p_k,c = r_c + beta_k p_{k-1},c formed on the fly (into p_new);
+//           q = A p_k + alpha p_k, partial Re<p_k, q>
+// E_RHS   : out = r = DF^H(...) - alpha (x_n - x_ref), partial |r|^2; hout = H r
 // E_DFH   : out = DF^H z
-// E_NORMAL: out = (DF^H P DF + alpha) dx                      (dx = pv)
+// E_NORMAL: out = (DF^H P DF + alpha) dx                      (dx = p_new)
+// H is the y pass of W^-1 (as phase A computes it); for E_RHS the column
+// values are still in registers, so it costs one more exchange.
 template <class K>
-__device__ void phase_col_e(const Ctx& C, float2* sm, double* sred, int mode, float alpha,
-                            const float2* kbin, const float2* sin, const float2* pv,
-                            float2* out, int slot) {
+__device__ NLINV_PHASE void phase_col_e(const Ctx& C, float2* sm, double* sred, int mode, float alpha, int k,
+                            const float2* kbin, const float2* sin, const float2* p_old,
+                            float2* p_new, float2* out, float2* hout, int slot) {
   constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW;
   const int N = C.N, Gc = C.Gc, J = C.J, NN = N * N;
   const int t = threadIdx.x;
+  const bool withH = (mode == E_RHS);
+  double beta64 = 0.0;
+  if (mode == E_CG && k > 0) {
+    const double rr_k = slot_total(C, (k & 1) ? SLOT_RR1 : SLOT_RR0);
+    const double rr_m = slot_total(C, (k & 1) ? SLOT_RR0 : SLOT_RR1);
+    beta64 = (rr_m > 0.0) ? rr_k / rr_m : 0.0;
+  }
+  const Scal2 beta = split(beta64);
   const int tiles = (Gc + TW - 1) / TW;
   const int items = J * tiles;
-  double acc = 0.0;
+  float acc = 0.f;   // this thread's few terms; CTA and grid sums in FP64
   for (int it = blockIdx.x; it < items; it += gridDim.x) {
     const int j = it / tiles;
     const int fx = (it - j * tiles) * TW + (t % TW);
@@ -510,34 +636,68 @@ __device__ void phase_col_e(const Ctx& C, float2* sm, double* sred, int mode, fl
       }
     }
     __syncthreads();
-    {  // stage 2: thread (k2, c): forward DFT over n1, crop rows to G_c
-      const int k2 = t / TW, cc = t % TW;
-      if (k2 < G2 && colok) {
-        float2 b[G1];
+    // stage 2: thread (k2, c): forward DFT over n1, crop rows to G_c, the
+    // pointwise epilogue; then (E_CG/E_RHS) D_W^-1 and the inverse DFT over
+    // k1 of the new column for H
+    const int k2 = t / TW, cc = t % TW;
+    const bool ok = k2 < G2 && colok;
+    float2 b[G1];
+    if (ok) {
 #pragma unroll
-        for (int n1 = 0; n1 < G1; ++n1) b[n1] = sm[(k2 * G1 + n1) * TW + cc];
-        dft<G1, false>(b);
+      for (int n1 = 0; n1 < G1; ++n1) b[n1] = sm[(k2 * G1 + n1) * TW + cc];
+      dft<G1, false>(b);
 #pragma unroll
-        for (int k1 = 0; k1 < G1; ++k1) {
-          const int iy = coef_index(k2 + G2 * k1, G, Gc);
-          if (iy < 0) continue;
-          const size_t e = (size_t)NN + ((size_t)j * Gc + iy) * Gc + fx;
-          const float2 val = cscale(b[k1], C.inv_G * __ldg(C.dinv + iy * Gc + fx));
-          if (mode == E_CG) {
-            const float2 p = ldcg(pv + e);
-            const float2 qv = cfma(p, alpha, val);
-            out[e] = qv;
-            acc += (double)p.x * qv.x + (double)p.y * qv.y;
-          } else if (mode == E_RHS) {
-            const float2 d = csub(ldcg(C.xn + e), ldcg(C.xref + e));
-            const float2 bv = cfma(d, -alpha, val);
-            out[e] = bv;
-            acc += (double)bv.x * bv.x + (double)bv.y * bv.y;
-          } else if (mode == E_DFH) {
-            out[e] = val;
-          } else {
-            out[e] = cfma(ldcg(pv + e), alpha, val);
-          }
+      for (int k1 = 0; k1 < G1; ++k1) {
+        const int iy = coef_index(k2 + G2 * k1, G, Gc);
+        if (iy < 0) {
+          b[k1] = czero();
+          continue;
+        }
+        const size_t e = (size_t)NN + ((size_t)j * Gc + iy) * Gc + fx;
+        const float dv = __ldg(C.dinv + iy * Gc + fx);
+        const float2 val = cscale(b[k1], C.inv_G * dv);
+        float2 res;
+        if (mode == E_CG) {
+          const float2 rv = ldcg(C.r + e);
+          const float2 p = (k == 0) ? rv : axpy2(ldcg(p_old + e), beta, rv);
+          p_new[e] = p;
+          res = cfma(p, alpha, val);
+          acc = fmaf(p.x, res.x, fmaf(p.y, res.y, acc));
+        } else if (mode == E_RHS) {
+          const float2 d = csub(ldcg(C.xn + e), ldcg(C.xref + e));
+          res = cfma(d, -alpha, val);
+          acc = fmaf(res.x, res.x, fmaf(res.y, res.y, acc));
+        } else if (mode == E_DFH) {
+          res = val;
+        } else {
+          res = cfma(ldcg(p_new + e), alpha, val);
+        }
+        out[e] = res;
+        b[k1] = cscale(res, dv);
+      }
+      if (withH) {
+        dft<G1, true>(b);
+#pragma unroll
+        for (int m1 = 1; m1 < G1; ++m1) b[m1] = cmul(b[m1], twg<true>(C.tw, k2 * m1));
+      }
+    }
+    if (withH) {
+      __syncthreads();
+      if (ok) {
+#pragma unroll
+        for (int m1 = 0; m1 < G1; ++m1) sm[(m1 * G2 + k2) * TW + cc] = b[m1];
+      }
+      __syncthreads();
+      {  // stage 3: thread (m1, c): inverse DFT over k2 -> y = m1 + G1 m2 < N
+        const int m1 = t / TW;
+        if (m1 < G1 && colok) {
+          float2 d[G2];
+#pragma unroll
+          for (int a2 = 0; a2 < G2; ++a2) d[a2] = sm[(m1 * G2 + a2) * TW + (t % TW)];
+          dft<G2, true>(d);
+#pragma unroll
+          for (int m2 = 0; m2 < G2 / 2; ++m2)
+            hout[((size_t)j * N + m1 + G1 * m2) * Gc + fx] = cscale(d[m2], C.inv_G);
         }
       }
     }
@@ -548,54 +708,106 @@ __device__ void phase_col_e(const Ctx& C, float2* sm, double* sred, int mode, fl
     float2 sv = czero();
     for (int j = 0; j < J; ++j) sv = cadd(sv, ldcg(sin + (size_t)j * NN + e));
     if (mode == E_CG) {
-      const float2 p = ldcg(pv + e);
+      const float2 p = ldcg(p_new + e);
       const float2 qv = cfma(p, alpha, sv);
       out[e] = qv;
-      acc += (double)p.x * qv.x + (double)p.y * qv.y;
+      acc = fmaf(p.x, qv.x, fmaf(p.y, qv.y, acc));
     } else if (mode == E_RHS) {
       const float2 d = csub(ldcg(C.xn + e), ldcg(C.xref + e));
       const float2 bv = cfma(d, -alpha, sv);
       out[e] = bv;
-      acc += (double)bv.x * bv.x + (double)bv.y * bv.y;
+      acc = fmaf(bv.x, bv.x, fmaf(bv.y, bv.y, acc));
     } else if (mode == E_DFH) {
       out[e] = sv;
     } else {
-      out[e] = cfma(ldcg(pv + e), alpha, sv);
+      out[e] = cfma(ldcg(p_new + e), alpha, sv);
     }
   }
-  if (mode == E_CG || mode == E_RHS) block_partial(C, acc, slot, sred);
+  if (mode == E_CG || mode == E_RHS) block_partial(C, (double)acc, slot, sred);
 }
 
 // -------------------------------------------------- F: CG vector update
-// a = |r_k|^2 / Re<p, A p> (FP64); x += a p; r -= a q; partial |r_{k+1}|^2.
-// On the last iteration the Newton update x^_{n+1} = x^_n + x is applied.
-__device__ __forceinline__ void phase_upd(const Ctx& C, double* sred, int k, bool last) {
-  const double rr = slot_total(C, (k & 1) ? SLOT_RR1 : SLOT_RR0, sred);
-  const double pq = slot_total(C, SLOT_PQ, sred);
-  double a = 0.0;
-  if (rr > 0.0) {
-    if (pq > 0.0 && isfinite(pq)) {
-      a = rr / pq;
-    } else if (blockIdx.x == 0 && threadIdx.x == 0) {
-      raise_err(C, DEV_ENUMERIC);
-    }
-  }
-  double acc = 0.0;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < C.nx; e += gridDim.x * blockDim.x) {
-    const float2 p = ldcg(C.p + e);
-    const float2 xv = axpy64(p, a, k > 0 ? ldcg(C.xcg + e) : czero());
-    const float2 rv = axpy64(ldcg(C.q + e), -a, ldcg(C.r + e));
+// a = |r_k|^2 / Re<p_k, A p_k> (FP64); x += a p_k; r -= a q; partial
+// |r_{k+1}|^2; and H r_{k+1} (the y pass of W^-1 of the rounded new r) for
+// the next direction.  Coil columns are handled per (channel, column tile)
+// so the transform stays on chip; rho elementwise.  On the last iteration
+// x^_{n+1} = x^_n + x is applied and H is not needed.
+template <class K>
+__device__ NLINV_PHASE void phase_upd(const Ctx& C, float2* sm, double* sred, int k, bool last,
+                                       const float2* p) {
+  constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW;
+  const int N = C.N, Gc = C.Gc, J = C.J, NN = N * N;
+  const int t = threadIdx.x;
+  const double rr = slot_total(C, (k & 1) ? SLOT_RR1 : SLOT_RR0);
+  const double pq = slot_total(C, SLOT_PQ);
+  const double a64 = cg_step(rr, pq);
+  if (rr > 0.0 && a64 == 0.0 && blockIdx.x == 0 && t == 0) raise_err(C, DEV_ENUMERIC);
+  const Scal2 a = split(a64), na = split(-a64);
+  float acc = 0.f;   // this thread's few terms; CTA and grid sums in FP64
+  auto update = [&](size_t e) -> float2 {
+    const float2 pv = ldcg(p + e);
+    const float2 xv = axpy2(pv, a, k > 0 ? ldcg(C.xcg + e) : czero());
+    const float2 rv = axpy2(ldcg(C.q + e), na, ldcg(C.r + e));
     C.r[e] = rv;
-    acc += (double)rv.x * rv.x + (double)rv.y * rv.y;
+    acc = fmaf(rv.x, rv.x, fmaf(rv.y, rv.y, acc));
     if (last) C.xn[e] = cadd(ldcg(C.xn + e), xv);
     else C.xcg[e] = xv;
+    return rv;
+  };
+  const int tiles = (Gc + TW - 1) / TW;
+  const int items = J * tiles;
+  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+    const int j = it / tiles;
+    const int fx = (it - j * tiles) * TW + (t % TW);
+    const bool colok = fx < Gc;
+    {  // stage 1: thread (n1, c): update the column's entries, inverse DFT over n2
+      const int n1 = t / TW;
+      if (n1 < G1) {
+        float2 av[G2];
+#pragma unroll
+        for (int n2 = 0; n2 < G2; ++n2) {
+          const int iy = coef_index(n1 + G1 * n2, G, Gc);
+          float2 val = czero();
+          if (colok && iy >= 0) {
+            const float2 rv = update((size_t)NN + ((size_t)j * Gc + iy) * Gc + fx);
+            val = cscale(rv, __ldg(C.dinv + iy * Gc + fx));
+          }
+          av[n2] = val;
+        }
+        if (!last) {
+          dft<G2, true>(av);
+#pragma unroll
+          for (int k2 = 0; k2 < G2; ++k2) {
+            float2 x = av[k2];
+            if (k2) x = cmul(x, twg<true>(C.tw, n1 * k2));
+            sm[(k2 * G1 + n1) * TW + (t % TW)] = x;
+          }
+        }
+      }
+    }
+    if (!last) {
+      __syncthreads();
+      const int k2 = t / TW, cc = t % TW;
+      if (k2 < G2 && colok) {  // stage 2: inverse DFT over n1, keep y < N
+        float2 b[G1];
+#pragma unroll
+        for (int n1 = 0; n1 < G1; ++n1) b[n1] = sm[(k2 * G1 + n1) * TW + cc];
+        dft<G1, true>(b);
+#pragma unroll
+        for (int k1 = 0; k1 < G1 / 2; ++k1)
+          C.Hr[((size_t)j * N + k2 + G2 * k1) * Gc + fx] = cscale(b[k1], C.inv_G);
+      }
+      __syncthreads();
+    }
   }
-  block_partial(C, acc, (k & 1) ? SLOT_RR0 : SLOT_RR1, sred);
+  for (int e = blockIdx.x * blockDim.x + t; e < NN; e += gridDim.x * blockDim.x) update((size_t)e);
+  block_partial(C, (double)acc, (k & 1) ? SLOT_RR0 : SLOT_RR1, sred);
 }
 
 // x^_0 = x_prev (or rho = 1, c^ = 0), x_ref = damping * x_prev
 __device__ __forceinline__ void phase_init(const Ctx& C, const float2* xprev, float damping) {
   const int NN = C.N * C.N;
+  if (blockIdx.x == 0 && threadIdx.x < NSLOT) C.cnt[threadIdx.x] = 0u;   // fresh reductions
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < C.nx; e += gridDim.x * blockDim.x) {
     float2 v = xprev ? ldcg(xprev + e) : make_float2(e < NN ? 1.f : 0.f, 0.f);
     C.xn[e] = v;
@@ -624,32 +836,39 @@ __device__ __forceinline__ void phase_final(const Ctx& C, float2* xout, float2* 
 }
 
 // ------------------------------------------------------- grid barrier
-// Sense-free generation barrier for the cooperative persistent kernel.
-// Every wait is bounded by spin_limit polls; on expiry the error word is set
-// and all CTAs leave at their next barrier.
-__device__ __forceinline__ bool grid_sync(const Ctx& C) {
+// Monotone-counter barrier for the cooperative persistent kernel: arrival is
+// an acq_rel atomic add on one counter (zeroed before each launch); barrier
+// number e is passed once the counter reaches e * gridDim.x.  Every wait is
+// bounded by spin_limit polls; on expiry the error word is set and all CTAs
+// leave at their next barrier.
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
+  unsigned o;
+  asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(o) : "l"(p), "r"(v) : "memory");
+  return o;
+}
+
+__device__ __forceinline__ bool grid_sync(const Ctx& C, unsigned& epoch) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* gen = C.bar + 1;
-    const unsigned g = *gen;
-    __threadfence();
-    const unsigned prev = atomicAdd(C.bar, 1u);
-    if (prev == gridDim.x - 1) {
-      atomicExch(C.bar, 0u);
-      __threadfence();
-      atomicAdd(C.bar + 1, 1u);
-    } else {
+    epoch += 1;
+    const unsigned target = epoch * gridDim.x;
+    const unsigned prev = atom_add_acq_rel(C.bar, 1u);
+    if (prev + 1 != target) {
       long long it = 0;
-      while (*gen == g) {
+      while ((int)(ld_acquire(C.bar) - target) < 0) {
         if (*(volatile int*)C.err != 0) break;
         if (++it > C.spin_limit) {
           raise_err(C, DEV_ETIMEOUT);
           break;
         }
-        __nanosleep(20);
+        if (NLINV_BAR_SLEEP_NS > 0) __nanosleep(NLINV_BAR_SLEEP_NS);
       }
     }
-    __threadfence();
   }
   __syncthreads();
   return *(volatile int*)C.err == 0;

@@ -14,7 +14,7 @@ import os
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libnlinv.so")
+LIB_PATH = os.environ.get("NLINV_LIB") or os.path.join(_HERE, "libnlinv.so")
 
 NLINV_OK = 0
 NLINV_EINVAL = -1
