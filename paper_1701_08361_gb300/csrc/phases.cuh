@@ -87,6 +87,8 @@ template <int G1_, int G2_> struct Cfg {
   // CTAs per SM the persistent kernel is compiled for (caps registers)
   static constexpr int MINB = BS <= 256 ? 2 : 1;
   static_assert(G1 % 2 == 0 && G2 % 2 == 0, "G1, G2 must be even");
+  // the FP64 block reductions use full-warp shuffles over blockDim / 32 warps
+  static_assert(BS % 32 == 0, "threads per CTA must be a whole number of warps");
 };
 
 __device__ __forceinline__ float2 ldcg(const float2* p) { return __ldcg(p); }
