@@ -69,6 +69,8 @@ typedef struct {
   long long spin_limit; /* polls before a device-side wait gives up; 0 -> default */
   int exec_mode;      /* 0: one persistent cooperative launch per frame;
                          1: one launch per phase (unfused comparator) */
+  int max_batch;      /* frames of this plan one nlinv_batch call may hold, 1..64;
+                         0 -> 1 (the plan allocates one workspace per frame) */
 } nlinv_params_t;
 
 /* Fill `p` with the defaults for an N x N image and J channels:
@@ -161,6 +163,31 @@ int nlinv_apply_normal_static(int N, int J, int Gc, double w_a, double w_l,
  * [N][N] rho * sqrt(sum_j |c_j|^2) or NULL. */
 int nlinv_frame(nlinv_plan_t plan, const void* Y, int turn, const void* x_prev,
                 void* x_out, void* rho_out, void* img_out, nlinv_stream_t stream);
+
+/* One frame of an nlinv_batch call. */
+typedef struct {
+  nlinv_plan_t plan;    /* size class (N, J, Gc, M, K, alpha schedule) of the frame */
+  const void* Y;        /* device complex64 [J][G][G] gridded data */
+  int turn;             /* PSF slot of the plan */
+  const void* x_prev;   /* device [n_x] initial value and regulariser, or NULL
+                           (rho = 1, c^ = 0) */
+  void* x_out;          /* device [n_x]; may alias this frame's x_prev, not another's */
+  void* rho_out;        /* device [N][N] or NULL */
+  void* img_out;        /* device [N][N] rho * sqrt(sum_j |c_j|^2) or NULL */
+} nlinv_frame_desc_t;
+
+/* Independent frames in flight together (the temporal decomposition of
+ * Sec. 3.3, Eq. 10: frames whose initial/regularisation values are already
+ * available are reconstructed at the same time).  Each frame is exactly
+ * nlinv_frame with its own inputs; frames may belong to different plans
+ * (grid sizes, channel counts).  Frames of one plan (at most its max_batch)
+ * run in one persistent cooperative launch whose CTAs are split into one
+ * group per frame; different plans run concurrently on the plans' own
+ * streams, each on a share of the SMs proportional to its work, and the
+ * call is ordered on `stream` before and after.  Which frame serves as
+ * whose x_prev (the schedule) is the caller's choice: no frame may read
+ * another frame's x_out of the same call. */
+int nlinv_batch(const nlinv_frame_desc_t* frames, int nframes, nlinv_stream_t stream);
 
 /* Bounded device-side wait until *flag == expected (flag: device int),
  * polling at most spin_limit times; on expiry the plan latches

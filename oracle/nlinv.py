@@ -312,13 +312,16 @@ def image(x: XVec, geom: Geometry) -> np.ndarray:
 
 
 def source_frame(n: int, delay: int, warmup: int) -> int:
-    """Frame whose x^ initialises and regularises frame n under the batched
-    relaxation of the temporal decomposition (Sec. 3.3, Eq. (10) with a fixed
-    offset): in order (n-1) for n <= warmup, n - delay afterwards.  -1 means
-    the initial value (rho = 1, c = 0)."""
+    """Frame whose x^ initialises and regularises frame n under the temporal
+    decomposition (Sec. 3.3, Eq. (10)): frames n <= warmup follow strictly in
+    order (n - 1); later frames are reconstructed `delay` at a time and each
+    uses the most recent frame available when its group starts, i.e. the last
+    frame of the previous group (frame `warmup` for the first group), which
+    lies within [n - delay, n - 1].  delay = 1 is the sequential stream.
+    -1 means the initial value (rho = 1, c = 0)."""
     if n <= warmup:
         return n - 1
-    return max(n - delay, -1)
+    return warmup + ((n - warmup - 1) // delay) * delay
 
 
 def nlinv_stream(frames, geom: Geometry, prm: Params = Params(),

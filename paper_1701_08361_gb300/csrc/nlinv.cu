@@ -41,113 +41,170 @@ int cuda_fail(cudaError_t e, const char* what) {
   } while (0)
 
 // ---------------------------------------------------- kernel wrappers
+// every CTA of a one-frame launch works on that frame
+__device__ __forceinline__ Ctx whole_grid(const Ctx& C0) {
+  Ctx C = C0;
+  C.bid = blockIdx.x;
+  C.nb = gridDim.x;
+  return C;
+}
+
 template <class K>
-__global__ void __launch_bounds__(K::BS) k_coil_y(Ctx C, const float2* src, float2* hout) {
+__global__ void __launch_bounds__(K::BS) k_coil_y(Ctx C0, const float2* src, float2* hout) {
+  const Ctx C = whole_grid(C0);
   extern __shared__ float2 sm[];
   phase_coil_y<K>(C, sm, src, hout);
 }
 
 template <class K>
-__global__ void __launch_bounds__(K::BS) k_row_cg(Ctx C, int k, const float2* p_old, float2* p_new,
+__global__ void __launch_bounds__(K::BS) k_row_cg(Ctx C0, int k, const float2* p_old, float2* p_new,
                                                   float2* vout) {
+  const Ctx C = whole_grid(C0);
   extern __shared__ float2 sm[];
   __shared__ double sred[32];
   phase_row_cg<K>(C, sm, sred, k, p_old, p_new, vout);
 }
 
 template <class K>
-__global__ void __launch_bounds__(K::BS) k_row_b(Ctx C, int mode, const float2* hin, const float2* rho,
+__global__ void __launch_bounds__(K::BS) k_row_b(Ctx C0, int mode, const float2* hin, const float2* rho,
                                                  const float2* drho, const float2* img, float2* vout) {
+  const Ctx C = whole_grid(C0);
   extern __shared__ float2 sm[];
   phase_row_b<K>(C, sm, mode, hin, rho, drho, img, vout);
 }
 
 template <class K>
-__global__ void __launch_bounds__(K::BS) k_col_c(Ctx C, int mode, const float* P, const float2* Yin,
+__global__ void __launch_bounds__(K::BS) k_col_c(Ctx C0, int mode, const float* P, const float2* Yin,
                                                  float2* zout, float2* vio) {
+  const Ctx C = whole_grid(C0);
   extern __shared__ float2 sm[];
   phase_col_c<K>(C, sm, mode, P, Yin, zout, vio);
 }
 
 template <class K>
-__global__ void __launch_bounds__(K::BS) k_row_d(Ctx C, const float2* rho, const float2* win, float2* sout,
+__global__ void __launch_bounds__(K::BS) k_row_d(Ctx C0, const float2* rho, const float2* win, float2* sout,
                                                  float2* kbout) {
+  const Ctx C = whole_grid(C0);
   extern __shared__ float2 sm[];
   phase_row_d<K>(C, sm, rho, win, sout, kbout);
 }
 
 template <class K>
-__global__ void __launch_bounds__(K::BS) k_col_e(Ctx C, int mode, float alpha, int k, const float2* kbin,
+__global__ void __launch_bounds__(K::BS) k_col_e(Ctx C0, int mode, float alpha, int k, const float2* kbin,
                                                  const float2* sin, const float2* p_old, float2* p_new,
                                                  float2* out, float2* hout, int slot) {
+  const Ctx C = whole_grid(C0);
   extern __shared__ float2 sm[];
   __shared__ double sred[32];
   phase_col_e<K>(C, sm, sred, mode, alpha, k, kbin, sin, p_old, p_new, out, hout, slot);
 }
 
 template <class K>
-__global__ void __launch_bounds__(K::BS) k_upd(Ctx C, int k, int last, const float2* p) {
+__global__ void __launch_bounds__(K::BS) k_upd(Ctx C0, int k, int last, const float2* p) {
+  const Ctx C = whole_grid(C0);
   extern __shared__ float2 sm[];
   __shared__ double sred[32];
   phase_upd<K>(C, sm, sred, k, last != 0, p);
 }
 
-__global__ void k_init(Ctx C, const float2* xprev, float damping) { phase_init(C, xprev, damping); }
+__global__ void k_init(Ctx C0, const float2* xprev, float damping) {
+  const Ctx C = whole_grid(C0);
+  phase_init(C, xprev, damping);
+}
 
-__global__ void k_final(Ctx C, float2* xout, float2* rho_out, float2* img_out) {
+__global__ void k_final(Ctx C0, float2* xout, float2* rho_out, float2* img_out) {
+  const Ctx C = whole_grid(C0);
   phase_final(C, xout, rho_out, img_out);
 }
 
 constexpr int kMaxNewton = 32;
-struct FrameArgs {
+constexpr int kMaxBatch = 64;
+
+// per-frame inputs and outputs
+struct FrameIO {
   const float2* Y;
   const float* P;
   const float2* xprev;
   float2* xout;
   float2* rho_out;
   float2* img_out;
+};
+
+struct FrameArgs {
+  FrameIO io;
   int M, K;
   float damping;
   float alpha[kMaxNewton];
 };
 
-// One whole NLINV frame in one cooperative launch: every phase of every
-// Newton step and CG iteration, separated by bounded grid barriers.
+struct BatchArgs {
+  int nf, M, K;
+  float damping;
+  float alpha[kMaxNewton];
+  size_t fstride;             // bytes between the frames' workspaces
+  FrameIO io[kMaxBatch];
+};
+
+// the workspace of frame f: every per-frame buffer moved by `off` bytes
+__host__ __device__ __forceinline__ Ctx frame_ctx(Ctx C, size_t off) {
+#define NLINV_ADV(T, p) C.p = (T*)((char*)C.p + off)
+  NLINV_ADV(float2, c);
+  NLINV_ADV(float2, h);
+  NLINV_ADV(float2, v);
+  NLINV_ADV(float2, s);
+  NLINV_ADV(float2, kb);
+  NLINV_ADV(float2, xn);
+  NLINV_ADV(float2, xref);
+  NLINV_ADV(float2, xcg);
+  NLINV_ADV(float2, r);
+  NLINV_ADV(float2, q);
+  NLINV_ADV(float2, pb[0]);
+  NLINV_ADV(float2, pb[1]);
+  NLINV_ADV(double, part);
+  NLINV_ADV(double, tot);
+  NLINV_ADV(unsigned, cnt);
+  NLINV_ADV(float2, Hr);
+  NLINV_ADV(float2, Hp);
+#undef NLINV_ADV
+  return C;
+}
+
+// Every phase of every Newton step and CG iteration of one frame, separated
+// by bounded grid barriers (which all CTAs of the launch pass together).
 template <class K>
-__global__ void __launch_bounds__(K::BS, K::MINB) k_frame(Ctx C, FrameArgs F) {
-  extern __shared__ float2 sm[];
-  __shared__ double sred[32];
+__device__ __forceinline__ void frame_body(const Ctx& C, float2* sm, double* sred, const FrameIO& io, int M,
+                                           int Kcg, float damping, const float* alpha) {
   const int NN = C.N * C.N;
   unsigned epoch = 0;
 #define NLINV_SYNC() \
   if (!grid_sync(C, epoch)) return
-  phase_init(C, F.xprev, F.damping);
+  phase_init(C, io.xprev, damping);
   NLINV_SYNC();
-  for (int n = 0; n < F.M; ++n) {
-    const float alpha = F.alpha[n];
+  for (int n = 0; n < M; ++n) {
+    const float al = alpha[n];
     // Newton right-hand side: DF^H (Y - P F^(x^_n)) - alpha_n (x^_n - x_ref)
     phase_coil_y<K>(C, sm, C.xn + NN, C.h);
     NLINV_SYNC();
     phase_row_b<K>(C, sm, ROW_COIL, C.h, C.xn, nullptr, nullptr, C.v);
     NLINV_SYNC();
-    phase_col_c<K>(C, sm, COL_RHS, F.P, F.Y, nullptr, C.v);
+    phase_col_c<K>(C, sm, COL_RHS, io.P, io.Y, nullptr, C.v);
     NLINV_SYNC();
     phase_row_d<K>(C, sm, C.xn, C.v, C.s, C.kb);
     NLINV_SYNC();
-    phase_col_e<K>(C, sm, sred, E_RHS, alpha, 0, C.kb, C.s, nullptr, nullptr, C.r, C.Hr, SLOT_RR0);
+    phase_col_e<K>(C, sm, sred, E_RHS, al, 0, C.kb, C.s, nullptr, nullptr, C.r, C.Hr, SLOT_RR0);
     NLINV_SYNC();
-    for (int k = 0; k < F.K; ++k) {
+    for (int k = 0; k < Kcg; ++k) {
       float2* pk = C.pb[k & 1];
       const float2* pm = C.pb[(k + 1) & 1];
       phase_row_cg<K>(C, sm, sred, k, pm, pk, C.v);
       NLINV_SYNC();
-      phase_col_c<K>(C, sm, COL_TOEP, F.P, nullptr, nullptr, C.v);
+      phase_col_c<K>(C, sm, COL_TOEP, io.P, nullptr, nullptr, C.v);
       NLINV_SYNC();
       phase_row_d<K>(C, sm, C.xn, C.v, C.s, C.kb);
       NLINV_SYNC();
-      phase_col_e<K>(C, sm, sred, E_CG, alpha, k, C.kb, C.s, pm, pk, C.q, nullptr, SLOT_PQ);
+      phase_col_e<K>(C, sm, sred, E_CG, al, k, C.kb, C.s, pm, pk, C.q, nullptr, SLOT_PQ);
       NLINV_SYNC();
-      phase_upd<K>(C, sm, sred, k, k == F.K - 1, pk);
+      phase_upd<K>(C, sm, sred, k, k == Kcg - 1, pk);
       NLINV_SYNC();
     }
   }
@@ -155,8 +212,34 @@ __global__ void __launch_bounds__(K::BS, K::MINB) k_frame(Ctx C, FrameArgs F) {
   NLINV_SYNC();
   phase_row_b<K>(C, sm, ROW_COILONLY, C.h, nullptr, nullptr, nullptr, nullptr);
   NLINV_SYNC();
-  phase_final(C, F.xout, F.rho_out, F.img_out);
+  phase_final(C, io.xout, io.rho_out, io.img_out);
 #undef NLINV_SYNC
+}
+
+// One whole NLINV frame in one cooperative launch.
+template <class K>
+__global__ void __launch_bounds__(K::BS, K::MINB) k_frame(Ctx C0, FrameArgs F) {
+  extern __shared__ float2 sm[];
+  __shared__ double sred[32];
+  const Ctx C = whole_grid(C0);
+  frame_body<K>(C, sm, sred, F.io, F.M, F.K, F.damping, F.alpha);
+}
+
+// Several independent frames of one size in one cooperative launch: the CTAs
+// are split into one contiguous group per frame; each group runs its frame
+// on its own workspace, all groups step through the phases together.
+template <class K>
+__global__ void __launch_bounds__(K::BS, K::MINB) k_batch(Ctx C0, BatchArgs B) {
+  extern __shared__ float2 sm[];
+  __shared__ double sred[32];
+  const int nf = B.nf;
+  const int f = (int)(((long long)blockIdx.x * nf) / gridDim.x);
+  const int lo = (int)(((long long)f * gridDim.x + nf - 1) / nf);
+  const int hi = (int)(((long long)(f + 1) * gridDim.x + nf - 1) / nf);
+  Ctx C = frame_ctx(C0, (size_t)f * B.fstride);
+  C.bid = blockIdx.x - lo;
+  C.nb = hi - lo;
+  frame_body<K>(C, sm, sred, B.io[f], B.M, B.K, B.damping, B.alpha);
 }
 
 // bounded wait on a device flag (used to test the timeout path)
@@ -300,12 +383,17 @@ struct nlinv_plan_s {
   int N, G, Gc, J, U;
   long long nx;
   int dev, nsm;
+  int max_batch = 1;
+  size_t fstride = 0;         // bytes between the per-frame workspaces
   void* mem = nullptr;
   void* prep = nullptr;
   size_t prep_bytes = 0;
-  Ctx C;
+  Ctx C;                      // frame 0's workspace
   float* psf;
-  int coop_grid = 0;
+  int coop_grid = 0;          // co-resident CTAs of k_frame
+  int batch_occ = 0;          // co-resident CTAs per SM of k_batch
+  cudaStream_t aux = nullptr; // stream of this plan's group inside nlinv_batch
+  cudaEvent_t ev_fork = nullptr, ev_done = nullptr;
 };
 
 namespace {
@@ -329,6 +417,7 @@ int set_smem_attrs() {
     CK(cudaFuncSetAttribute(k_row_cg<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(k_upd<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(k_frame<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
+    CK(cudaFuncSetAttribute(k_batch<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
   }
   return NLINV_OK;
 }
@@ -443,6 +532,7 @@ int nlinv_default_params(nlinv_params_t* p, int N, int J) {
   p->w_l = 32.0;
   p->spin_limit = 0;
   p->exec_mode = 0;
+  p->max_batch = 1;
   return NLINV_OK;
 }
 
@@ -460,6 +550,7 @@ int nlinv_plan(nlinv_plan_t* out, const nlinv_params_t* p, const float* psf, nli
   if (!(p->alpha0 > 0.0) || !(p->q > 0.0) || p->q > 1.0 || !(p->damping >= 0.0)) return NLINV_EINVAL;
   if (!(p->w_a >= 0.0) || !(p->w_l >= 0.0)) return NLINV_EINVAL;
   if (p->exec_mode != 0 && p->exec_mode != 1) return NLINV_EINVAL;
+  if (p->max_batch < 0 || p->max_batch > kMaxBatch) return NLINV_EINVAL;
   if (psf && ((uintptr_t)psf & 3u)) return NLINV_EINVAL;
 
   cudaStream_t st = (cudaStream_t)stream;
@@ -476,6 +567,7 @@ int nlinv_plan(nlinv_plan_t* out, const nlinv_params_t* p, const float* psf, nli
   pl->Gc = Gc;
   pl->J = J;
   pl->U = p->n_turns;
+  pl->max_batch = p->max_batch > 0 ? p->max_batch : 1;
   pl->nx = (long long)N * N + (long long)J * Gc * Gc;
   pl->dev = dev;
   cudaError_t e = cudaDeviceGetAttribute(&pl->nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -484,7 +576,7 @@ int nlinv_plan(nlinv_plan_t* out, const nlinv_params_t* p, const float* psf, nli
     return cuda_fail(e, "cudaDeviceGetAttribute");
   }
 
-  // one allocation, carved into the buffers
+  // one allocation: shared tables, then max_batch per-frame workspaces
   const size_t f2 = sizeof(float2);
   const size_t nx = (size_t)pl->nx;
   size_t off[40];
@@ -497,17 +589,20 @@ int nlinv_plan(nlinv_plan_t* out, const nlinv_params_t* p, const float* psf, nli
   take(G * f2);                          // 0 tw
   take((size_t)Gc * Gc * sizeof(float)); // 1 dinv
   take((size_t)pl->U * G * G * sizeof(float));  // 2 psf
-  take((size_t)J * N * N * f2);          // 3 c
-  take((size_t)J * N * Gc * f2);         // 4 h
-  take((size_t)J * N * G * f2);          // 5 v
-  take((size_t)J * N * N * f2);          // 6 s
-  take((size_t)J * N * Gc * f2);         // 7 kb
-  for (int i = 0; i < 7; ++i) take(nx * f2);  // 8..14 xn xref xcg r q p0 p1
-  take((size_t)NSLOT * kMaxPart * sizeof(double));  // 15 part
-  take(NSLOT * (sizeof(double) + sizeof(unsigned)));  // 16 tot, cnt
-  take(sizeof(int));                     // 17 err
-  take(2 * sizeof(unsigned));            // 18 bar
+  take(sizeof(int));                     // 3 err
+  take(2 * sizeof(unsigned));            // 4 bar
+  const size_t shared_bytes = tot;
+  take((size_t)J * N * N * f2);          // 5 c
+  take((size_t)J * N * Gc * f2);         // 6 h
+  take((size_t)J * N * G * f2);          // 7 v
+  take((size_t)J * N * N * f2);          // 8 s
+  take((size_t)J * N * Gc * f2);         // 9 kb
+  for (int i = 0; i < 7; ++i) take(nx * f2);  // 10..16 xn xref xcg r q p0 p1
+  take((size_t)NSLOT * kMaxPart * sizeof(double));  // 17 part
+  take(NSLOT * (sizeof(double) + sizeof(unsigned)));  // 18 tot, cnt
   for (int i = 0; i < 2; ++i) take((size_t)J * N * Gc * f2);  // 19..20 Hr Hp
+  pl->fstride = tot - shared_bytes;
+  tot = shared_bytes + pl->fstride * (size_t)pl->max_batch;
   e = cudaMalloc(&pl->mem, tot);
   if (e != cudaSuccess) {
     delete pl;
@@ -515,6 +610,7 @@ int nlinv_plan(nlinv_plan_t* out, const nlinv_params_t* p, const float* psf, nli
   }
   char* base = (char*)pl->mem;
   Ctx& C = pl->C;
+  std::memset(&C, 0, sizeof(C));
   C.N = N;
   C.G = G;
   C.Gc = Gc;
@@ -527,23 +623,23 @@ int nlinv_plan(nlinv_plan_t* out, const nlinv_params_t* p, const float* psf, nli
   C.dinv = (const float*)(base + off[1]);
   pl->psf = (float*)(base + off[2]);
   C.psf = pl->psf;
-  C.c = (float2*)(base + off[3]);
-  C.h = (float2*)(base + off[4]);
-  C.v = (float2*)(base + off[5]);
-  C.s = (float2*)(base + off[6]);
-  C.kb = (float2*)(base + off[7]);
-  C.xn = (float2*)(base + off[8]);
-  C.xref = (float2*)(base + off[9]);
-  C.xcg = (float2*)(base + off[10]);
-  C.r = (float2*)(base + off[11]);
-  C.q = (float2*)(base + off[12]);
-  C.pb[0] = (float2*)(base + off[13]);
-  C.pb[1] = (float2*)(base + off[14]);
-  C.part = (double*)(base + off[15]);
-  C.tot = (double*)(base + off[16]);
+  C.err = (int*)(base + off[3]);
+  C.bar = (unsigned*)(base + off[4]);
+  C.c = (float2*)(base + off[5]);
+  C.h = (float2*)(base + off[6]);
+  C.v = (float2*)(base + off[7]);
+  C.s = (float2*)(base + off[8]);
+  C.kb = (float2*)(base + off[9]);
+  C.xn = (float2*)(base + off[10]);
+  C.xref = (float2*)(base + off[11]);
+  C.xcg = (float2*)(base + off[12]);
+  C.r = (float2*)(base + off[13]);
+  C.q = (float2*)(base + off[14]);
+  C.pb[0] = (float2*)(base + off[15]);
+  C.pb[1] = (float2*)(base + off[16]);
+  C.part = (double*)(base + off[17]);
+  C.tot = (double*)(base + off[18]);
   C.cnt = (unsigned*)(C.tot + NSLOT);
-  C.err = (int*)(base + off[17]);
-  C.bar = (unsigned*)(base + off[18]);
   C.Hr = (float2*)(base + off[19]);
   C.Hp = (float2*)(base + off[20]);
   C.spin_limit = pl->prm.spin_limit;
@@ -590,7 +686,13 @@ int nlinv_plan(nlinv_plan_t* out, const nlinv_params_t* p, const float* psf, nli
     int g = nbk * pl->nsm;
     if (g > kMaxPart) g = kMaxPart;
     pl->coop_grid = g;
-    return g > 0 ? NLINV_OK : NLINV_ECUDA;
+    int nbb = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nbb, k_batch<K>, K::BS, K::SMEM));
+    pl->batch_occ = nbb;
+    CK(cudaStreamCreateWithFlags(&pl->aux, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&pl->ev_done, cudaEventDisableTiming));
+    return (g > 0 && nbb > 0) ? NLINV_OK : NLINV_ECUDA;
   });
   if (rc != NLINV_OK) return fail(rc);
   *out = pl;
@@ -599,6 +701,9 @@ int nlinv_plan(nlinv_plan_t* out, const nlinv_params_t* p, const float* psf, nli
 
 int nlinv_plan_destroy(nlinv_plan_t pl) {
   if (!pl) return NLINV_EINVAL;
+  if (pl->ev_fork) cudaEventDestroy(pl->ev_fork);
+  if (pl->ev_done) cudaEventDestroy(pl->ev_done);
+  if (pl->aux) cudaStreamDestroy(pl->aux);
   cudaFree(pl->prep);
   cudaError_t e = cudaFree(pl->mem);
   delete pl;
@@ -743,12 +848,12 @@ int nlinv_frame(nlinv_plan_t pl, const void* Y, int turn, const void* x_prev, vo
   const nlinv_params_t& p = pl->prm;
   FrameArgs F;
   std::memset(&F, 0, sizeof(F));
-  F.Y = (const float2*)Y;
-  F.P = pl->psf + (size_t)turn * pl->G * pl->G;
-  F.xprev = (const float2*)x_prev;
-  F.xout = (float2*)x_out;
-  F.rho_out = (float2*)rho_out;
-  F.img_out = (float2*)img_out;
+  F.io.Y = (const float2*)Y;
+  F.io.P = pl->psf + (size_t)turn * pl->G * pl->G;
+  F.io.xprev = (const float2*)x_prev;
+  F.io.xout = (float2*)x_out;
+  F.io.rho_out = (float2*)rho_out;
+  F.io.img_out = (float2*)img_out;
   F.M = p.newton_steps;
   F.K = p.cg_iters;
   F.damping = (float)p.damping;
@@ -766,30 +871,112 @@ int nlinv_frame(nlinv_plan_t pl, const void* Y, int turn, const void* x_prev, vo
     }
     Launch<K> L{pl, st};
     const int ge = plan_grid((int)((C.nx + 255) / 256), 1);
-    k_init<<<ge, 256, 0, st>>>(C, F.xprev, F.damping);
+    k_init<<<ge, 256, 0, st>>>(C, F.io.xprev, F.damping);
     CKL("k_init");
     for (int n = 0; n < F.M; ++n) {
       const float alpha = F.alpha[n];
       RC(L.coil_y(C.xn + NN, C.h));
       RC(L.row_b(ROW_COIL, C.h, C.xn, nullptr, nullptr, C.v));
-      RC(L.col_c(COL_RHS, F.P, F.Y, nullptr, C.v));
+      RC(L.col_c(COL_RHS, F.io.P, F.io.Y, nullptr, C.v));
       RC(L.row_d(C.xn, C.v, C.s, C.kb));
       RC(L.col_e(E_RHS, alpha, 0, C.kb, C.s, nullptr, nullptr, C.r, C.Hr, SLOT_RR0));
       for (int kk = 0; kk < F.K; ++kk) {
         float2* pk = C.pb[kk & 1];
         const float2* pm = C.pb[(kk + 1) & 1];
         RC(L.row_cg(kk, pm, pk, C.v));
-        RC(L.col_c(COL_TOEP, F.P, nullptr, nullptr, C.v));
+        RC(L.col_c(COL_TOEP, F.io.P, nullptr, nullptr, C.v));
         RC(L.row_d(C.xn, C.v, C.s, C.kb));
         RC(L.col_e(E_CG, alpha, kk, C.kb, C.s, pm, pk, C.q, nullptr, SLOT_PQ));
         RC(L.upd(kk, kk == F.K - 1, pk));
       }
     }
     RC(L.coils(C.xn));
-    k_final<<<ge, 256, 0, st>>>(C, F.xout, F.rho_out, F.img_out);
+    k_final<<<ge, 256, 0, st>>>(C, F.io.xout, F.io.rho_out, F.io.img_out);
     CKL("k_final");
     return NLINV_OK;
   });
+}
+
+int nlinv_batch(const nlinv_frame_desc_t* frames, int nframes, nlinv_stream_t stream) {
+  if (!frames || nframes <= 0) return NLINV_EINVAL;
+  // group the frames by plan, keeping their order
+  std::vector<nlinv_plan_s*> plans;
+  std::vector<std::vector<int>> members;
+  for (int i = 0; i < nframes; ++i) {
+    const nlinv_frame_desc_t& d = frames[i];
+    nlinv_plan_s* pl = d.plan;
+    if (!pl) return NLINV_EINVAL;
+    if (!d.Y || !d.x_out || !aligned8(d.Y) || !aligned8(d.x_out)) return NLINV_EINVAL;
+    if ((d.x_prev && !aligned8(d.x_prev)) || (d.rho_out && !aligned8(d.rho_out)) ||
+        (d.img_out && !aligned8(d.img_out)))
+      return NLINV_EINVAL;
+    if (d.turn < 0 || d.turn >= pl->U) return NLINV_EINVAL;
+    size_t g = 0;
+    while (g < plans.size() && plans[g] != pl) ++g;
+    if (g == plans.size()) {
+      plans.push_back(pl);
+      members.emplace_back();
+    }
+    members[g].push_back(i);
+  }
+  double wsum = 0.0;
+  std::vector<double> w(plans.size());
+  for (size_t g = 0; g < plans.size(); ++g) {
+    nlinv_plan_s* pl = plans[g];
+    if ((int)members[g].size() > pl->max_batch) return NLINV_EINVAL;
+    if (pl->dev != plans[0]->dev || pl->nsm != plans[0]->nsm) return NLINV_EINVAL;
+    w[g] = (double)members[g].size() * pl->J * (double)pl->G * pl->G * std::log2((double)pl->G);
+    wsum += w[g];
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool fork = plans.size() > 1;
+  if (fork) CK(cudaEventRecord(plans[0]->ev_fork, st));
+  const int nsm = plans[0]->nsm;
+  for (size_t g = 0; g < plans.size(); ++g) {
+    nlinv_plan_s* pl = plans[g];
+    const nlinv_params_t& p = pl->prm;
+    BatchArgs B;
+    std::memset(&B, 0, sizeof(B));
+    B.nf = (int)members[g].size();
+    B.M = p.newton_steps;
+    B.K = p.cg_iters;
+    B.damping = (float)p.damping;
+    for (int n = 0; n < B.M; ++n) B.alpha[n] = (float)(p.alpha0 * std::pow(p.q, n));
+    B.fstride = pl->fstride;
+    for (int f = 0; f < B.nf; ++f) {
+      const nlinv_frame_desc_t& d = frames[members[g][f]];
+      B.io[f].Y = (const float2*)d.Y;
+      B.io[f].P = pl->psf + (size_t)d.turn * pl->G * pl->G;
+      B.io[f].xprev = (const float2*)d.x_prev;
+      B.io[f].xout = (float2*)d.x_out;
+      B.io[f].rho_out = (float2*)d.rho_out;
+      B.io[f].img_out = (float2*)d.img_out;
+    }
+    // this group's share of the SMs, at least one CTA per frame
+    int sms = fork ? (int)std::lround(nsm * w[g] / wsum) : nsm;
+    if (sms < 1) sms = 1;
+    int grid = sms * pl->batch_occ;
+    if (grid < B.nf) grid = B.nf;
+    if (grid > pl->batch_occ * nsm) grid = pl->batch_occ * nsm;
+    if (grid < B.nf) return NLINV_EINVAL;
+    cudaStream_t gs = fork ? pl->aux : st;
+    if (fork) CK(cudaStreamWaitEvent(gs, plans[0]->ev_fork, 0));
+    Ctx C = pl->C;
+    const int rc = dispatch(pl->G, [&](auto k) -> int {
+      using K = decltype(k);
+      CK(cudaMemsetAsync(C.bar, 0, 2 * sizeof(unsigned), gs));
+      void* args[] = {(void*)&C, (void*)&B};
+      CK(cudaLaunchCooperativeKernel((const void*)k_batch<K>, dim3(grid), dim3(K::BS), args,
+                                     (size_t)K::SMEM, gs));
+      return NLINV_OK;
+    });
+    if (rc != NLINV_OK) return rc;
+    if (fork) {
+      CK(cudaEventRecord(pl->ev_done, gs));
+      CK(cudaStreamWaitEvent(st, pl->ev_done, 0));
+    }
+  }
+  return NLINV_OK;
 }
 
 int nlinv_sync(nlinv_plan_t pl, nlinv_stream_t stream) {

@@ -72,8 +72,9 @@ struct Ctx {
   double* tot;          // [NSLOT] totals, written by the last CTA of the producer
   unsigned* cnt;        // [NSLOT] arrival counters of the producer (self-resetting)
   int* err;             // latched device error
-  unsigned* bar;        // grid barrier {count, generation}
+  unsigned* bar;        // grid barrier counter
   long long spin_limit;
+  int bid, nb;          // this CTA's index within the CTAs working on this frame, and their count
 };
 
 template <int G1_, int G2_> struct Cfg {
@@ -137,15 +138,15 @@ __device__ __forceinline__ void block_partial(const Ctx& C, double v, int slot, 
     const int nw = blockDim.x >> 5;
     double a = 0.0;
     for (int i = 0; i < nw; ++i) a += sred[i];
-    C.part[slot * kMaxPart + blockIdx.x] = a;
+    C.part[slot * kMaxPart + C.bid] = a;
     __threadfence();
-    s_last = (atomicAdd(C.cnt + slot, 1u) == gridDim.x - 1);
+    s_last = (atomicAdd(C.cnt + slot, 1u) == (unsigned)C.nb - 1);
   }
   __syncthreads();
   if (s_last && w == 0) {
     __threadfence();
     double a = 0.0;
-    for (int i = l; i < (int)gridDim.x; i += 32) a += __ldcg(C.part + slot * kMaxPart + i);
+    for (int i = l; i < C.nb; i += 32) a += __ldcg(C.part + slot * kMaxPart + i);
     a = warp_sum(a);
     if (l == 0) {
       C.tot[slot] = a;
@@ -170,7 +171,7 @@ __device__ NLINV_PHASE void phase_coil_y(const Ctx& C, float2* sm, const float2*
   const int t = threadIdx.x;
   const int tiles = (Gc + TW - 1) / TW;
   const int items = J * tiles;
-  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+  for (int it = C.bid; it < items; it += C.nb) {
     const int j = it / tiles;
     const int fx = (it - j * tiles) * TW + (t % TW);
     const bool colok = fx < Gc;
@@ -233,7 +234,7 @@ __device__ NLINV_PHASE void phase_row_b(const Ctx& C, float2* sm, int mode, cons
   const int t = threadIdx.x;
   const int groups = (N + TW - 1) / TW;
   const int items = J * groups;
-  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+  for (int it = C.bid; it < items; it += C.nb) {
     const int j = it / groups;
     const int y0 = (it - j * groups) * TW;
     if (mode != ROW_IMG) {  // stage 1: thread (row, n1): inverse DFT over n2
@@ -342,7 +343,7 @@ __device__ NLINV_PHASE void phase_row_cg(const Ctx& C, float2* sm, double* sred,
   const Scal2 beta = split(beta64);
   const int groups = (N + TW - 1) / TW;
   const int items = J * groups;
-  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+  for (int it = C.bid; it < items; it += C.nb) {
     const int j = it / groups;
     const int y0 = (it - j * groups) * TW;
     {  // stage 1: thread (row, n1): direction update of H p, inverse DFT over n2
@@ -433,7 +434,7 @@ __device__ NLINV_PHASE void phase_col_c(const Ctx& C, float2* sm, int mode, cons
   const int t = threadIdx.x;
   constexpr int tiles = (G + TW - 1) / TW;
   const int items = J * tiles;
-  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+  for (int it = C.bid; it < items; it += C.nb) {
     const int j = it / tiles;
     const int x = (it - j * tiles) * TW + (t % TW);
     const bool colok = x < G;
@@ -522,7 +523,7 @@ __device__ NLINV_PHASE void phase_row_d(const Ctx& C, float2* sm, const float2* 
   const int t = threadIdx.x;
   const int groups = (N + TW - 1) / TW;
   const int items = J * groups;
-  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+  for (int it = C.bid; it < items; it += C.nb) {
     const int j = it / groups;
     const int y0 = (it - j * groups) * TW;
     {  // stage 1: thread (row, n1): inverse DFT over n2
@@ -616,7 +617,7 @@ __device__ NLINV_PHASE void phase_col_e(const Ctx& C, float2* sm, double* sred, 
   const int tiles = (Gc + TW - 1) / TW;
   const int items = J * tiles;
   float acc = 0.f;   // this thread's few terms; CTA and grid sums in FP64
-  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+  for (int it = C.bid; it < items; it += C.nb) {
     const int j = it / tiles;
     const int fx = (it - j * tiles) * TW + (t % TW);
     const bool colok = fx < Gc;
@@ -706,7 +707,7 @@ __device__ NLINV_PHASE void phase_col_e(const Ctx& C, float2* sm, double* sred, 
     __syncthreads();
   }
   // rho part: channel sum of s_j = conj(c_j) t_j
-  for (int e = blockIdx.x * blockDim.x + t; e < NN; e += gridDim.x * blockDim.x) {
+  for (int e = C.bid * blockDim.x + t; e < NN; e += C.nb * blockDim.x) {
     float2 sv = czero();
     for (int j = 0; j < J; ++j) sv = cadd(sv, ldcg(sin + (size_t)j * NN + e));
     if (mode == E_CG) {
@@ -743,7 +744,7 @@ __device__ NLINV_PHASE void phase_upd(const Ctx& C, float2* sm, double* sred, in
   const double rr = slot_total(C, (k & 1) ? SLOT_RR1 : SLOT_RR0);
   const double pq = slot_total(C, SLOT_PQ);
   const double a64 = cg_step(rr, pq);
-  if (rr > 0.0 && a64 == 0.0 && blockIdx.x == 0 && t == 0) raise_err(C, DEV_ENUMERIC);
+  if (rr > 0.0 && a64 == 0.0 && C.bid == 0 && t == 0) raise_err(C, DEV_ENUMERIC);
   const Scal2 a = split(a64), na = split(-a64);
   float acc = 0.f;   // this thread's few terms; CTA and grid sums in FP64
   auto update = [&](size_t e) -> float2 {
@@ -758,7 +759,7 @@ __device__ NLINV_PHASE void phase_upd(const Ctx& C, float2* sm, double* sred, in
   };
   const int tiles = (Gc + TW - 1) / TW;
   const int items = J * tiles;
-  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+  for (int it = C.bid; it < items; it += C.nb) {
     const int j = it / tiles;
     const int fx = (it - j * tiles) * TW + (t % TW);
     const bool colok = fx < Gc;
@@ -802,15 +803,15 @@ __device__ NLINV_PHASE void phase_upd(const Ctx& C, float2* sm, double* sred, in
       __syncthreads();
     }
   }
-  for (int e = blockIdx.x * blockDim.x + t; e < NN; e += gridDim.x * blockDim.x) update((size_t)e);
+  for (int e = C.bid * blockDim.x + t; e < NN; e += C.nb * blockDim.x) update((size_t)e);
   block_partial(C, (double)acc, (k & 1) ? SLOT_RR0 : SLOT_RR1, sred);
 }
 
 // x^_0 = x_prev (or rho = 1, c^ = 0), x_ref = damping * x_prev
 __device__ __forceinline__ void phase_init(const Ctx& C, const float2* xprev, float damping) {
   const int NN = C.N * C.N;
-  if (blockIdx.x == 0 && threadIdx.x < NSLOT) C.cnt[threadIdx.x] = 0u;   // fresh reductions
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < C.nx; e += gridDim.x * blockDim.x) {
+  if (C.bid == 0 && threadIdx.x < NSLOT) C.cnt[threadIdx.x] = 0u;   // fresh reductions
+  for (int e = C.bid * blockDim.x + threadIdx.x; e < C.nx; e += C.nb * blockDim.x) {
     float2 v = xprev ? ldcg(xprev + e) : make_float2(e < NN ? 1.f : 0.f, 0.f);
     C.xn[e] = v;
     C.xref[e] = cscale(v, damping);
@@ -820,7 +821,7 @@ __device__ __forceinline__ void phase_init(const Ctx& C, const float2* xprev, fl
 // outputs: x^ copy, rho, rho * sqrt(sum_j |c_j|^2)
 __device__ __forceinline__ void phase_final(const Ctx& C, float2* xout, float2* rho_out, float2* img_out) {
   const int NN = C.N * C.N;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < C.nx; e += gridDim.x * blockDim.x) {
+  for (int e = C.bid * blockDim.x + threadIdx.x; e < C.nx; e += C.nb * blockDim.x) {
     const float2 v = ldcg(C.xn + e);
     if (xout) xout[e] = v;
     if (e < NN) {

@@ -41,6 +41,15 @@ class nlinv_params_t(ctypes.Structure):
         ("alpha0", ctypes.c_double), ("q", ctypes.c_double), ("damping", ctypes.c_double),
         ("w_a", ctypes.c_double), ("w_l", ctypes.c_double),
         ("spin_limit", ctypes.c_longlong), ("exec_mode", ctypes.c_int),
+        ("max_batch", ctypes.c_int),
+    ]
+
+
+class nlinv_frame_desc_t(ctypes.Structure):
+    _fields_ = [
+        ("plan", ctypes.c_void_p), ("Y", ctypes.c_void_p), ("turn", ctypes.c_int),
+        ("x_prev", ctypes.c_void_p), ("x_out", ctypes.c_void_p), ("rho_out", ctypes.c_void_p),
+        ("img_out", ctypes.c_void_p),
     ]
 
 
@@ -63,6 +72,7 @@ _SIGS = {
     "nlinv_frame": (_I, [_VP, _VP, _I, _VP, _VP, _VP, _VP, _VP]),
     "nlinv_apply_normal_static": (_I, [_I, _I, _I, ctypes.c_double, ctypes.c_double, _VP, _VP, _VP,
                                        ctypes.c_double, _VP, _VP]),
+    "nlinv_batch": (_I, [ctypes.POINTER(nlinv_frame_desc_t), _I, _VP]),
     "nlinv_wait_flag": (_I, [_VP, _VP, _I, ctypes.c_longlong, _VP]),
     "nlinv_sync": (_I, [_VP, _VP]),
     "nlinv_strerror": (ctypes.c_char_p, [_I]),
@@ -232,6 +242,23 @@ def nlinv_frame(plan: Plan, Y, turn: int, x_prev, x_out, rho_out=None, img_out=N
                               _ptr(rho_out, numel=NN, name="rho_out"),
                               _ptr(img_out, numel=NN, name="img_out"),
                               _stream(stream)), "nlinv_frame")
+
+
+def nlinv_batch(frames, stream=None):
+    """frames: list of dicts with keys plan, Y, turn, x_prev (tensor or None),
+    x_out, and optionally rho_out, img_out."""
+    arr = (nlinv_frame_desc_t * len(frames))()
+    for i, f in enumerate(frames):
+        pl = f["plan"]
+        NN = pl.N * pl.N
+        arr[i].plan = pl.handle
+        arr[i].Y = _ptr(f["Y"], numel=pl.J * pl.G * pl.G, name="Y")
+        arr[i].turn = int(f.get("turn", 0))
+        arr[i].x_prev = _ptr(f.get("x_prev"), numel=pl.nx, name="x_prev")
+        arr[i].x_out = _ptr(f["x_out"], numel=pl.nx, name="x_out")
+        arr[i].rho_out = _ptr(f.get("rho_out"), numel=NN, name="rho_out")
+        arr[i].img_out = _ptr(f.get("img_out"), numel=NN, name="img_out")
+    _check(_lib().nlinv_batch(arr, len(frames), _stream(stream)), "nlinv_batch")
 
 
 def nlinv_wait_flag(plan: Plan, flag, expected: int, spin_limit: int, stream=None):

@@ -1,0 +1,115 @@
+"""GPU parity of nlinv_batch (independent frames in flight together, the
+temporal decomposition of Sec. 3.3 / Eq. (10)) against the FP64 oracle and
+against one-frame launches, through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synth as S
+from gpu_util import make_plan, rel, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-3
+
+
+def cart_frames(N, J, n, seed):
+    return [S.cartesian_frame(N, J, seed=seed, sigma=1e-3, frame=f)[:2] for f in range(n)]
+
+
+def test_batch_of_independent_frames_matches_oracle_and_single_launches():
+    from paper_1701_08361_gb300 import nlinv as L
+    N, J, B = 64, 4, 5
+    g = O.Geometry(N=N, J=J)
+    frames = cart_frames(N, J, B, seed=11)
+    P = frames[0][1]
+    plan = make_plan(N, J, psf=P, max_batch=8)
+    # each frame starts from its own x_prev (frame 0 from the initial value)
+    xps = [None] + [O.XVec(S.random_complex((N, N), 40 + f, 0.3) + 1.0,
+                           S.random_complex((J, g.gc, g.gc), 50 + f, 20.0)) for f in range(1, B)]
+    descs, outs = [], []
+    for f, (Y, _) in enumerate(frames):
+        xo = torch.empty(plan.nx, dtype=torch.complex64, device="cuda")
+        img = torch.empty(N * N, dtype=torch.complex64, device="cuda")
+        descs.append(dict(plan=plan, Y=to_dev(Y), turn=0,
+                          x_prev=None if xps[f] is None else to_dev(xps[f].flat()),
+                          x_out=xo, img_out=img))
+        outs.append((xo, img))
+    L.nlinv_batch(descs)
+    assert L.nlinv_sync(plan) == 0
+    for f, (Y, _) in enumerate(frames):
+        x0 = O.XVec.initial(g) if xps[f] is None else xps[f]
+        ref = O.nlinv_frame(Y, P, x0, x0, g, O.Params())
+        assert rel(to_np(outs[f][0]), ref.flat()) <= TOL, f
+        assert rel(to_np(outs[f][1]), O.image(ref, g)) <= TOL, f
+        # the same frame alone
+        xs = torch.empty(plan.nx, dtype=torch.complex64, device="cuda")
+        L.nlinv_frame(plan, descs[f]["Y"], 0, descs[f]["x_prev"], xs)
+        assert L.nlinv_sync(plan) == 0
+        assert rel(to_np(outs[f][0]), to_np(xs)) <= 1e-5, f
+
+
+def test_batch_mixes_grid_sizes_and_channel_counts():
+    from paper_1701_08361_gb300 import nlinv as L
+    specs = [(32, 3, 2), (64, 4, 3), (20, 2, 1)]
+    plans, descs, refs = [], [], []
+    for i, (N, J, nf) in enumerate(specs):
+        g = O.Geometry(N=N, J=J)
+        frames = cart_frames(N, J, nf, seed=100 + i)
+        P = frames[0][1]
+        plan = make_plan(N, J, psf=P, max_batch=nf, newton_steps=5, cg_iters=8)
+        plans.append(plan)
+        for f, (Y, _) in enumerate(frames):
+            xo = torch.empty(plan.nx, dtype=torch.complex64, device="cuda")
+            descs.append(dict(plan=plan, Y=to_dev(Y), turn=0, x_prev=None, x_out=xo))
+            refs.append((g, O.nlinv_frame(Y, P, O.XVec.initial(g), O.XVec.initial(g), g,
+                                          O.Params(newton_steps=5, cg_iters=8))))
+    L.nlinv_batch(descs)
+    for pl in plans:
+        assert L.nlinv_sync(pl) == 0
+    for d, (g, ref) in zip(descs, refs):
+        assert rel(to_np(d["x_out"]), ref.flat()) <= TOL
+
+
+def test_scheduled_radial_stream_matches_oracle_stream():
+    """8 radial frames (N=64, 4 coils, 13 spokes, 5 turns): frames 0..2 in
+    order, then 3 in flight at a time, each from the most recent finished
+    frame (Eq. (10) with o = 3)."""
+    from paper_1701_08361_gb300 import nlinv as L
+    from paper_1701_08361_gb300 import stream as ST
+    N, J, K, U, NF, D, WU = 64, 4, 13, 5, 8, 3, 2
+    g = O.Geometry(N=N, J=J)
+    plan = make_plan(N, J, turns=U, max_batch=D)
+    frames_o, Ys, turns = [], [], []
+    coils = S.coil_maps(N, J, 9)
+    for n in range(NF):
+        kx, ky, y, _, _ = S.radial_frame(N, J, K, U, n, seed=9, coils=coils)
+        frames_o.append((O.grid_data(kx, ky, y, N, g.G), O.psf_kernel(kx, ky, N, g.G).real))
+        kxy = torch.tensor(np.stack([kx, ky], 1), dtype=torch.float64, device="cuda")
+        if n < U:
+            L.nlinv_psf(plan, n, kxy)
+        Yd = torch.empty(J * g.G * g.G, dtype=torch.complex64, device="cuda")
+        L.nlinv_grid(plan, kxy, to_dev(y), Yd)
+        Ys.append(Yd)
+        turns.append(n % U)
+    xs = torch.empty((NF, plan.nx), dtype=torch.complex64, device="cuda")
+    ST.run([dict(plan=plan, Y=Ys, turns=turns, delay=D, warmup=WU, x=xs)])
+    assert L.nlinv_sync(plan) == 0
+    ref = O.nlinv_stream(frames_o, g, O.Params(), delay=D, warmup=WU)
+    for n in range(NF):
+        assert rel(to_np(xs[n]), ref[n].flat()) <= TOL, n
+
+
+def test_batch_rejects_more_frames_than_the_plan_holds():
+    from paper_1701_08361_gb300 import nlinv as L
+    plan = make_plan(8, 2, psf=np.ones((16, 16)), max_batch=2)
+    Y = torch.zeros(2 * 16 * 16, dtype=torch.complex64, device="cuda")
+    frames = [dict(plan=plan, Y=Y, turn=0, x_prev=None,
+                   x_out=torch.empty(plan.nx, dtype=torch.complex64, device="cuda")) for _ in range(3)]
+    with pytest.raises(L.NlinvError) as e:
+        L.nlinv_batch(frames)
+    assert e.value.code == L.NLINV_EINVAL
+    frames[0]["turn"] = 1
+    with pytest.raises(L.NlinvError):
+        L.nlinv_batch(frames[:2])

@@ -139,7 +139,15 @@ def test_noiseless_phantom_recovery_cartesian():
 
 def test_schedule_source_frames():
     assert [O.source_frame(n, 1, 0) for n in range(5)] == [-1, 0, 1, 2, 3]
-    assert [O.source_frame(n, 3, 2) for n in range(7)] == [-1, 0, 1, 0, 1, 2, 3]
+    assert [O.source_frame(n, 1, 3) for n in range(6)] == [-1, 0, 1, 2, 3, 4]
+    # warm-up 0..2 in order, then groups {3,4,5} -> 2, {6,7,8} -> 5, {9} -> 8
+    assert [O.source_frame(n, 3, 2) for n in range(10)] == [-1, 0, 1, 2, 2, 2, 5, 5, 5, 8]
+    # every source lies in the window [n - delay, n - 1] of Eq. (10)
+    for D in (1, 2, 5, 11):
+        for l in (0, 1, 5):
+            for n in range(l + 1, 60):
+                s = O.source_frame(n, D, l)
+                assert n - D <= s <= n - 1
 
 
 def test_stream_delay_one_is_sequential():
