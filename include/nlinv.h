@@ -189,6 +189,27 @@ typedef struct {
  * another frame's x_out of the same call. */
 int nlinv_batch(const nlinv_frame_desc_t* frames, int nframes, nlinv_stream_t stream);
 
+/* Change alpha_0 of the plan's schedule alpha_n = alpha0 q^n (alpha0 > 0);
+ * applies to calls issued afterwards. */
+int nlinv_set_alpha0(nlinv_plan_t plan, double alpha0);
+
+/* Reverse-mode derivative of nlinv_frame through the unrolled IRGNM / CG
+ * (Sec. 2.2, Eqs. 2-5: every Newton step and CG iteration exactly as
+ * computed, with the data-dependent step lengths), recomputing each Newton
+ * step from its checkpoint x^_n.  With gbar = dL/dx^_M (device [n_x]; for
+ * complex vectors the gradient of a real L is dL/dRe + i dL/dIm):
+ *   Ybar_out       device [J][G][G] complex64: dL/dY
+ *   alpha0_bar_out host double: dL/dalpha_0 (alpha_n = alpha0 q^n), or NULL
+ *   xprev_bar_out  device [n_x]: dL/dx_prev through the initial value and
+ *                  the regulariser x_ref = damping x_prev, or NULL (zero
+ *                  when x_prev is NULL).
+ * Y, turn and x_prev as in nlinv_frame.  Uses a plan-owned workspace that
+ * is allocated on first use; reads scalars back, so the call returns after
+ * the work on `stream` is complete. */
+int nlinv_frame_vjp(nlinv_plan_t plan, const void* Y, int turn, const void* x_prev,
+                    const void* gbar, void* Ybar_out, double* alpha0_bar_out,
+                    void* xprev_bar_out, nlinv_stream_t stream);
+
 /* Bounded device-side wait until *flag == expected (flag: device int),
  * polling at most spin_limit times; on expiry the plan latches
  * NLINV_ETIMEOUT, which nlinv_sync() returns.  This is the wait primitive of

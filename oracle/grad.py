@@ -106,8 +106,9 @@ def cg_vjp(tape, xbar: XVec, apply):
 
 def frame_vjp(Y: np.ndarray, P: np.ndarray, x_init: XVec, x_ref: XVec, geom: Geometry,
               prm: Params, gbar: XVec):
-    """Gradients of L with dL/dx^_M = gbar w.r.t. Y (complex, [J,G,G]) and
-    alpha_0 (real), through the unrolled frame of nlinv.nlinv_frame."""
+    """Gradients of L with dL/dx^_M = gbar w.r.t. Y (complex, [J,G,G]),
+    alpha_0 (real), the initial value x_init and the regulariser x_ref,
+    through the unrolled frame of nlinv.nlinv_frame."""
     M = prm.newton_steps
     ckpt = [x_init.copy()]
     for n in range(M):           # forward, checkpoint x^_n
@@ -119,6 +120,7 @@ def frame_vjp(Y: np.ndarray, P: np.ndarray, x_init: XVec, x_ref: XVec, geom: Geo
     Ybar = np.zeros_like(Y)
     alpha0_bar = 0.0
     xbar = gbar.copy()
+    xref_bar = _zero_like(gbar)
     for n in reversed(range(M)):
         x = ckpt[n]
         alpha = prm.alpha0 * prm.q ** n
@@ -138,5 +140,6 @@ def frame_vjp(Y: np.ndarray, P: np.ndarray, x_init: XVec, x_ref: XVec, geom: Geo
         Ybar = Ybar + DF(x, bbar, geom)
         alpha_bar -= dot(bbar, x - x_ref)
         alpha0_bar += prm.q ** n * alpha_bar
+        xref_bar = xref_bar + bbar.scale(alpha)
         xbar = xb_n
-    return Ybar, alpha0_bar, xbar
+    return Ybar, alpha0_bar, xbar, xref_bar

@@ -1133,3 +1133,399 @@ extern "C" int nlinv_apply_normal_static(int N, int J, int Gc, double w_a, doubl
     return L.col_e(E_NORMAL, (float)alpha, 0, C.kb, C.s, nullptr, (float2*)d, (float2*)out, nullptr, SLOT_PQ);
   });
 }
+
+// ======================================================================
+// Reverse-mode derivative of one frame through the unrolled IRGNM / CG
+// (Sec. 2.2, Eqs. (2)-(5)).  F^ is bilinear with the symmetric form
+// B(x, d) = DF(x)[d], so every derivative is DF / DF^H at some
+// linearisation point:
+//   A(x) p = DF(x)^H P DF(x) p + alpha p
+//     -> x-bar += DF(qbar)^H P DF(x) p + DF(p)^H P DF(x) qbar
+//   b(x) = DF(x)^H z - alpha (x - x_ref),  z = Y - P F^(x),  F^(x) = B(x, x) / 2
+//     -> x-bar += DF(bbar)^H z - DF(x)^H P DF(x) bbar - alpha bbar
+//        Y-bar += DF(x) bbar,  alpha-bar -= <bbar, x - x_ref>_R,  x_ref-bar += alpha bbar
+// The CG of each Newton step is recomputed from its checkpoint x^_n and
+// reversed step by step; scalars are handled on the host in FP64.
+namespace {
+
+// y = a x + b y  (a as a float pair; b == 0 overwrites y)
+__global__ void k_axpby(long long n, float2* y, const float2* x, float ahi, float alo, float b) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float2 xv = x[i];
+    float2 base = make_float2(0.f, 0.f);
+    if (b != 0.f) {
+      const float2 yv = y[i];
+      base = make_float2(b * yv.x, b * yv.y);
+    }
+    y[i] = make_float2(fmaf(ahi, xv.x, fmaf(alo, xv.x, base.x)), fmaf(ahi, xv.y, fmaf(alo, xv.y, base.y)));
+  }
+}
+
+// per-block FP64 partials of Re <u, v>
+__global__ void k_dot_part(long long n, const float2* u, const float2* v, double* part) {
+  __shared__ double sw[32];
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float2 a = u[i], b = v[i];
+    acc = fma((double)a.x, (double)b.x, fma((double)a.y, (double)b.y, acc));
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += sw[w];
+    part[blockIdx.x] = a;
+  }
+}
+
+__global__ void k_dot_final(int np, const double* part, double* out) {
+  if (threadIdx.x != 0) return;
+  double a = 0.0;
+  for (int i = 0; i < np; ++i) a += part[i];
+  *out = a;
+}
+
+// z <- s P z on [J][G][G]
+__global__ void k_psf_scale(int J, int G, float2* z, const float* __restrict__ P, float s) {
+  const long long n = (long long)J * G * G, g2 = (long long)G * G;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    z[i] = cscale(z[i], s * P[i % g2]);
+}
+
+// z <- Y - s P z
+__global__ void k_resid(int J, int G, float2* z, const float2* __restrict__ Y, const float* __restrict__ P, float s) {
+  const long long n = (long long)J * G * G, g2 = (long long)G * G;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float pk = s * P[i % g2];
+    const float2 zv = z[i], yv = Y[i];
+    z[i] = make_float2(fmaf(-pk, zv.x, yv.x), fmaf(-pk, zv.y, yv.y));
+  }
+}
+
+__global__ void k_init_x(int nx, int NN, float2* x) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nx; i += gridDim.x * blockDim.x)
+    x[i] = make_float2(i < NN ? 1.f : 0.f, 0.f);
+}
+
+constexpr int kDotBlocks = 256;
+
+struct GradOps {
+  nlinv_plan_s* pl;
+  cudaStream_t st;
+  const float* P;
+  long long nx, nk;
+  double* part;   // [kDotBlocks]
+  double* dres;   // device scalar
+
+  int grid(long long n) const {
+    long long g = (n + 255) / 256;
+    return (int)(g > 1024 ? 1024 : (g < 1 ? 1 : g));
+  }
+  int axpby(float2* y, const float2* x, double a, double b, long long n) const {
+    const float hi = (float)a, lo = (float)(a - (double)hi);
+    k_axpby<<<grid(n), 256, 0, st>>>(n, y, x, hi, lo, (float)b);
+    CKL("k_axpby");
+    return NLINV_OK;
+  }
+  int copy(float2* y, const float2* x, long long n) const {
+    CK(cudaMemcpyAsync(y, x, (size_t)n * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+    return NLINV_OK;
+  }
+  int zero(float2* y, long long n) const {
+    CK(cudaMemsetAsync(y, 0, (size_t)n * sizeof(float2), st));
+    return NLINV_OK;
+  }
+  int dot(const float2* u, const float2* v, long long n, double* out) const {
+    k_dot_part<<<kDotBlocks, 256, 0, st>>>(n, u, v, part);
+    CKL("k_dot_part");
+    k_dot_final<<<1, 32, 0, st>>>(kDotBlocks, part, dres);
+    CKL("k_dot_final");
+    CK(cudaMemcpyAsync(out, dres, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return NLINV_OK;
+  }
+  // z = DF(x)[d]
+  int DF(const float2* x, const float2* d, float2* z) const {
+    const size_t NN = (size_t)pl->N * pl->N;
+    return dispatch(pl->G, [&](auto k) -> int {
+      using K = decltype(k);
+      Launch<K> L{pl, st};
+      RC(L.coils(x));
+      RC(L.coil_y(d + NN, pl->C.h));
+      RC(L.row_b(ROW_LIN, pl->C.h, x, d, nullptr, pl->C.v));
+      return L.col_c(COL_FWD, nullptr, nullptr, z, pl->C.v);
+    });
+  }
+  // out = DF(w)^H z
+  int DFH(const float2* w, const float2* z, float2* out) const {
+    return dispatch(pl->G, [&](auto k) -> int {
+      using K = decltype(k);
+      Launch<K> L{pl, st};
+      RC(L.coils(w));
+      RC(L.col_c(COL_INV, nullptr, z, nullptr, pl->C.v));
+      RC(L.row_d(w, pl->C.v, pl->C.s, pl->C.kb));
+      return L.col_e(E_DFH, 0.f, 0, pl->C.kb, pl->C.s, nullptr, nullptr, out, nullptr, SLOT_PQ);
+    });
+  }
+  // out = (DF(x)^H P DF(x) + alpha) d
+  int normal(const float2* x, const float2* d, double alpha, float2* out) const {
+    const size_t NN = (size_t)pl->N * pl->N;
+    return dispatch(pl->G, [&](auto k) -> int {
+      using K = decltype(k);
+      Launch<K> L{pl, st};
+      RC(L.coils(x));
+      RC(L.coil_y(d + NN, pl->C.h));
+      RC(L.row_b(ROW_LIN, pl->C.h, x, d, nullptr, pl->C.v));
+      RC(L.col_c(COL_TOEP, P, nullptr, nullptr, pl->C.v));
+      RC(L.row_d(x, pl->C.v, pl->C.s, pl->C.kb));
+      return L.col_e(E_NORMAL, (float)alpha, 0, pl->C.kb, pl->C.s, nullptr, (float2*)d, out, nullptr, SLOT_PQ);
+    });
+  }
+  int psf(float2* z, float s) const {
+    k_psf_scale<<<grid(nk), 256, 0, st>>>(pl->J, pl->G, z, P, s);
+    CKL("k_psf_scale");
+    return NLINV_OK;
+  }
+  int resid(float2* z, const float2* Y) const {   // z <- Y - P z / 2
+    k_resid<<<grid(nk), 256, 0, st>>>(pl->J, pl->G, z, Y, P, 0.5f);
+    CKL("k_resid");
+    return NLINV_OK;
+  }
+};
+
+struct GradWS {
+  float2 *ck, *b, *z, *zt, *tp, *tq, *tr, *xb, *xbn, *pbar, *rbar, *qbar, *pb, *t1, *xref, *xrefbar, *xcg;
+  double *part, *dres;
+};
+
+int grad_workspace(nlinv_plan_s* pl, GradWS& w) {
+  const int M = pl->prm.newton_steps, Kc = pl->prm.cg_iters;
+  const size_t nx = (size_t)pl->nx, nk = (size_t)pl->J * pl->G * pl->G;
+  const size_t vb = align_up(nx * sizeof(float2)), kb = align_up(nk * sizeof(float2));
+  const size_t need = vb * ((M + 1) + 1 + Kc + Kc + (Kc + 1) + 10) + 2 * kb + align_up((kDotBlocks + 1) * sizeof(double));
+  RC(ensure_prep(pl, need));
+  char* p = (char*)pl->prep;
+  auto vec = [&](size_t count) {
+    float2* r = (float2*)p;
+    p += vb * count;
+    return r;
+  };
+  w.ck = vec(M + 1);
+  w.b = vec(1);
+  w.tp = vec(Kc > 0 ? Kc : 1);
+  w.tq = vec(Kc > 0 ? Kc : 1);
+  w.tr = vec(Kc + 1);
+  w.xb = vec(1);
+  w.xbn = vec(1);
+  w.pbar = vec(1);
+  w.rbar = vec(1);
+  w.qbar = vec(1);
+  w.pb = vec(1);
+  w.t1 = vec(1);
+  w.xref = vec(1);
+  w.xrefbar = vec(1);
+  w.xcg = vec(1);
+  w.z = (float2*)p;
+  p += kb;
+  w.zt = (float2*)p;
+  p += kb;
+  w.part = (double*)p;
+  w.dres = w.part + kDotBlocks;
+  return NLINV_OK;
+}
+
+struct CgTape {
+  int K = 0;
+  std::vector<double> a, beta, gamma, rho;
+};
+
+// b = DF(x)^H (Y - P F^(x)) - alpha (x - xref); leaves the residual in w.z
+int grad_rhs(const GradOps& O, const GradWS& w, const float2* Y, const float2* x, double alpha, float2* b) {
+  RC(O.DF(x, x, w.z));
+  RC(O.resid(w.z, Y));
+  RC(O.DFH(x, w.z, b));
+  RC(O.axpby(b, x, -alpha, 1.0, O.nx));
+  return O.axpby(b, w.xref, alpha, 1.0, O.nx);
+}
+
+// CG from zero recording p_k, q_k, r_k (k = 0..) and the scalars; delta in w.xcg
+int grad_cg(const GradOps& O, const GradWS& w, const float2* x, double alpha, const float2* b, int iters,
+            CgTape& T) {
+  const long long nx = O.nx;
+  T = CgTape();
+  float2* r0 = w.tr;
+  RC(O.copy(r0, b, nx));
+  RC(O.zero(w.xcg, nx));
+  double rr = 0.0;
+  RC(O.dot(r0, r0, nx, &rr));
+  T.rho.push_back(rr);
+  if (iters > 0) RC(O.copy(w.tp, r0, nx));
+  for (int k = 0; k < iters; ++k) {
+    if (rr == 0.0) break;
+    float2* p = w.tp + (size_t)k * (size_t)nx;
+    float2* q = w.tq + (size_t)k * (size_t)nx;
+    float2* r = w.tr + (size_t)k * (size_t)nx;
+    float2* r1 = w.tr + (size_t)(k + 1) * (size_t)nx;
+    RC(O.normal(x, p, alpha, q));
+    double pq = 0.0;
+    RC(O.dot(p, q, nx, &pq));
+    if (!(pq > 0.0) || !std::isfinite(pq)) return NLINV_ENUMERIC;
+    const double a = rr / pq;
+    RC(O.axpby(w.xcg, p, a, 1.0, nx));
+    RC(O.copy(r1, r, nx));
+    RC(O.axpby(r1, q, -a, 1.0, nx));
+    double rn = 0.0;
+    RC(O.dot(r1, r1, nx, &rn));
+    const double beta = rn / rr;
+    T.a.push_back(a);
+    T.gamma.push_back(pq);
+    T.beta.push_back(beta);
+    T.rho.push_back(rn);
+    T.K = k + 1;
+    if (k + 1 < iters) {
+      float2* p1 = w.tp + (size_t)(k + 1) * (size_t)nx;
+      RC(O.copy(p1, r1, nx));
+      RC(O.axpby(p1, p, beta, 1.0, nx));
+    }
+    rr = rn;
+  }
+  return NLINV_OK;
+}
+
+}  // namespace
+
+extern "C" int nlinv_set_alpha0(nlinv_plan_t pl, double alpha0) {
+  if (!pl || !(alpha0 > 0.0)) return NLINV_EINVAL;
+  pl->prm.alpha0 = alpha0;
+  return NLINV_OK;
+}
+
+extern "C" int nlinv_frame_vjp(nlinv_plan_t pl, const void* Y, int turn, const void* x_prev, const void* gbar,
+                               void* Ybar_out, double* alpha0_bar_out, void* xprev_bar_out,
+                               nlinv_stream_t stream) {
+  RC(check_plan(pl));
+  if (!Y || !gbar || !Ybar_out || !aligned8(Y) || !aligned8(gbar) || !aligned8(Ybar_out)) return NLINV_EINVAL;
+  if ((x_prev && !aligned8(x_prev)) || (xprev_bar_out && !aligned8(xprev_bar_out))) return NLINV_EINVAL;
+  if (turn < 0 || turn >= pl->U) return NLINV_EINVAL;
+  const nlinv_params_t& prm = pl->prm;
+  const int M = prm.newton_steps, Kc = prm.cg_iters;
+  GradWS w;
+  RC(grad_workspace(pl, w));
+  GradOps O{pl, (cudaStream_t)stream, pl->psf + (size_t)turn * pl->G * pl->G, pl->nx,
+            (long long)pl->J * pl->G * pl->G, w.part, w.dres};
+  const long long nx = O.nx, nk = O.nk;
+  const float2* Yd = (const float2*)Y;
+  // x^_0 and x_ref
+  if (x_prev) {
+    RC(O.copy(w.ck, (const float2*)x_prev, nx));
+  } else {
+    k_init_x<<<O.grid(nx), 256, 0, O.st>>>((int)nx, pl->N * pl->N, w.ck);
+    CKL("k_init_x");
+  }
+  RC(O.copy(w.xref, w.ck, nx));
+  RC(O.axpby(w.xref, w.xref, 0.0, prm.damping, nx));
+  // forward: checkpoints x^_n
+  CgTape T;
+  for (int n = 0; n < M; ++n) {
+    const float2* x = w.ck + (size_t)n * (size_t)nx;
+    float2* x1 = w.ck + (size_t)(n + 1) * (size_t)nx;
+    const double alpha = prm.alpha0 * std::pow(prm.q, n);
+    RC(grad_rhs(O, w, Yd, x, alpha, w.b));
+    RC(grad_cg(O, w, x, alpha, w.b, Kc, T));
+    RC(O.copy(x1, x, nx));
+    RC(O.axpby(x1, w.xcg, 1.0, 1.0, nx));
+  }
+  // reverse
+  float2* Ybar = (float2*)Ybar_out;
+  RC(O.zero(Ybar, nk));
+  RC(O.zero(w.xrefbar, nx));
+  RC(O.copy(w.xb, (const float2*)gbar, nx));
+  double a0bar = 0.0;
+  for (int n = M - 1; n >= 0; --n) {
+    const float2* x = w.ck + (size_t)n * (size_t)nx;
+    const double alpha = prm.alpha0 * std::pow(prm.q, n);
+    RC(grad_rhs(O, w, Yd, x, alpha, w.b));            // residual z stays in w.z
+    RC(grad_cg(O, w, x, alpha, w.b, Kc, T));
+    double alpha_bar = 0.0;
+    RC(O.copy(w.xbn, w.xb, nx));                      // x^_{n+1} = x^_n + delta
+    RC(O.zero(w.pbar, nx));
+    RC(O.zero(w.rbar, nx));
+    std::vector<double> rhobar(T.K + 1, 0.0);
+    for (int k = T.K - 1; k >= 0; --k) {
+      const float2* p = w.tp + (size_t)k * (size_t)nx;
+      const float2* q = w.tq + (size_t)k * (size_t)nx;
+      const float2* r1 = w.tr + (size_t)(k + 1) * (size_t)nx;
+      const double a = T.a[k], beta = T.beta[k], gamma = T.gamma[k];
+      const double rk = T.rho[k], rk1 = T.rho[k + 1];
+      RC(O.axpby(w.rbar, w.pbar, 1.0, 1.0, nx));      // p_{k+1} = r_{k+1} + beta p_k
+      double betabar = 0.0;
+      RC(O.dot(p, w.pbar, nx, &betabar));
+      RC(O.copy(w.pb, w.pbar, nx));
+      RC(O.axpby(w.pb, w.pb, 0.0, beta, nx));
+      rhobar[k + 1] += betabar / rk;                  // beta = rho_{k+1} / rho_k
+      rhobar[k] -= betabar * rk1 / (rk * rk);
+      RC(O.axpby(w.rbar, r1, 2.0 * rhobar[k + 1], 1.0, nx));  // rho_{k+1} = <r, r>
+      double t = 0.0;
+      RC(O.dot(q, w.rbar, nx, &t));                   // r_{k+1} = r_k - a q_k
+      double abar = -t;
+      RC(O.copy(w.qbar, w.rbar, nx));
+      RC(O.axpby(w.qbar, w.qbar, 0.0, -a, nx));
+      RC(O.dot(p, w.xb, nx, &t));                     // x_{k+1} = x_k + a p_k
+      abar += t;
+      RC(O.axpby(w.pb, w.xb, a, 1.0, nx));
+      rhobar[k] += abar / gamma;                      // a = rho_k / gamma_k
+      const double gammabar = -abar * rk / (gamma * gamma);
+      RC(O.axpby(w.pb, q, gammabar, 1.0, nx));        // gamma = <p, q>
+      RC(O.axpby(w.qbar, p, gammabar, 1.0, nx));
+      RC(O.normal(x, w.qbar, alpha, w.t1));           // q = A p
+      RC(O.axpby(w.pb, w.t1, 1.0, 1.0, nx));
+      RC(O.dot(p, w.qbar, nx, &t));                   // A depends on alpha and x^_n
+      alpha_bar += t;
+      RC(O.DF(x, p, w.zt));
+      RC(O.psf(w.zt, 1.f));
+      RC(O.DFH(w.qbar, w.zt, w.t1));
+      RC(O.axpby(w.xbn, w.t1, 1.0, 1.0, nx));
+      RC(O.DF(x, w.qbar, w.zt));
+      RC(O.psf(w.zt, 1.f));
+      RC(O.DFH(p, w.zt, w.t1));
+      RC(O.axpby(w.xbn, w.t1, 1.0, 1.0, nx));
+      std::swap(w.pbar, w.pb);
+    }
+    // p_0 = r_0 = b, rho_0 = <r_0, r_0>:  b-bar
+    RC(O.axpby(w.rbar, w.pbar, 1.0, 1.0, nx));
+    RC(O.axpby(w.rbar, w.tr, 2.0 * rhobar[0], 1.0, nx));
+    const float2* bbar = w.rbar;
+    // right-hand side
+    RC(O.DFH(bbar, w.z, w.t1));
+    RC(O.axpby(w.xbn, w.t1, 1.0, 1.0, nx));
+    RC(O.DF(x, bbar, w.zt));
+    {  // Y-bar += DF(x) b-bar
+      const float hi = 1.f;
+      k_axpby<<<O.grid(nk), 256, 0, O.st>>>(nk, Ybar, w.zt, hi, 0.f, 1.f);
+      CKL("k_axpby");
+    }
+    RC(O.psf(w.zt, 1.f));
+    RC(O.DFH(x, w.zt, w.t1));
+    RC(O.axpby(w.xbn, w.t1, -1.0, 1.0, nx));
+    RC(O.axpby(w.xbn, bbar, -alpha, 1.0, nx));
+    double t1 = 0.0, t2 = 0.0;
+    RC(O.dot(bbar, x, nx, &t1));
+    RC(O.dot(bbar, w.xref, nx, &t2));
+    alpha_bar -= (t1 - t2);
+    a0bar += std::pow(prm.q, n) * alpha_bar;
+    RC(O.axpby(w.xrefbar, bbar, alpha, 1.0, nx));
+    std::swap(w.xb, w.xbn);
+  }
+  if (alpha0_bar_out) *alpha0_bar_out = a0bar;
+  if (xprev_bar_out) {
+    if (x_prev) {
+      RC(O.copy((float2*)xprev_bar_out, w.xb, nx));
+      RC(O.axpby((float2*)xprev_bar_out, w.xrefbar, prm.damping, 1.0, nx));
+    } else {
+      RC(O.zero((float2*)xprev_bar_out, nx));
+    }
+  }
+  CK(cudaStreamSynchronize(O.st));
+  return NLINV_OK;
+}

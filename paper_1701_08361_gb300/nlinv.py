@@ -74,6 +74,8 @@ _SIGS = {
                                        ctypes.c_double, _VP, _VP]),
     "nlinv_batch": (_I, [ctypes.POINTER(nlinv_frame_desc_t), _I, _VP]),
     "nlinv_wait_flag": (_I, [_VP, _VP, _I, ctypes.c_longlong, _VP]),
+    "nlinv_set_alpha0": (_I, [_VP, ctypes.c_double]),
+    "nlinv_frame_vjp": (_I, [_VP, _VP, _I, _VP, _VP, _VP, ctypes.POINTER(ctypes.c_double), _VP, _VP]),
     "nlinv_sync": (_I, [_VP, _VP]),
     "nlinv_strerror": (ctypes.c_char_p, [_I]),
     "nlinv_last_cuda_error": (ctypes.c_char_p, []),
@@ -259,6 +261,24 @@ def nlinv_batch(frames, stream=None):
         arr[i].rho_out = _ptr(f.get("rho_out"), numel=NN, name="rho_out")
         arr[i].img_out = _ptr(f.get("img_out"), numel=NN, name="img_out")
     _check(_lib().nlinv_batch(arr, len(frames), _stream(stream)), "nlinv_batch")
+
+
+def nlinv_set_alpha0(plan: Plan, alpha0: float):
+    _check(_lib().nlinv_set_alpha0(plan.handle, float(alpha0)), "nlinv_set_alpha0")
+
+
+def nlinv_frame_vjp(plan: Plan, Y, turn: int, x_prev, gbar, Ybar_out, xprev_bar_out=None,
+                    stream=None) -> float:
+    """dL/dY into Ybar_out (and dL/dx_prev into xprev_bar_out) for
+    dL/dx^_M = gbar; returns dL/dalpha_0."""
+    a0 = ctypes.c_double(0.0)
+    _check(_lib().nlinv_frame_vjp(plan.handle, _ptr(Y, numel=plan.J * plan.G * plan.G, name="Y"), turn,
+                                  _ptr(x_prev, numel=plan.nx, name="x_prev"),
+                                  _ptr(gbar, numel=plan.nx, name="gbar"),
+                                  _ptr(Ybar_out, numel=plan.J * plan.G * plan.G, name="Ybar_out"),
+                                  ctypes.byref(a0), _ptr(xprev_bar_out, numel=plan.nx, name="xprev_bar_out"),
+                                  _stream(stream)), "nlinv_frame_vjp")
+    return a0.value
 
 
 def nlinv_wait_flag(plan: Plan, flag, expected: int, spin_limit: int, stream=None):

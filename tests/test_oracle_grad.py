@@ -29,7 +29,7 @@ def test_frame_gradients_match_central_differences(M, K):
     g, Y, P, x0 = setup()
     prm = O.Params(newton_steps=M, cg_iters=K, alpha0=1.0, q=0.5, damping=0.9)
     gvec = rand_x(g, 90)
-    Ybar, a0bar, xbar = OG.frame_vjp(Y, P, x0, x0.scale(0.9), g, prm, gvec)
+    Ybar, a0bar, xbar, xrbar = OG.frame_vjp(Y, P, x0, x0.scale(0.9), g, prm, gvec)
     # alpha_0
     h = 1e-5
     lp = loss(Y, P, x0, g, O.Params(M, K, 1.0 + h, 0.5, 0.9), gvec)
@@ -41,6 +41,11 @@ def test_frame_gradients_match_central_differences(M, K):
     h = 1e-6
     fd = (loss(Y + h * dY, P, x0, g, prm, gvec) - loss(Y - h * dY, P, x0, g, prm, gvec)) / (2 * h)
     an = float(np.real(np.vdot(Ybar, dY)))
+    assert abs(an - fd) <= 1e-6 * abs(fd), (an, fd)
+    # x_prev (initial value and regulariser x_ref = 0.9 x_prev) along a direction
+    dx = rand_x(g, 92)
+    fd = (loss(Y, P, x0 + dx.scale(h), g, prm, gvec) - loss(Y, P, x0 - dx.scale(h), g, prm, gvec)) / (2 * h)
+    an = O.dot(xbar + xrbar.scale(0.9), dx)
     assert abs(an - fd) <= 1e-6 * abs(fd), (an, fd)
 
 
