@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(K::BS) k_row_cg(Ctx C0, int k, const float2* p
                                                   float2* vout) {
   const Ctx C = whole_grid(C0);
   extern __shared__ float2 sm[];
-  __shared__ double sred[32];
+  __shared__ float2 sred[32];
   phase_row_cg<K>(C, sm, sred, k, p_old, p_new, vout);
 }
 
@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(K::BS) k_col_e(Ctx C0, int mode, float alpha, 
                                                  float2* out, float2* hout, int slot) {
   const Ctx C = whole_grid(C0);
   extern __shared__ float2 sm[];
-  __shared__ double sred[32];
+  __shared__ float2 sred[32];
   phase_col_e<K>(C, sm, sred, mode, alpha, k, kbin, sin, p_old, p_new, out, hout, slot);
 }
 
@@ -103,7 +103,7 @@ template <class K>
 __global__ void __launch_bounds__(K::BS) k_upd(Ctx C0, int k, int last, const float2* p) {
   const Ctx C = whole_grid(C0);
   extern __shared__ float2 sm[];
-  __shared__ double sred[32];
+  __shared__ float2 sred[32];
   phase_upd<K>(C, sm, sred, k, last != 0, p);
 }
 
@@ -156,28 +156,49 @@ __host__ __device__ __forceinline__ Ctx frame_ctx(Ctx C, size_t off) {
   NLINV_ADV(float2, xn);
   NLINV_ADV(float2, xref);
   NLINV_ADV(float2, xcg);
-  NLINV_ADV(float2, r);
+  NLINV_ADV(float2, rb[0]);
+  NLINV_ADV(float2, rb[1]);
   NLINV_ADV(float2, q);
   NLINV_ADV(float2, pb[0]);
   NLINV_ADV(float2, pb[1]);
-  NLINV_ADV(double, part);
-  NLINV_ADV(double, tot);
-  NLINV_ADV(unsigned, cnt);
+  NLINV_ADV(float2, part);
   NLINV_ADV(float2, Hr);
   NLINV_ADV(float2, Hp);
 #undef NLINV_ADV
   return C;
 }
 
+#ifdef NLINV_TIMELINE
+// profiling builds: per-CTA global timer at the start of every phase and
+// after every barrier of the first frame launch
+__device__ unsigned long long g_timeline[160][1024];
+__device__ __forceinline__ void tl_mark(int& i) {
+  if (threadIdx.x == 0 && blockIdx.x < 160 && i < 1024) {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    g_timeline[blockIdx.x][i] = t;
+  }
+  ++i;
+}
+#define NLINV_MARK() tl_mark(tl_i)
+#else
+#define NLINV_MARK()
+#endif
+
 // Every phase of every Newton step and CG iteration of one frame, separated
 // by bounded grid barriers (which all CTAs of the launch pass together).
 template <class K>
-__device__ __forceinline__ void frame_body(const Ctx& C, float2* sm, double* sred, const FrameIO& io, int M,
+__device__ __forceinline__ void frame_body(const Ctx& C, float2* sm, float2* sred, const FrameIO& io, int M,
                                            int Kcg, float damping, const float* alpha) {
   const int NN = C.N * C.N;
   unsigned epoch = 0;
-#define NLINV_SYNC() \
-  if (!grid_sync(C, epoch)) return
+#ifdef NLINV_TIMELINE
+  int tl_i = 0;
+#endif
+#define NLINV_SYNC()              \
+  NLINV_MARK();                   \
+  if (!grid_sync(C, epoch)) return; \
+  NLINV_MARK()
   phase_init(C, io.xprev, damping);
   NLINV_SYNC();
   for (int n = 0; n < M; ++n) {
@@ -191,7 +212,7 @@ __device__ __forceinline__ void frame_body(const Ctx& C, float2* sm, double* sre
     NLINV_SYNC();
     phase_row_d<K>(C, sm, C.xn, C.v, C.s, C.kb);
     NLINV_SYNC();
-    phase_col_e<K>(C, sm, sred, E_RHS, al, 0, C.kb, C.s, nullptr, nullptr, C.r, C.Hr, SLOT_RR0);
+    phase_col_e<K>(C, sm, sred, E_RHS, al, 0, C.kb, C.s, nullptr, nullptr, C.rb[0], C.Hr, SLOT_RR0);
     NLINV_SYNC();
     for (int k = 0; k < Kcg; ++k) {
       float2* pk = C.pb[k & 1];
@@ -220,7 +241,7 @@ __device__ __forceinline__ void frame_body(const Ctx& C, float2* sm, double* sre
 template <class K>
 __global__ void __launch_bounds__(K::BS, K::MINB) k_frame(Ctx C0, FrameArgs F) {
   extern __shared__ float2 sm[];
-  __shared__ double sred[32];
+  __shared__ float2 sred[32];
   const Ctx C = whole_grid(C0);
   frame_body<K>(C, sm, sred, F.io, F.M, F.K, F.damping, F.alpha);
 }
@@ -231,7 +252,7 @@ __global__ void __launch_bounds__(K::BS, K::MINB) k_frame(Ctx C0, FrameArgs F) {
 template <class K>
 __global__ void __launch_bounds__(K::BS, K::MINB) k_batch(Ctx C0, BatchArgs B) {
   extern __shared__ float2 sm[];
-  __shared__ double sred[32];
+  __shared__ float2 sred[32];
   const int nf = B.nf;
   const int f = (int)(((long long)blockIdx.x * nf) / gridDim.x);
   const int lo = (int)(((long long)f * gridDim.x + nf - 1) / nf);
@@ -427,17 +448,19 @@ template <class K>
 struct Launch {
   const nlinv_plan_s* pl;
   cudaStream_t st;
+  int fixed = 0;   // if > 0: every launch uses this many CTAs (CG reductions need equal counts)
+  int pick(int g) const { return fixed > 0 ? fixed : g; }
   int coil_y(const float2* src, float2* hout) const {
     const Ctx& C = pl->C;
     const int g = plan_grid(C.J * ((C.Gc + K::TW - 1) / K::TW), 1);
-    k_coil_y<K><<<g, K::BS, K::SMEM, st>>>(C, src, hout);
+    k_coil_y<K><<<pick(g), K::BS, K::SMEM, st>>>(C, src, hout);
     CKL("k_coil_y");
     return NLINV_OK;
   }
   int row_cg(int k, const float2* p_old, float2* p_new, float2* vout) const {
     const Ctx& C = pl->C;
     const int g = plan_grid(C.J * ((C.N + K::TW - 1) / K::TW), 1);
-    k_row_cg<K><<<g, K::BS, K::SMEM, st>>>(C, k, p_old, p_new, vout);
+    k_row_cg<K><<<pick(g), K::BS, K::SMEM, st>>>(C, k, p_old, p_new, vout);
     CKL("k_row_cg");
     return NLINV_OK;
   }
@@ -445,21 +468,21 @@ struct Launch {
             float2* vout) const {
     const Ctx& C = pl->C;
     const int g = plan_grid(C.J * ((C.N + K::TW - 1) / K::TW), 1);
-    k_row_b<K><<<g, K::BS, K::SMEM, st>>>(C, mode, hin, rho, drho, img, vout);
+    k_row_b<K><<<pick(g), K::BS, K::SMEM, st>>>(C, mode, hin, rho, drho, img, vout);
     CKL("k_row_b");
     return NLINV_OK;
   }
   int col_c(int mode, const float* P, const float2* Yin, float2* zout, float2* vio) const {
     const Ctx& C = pl->C;
     const int g = plan_grid(C.J * ((C.G + K::TW - 1) / K::TW), 1);
-    k_col_c<K><<<g, K::BS, K::SMEM, st>>>(C, mode, P, Yin, zout, vio);
+    k_col_c<K><<<pick(g), K::BS, K::SMEM, st>>>(C, mode, P, Yin, zout, vio);
     CKL("k_col_c");
     return NLINV_OK;
   }
   int row_d(const float2* rho, const float2* win, float2* sout, float2* kbout) const {
     const Ctx& C = pl->C;
     const int g = plan_grid(C.J * ((C.N + K::TW - 1) / K::TW), 1);
-    k_row_d<K><<<g, K::BS, K::SMEM, st>>>(C, rho, win, sout, kbout);
+    k_row_d<K><<<pick(g), K::BS, K::SMEM, st>>>(C, rho, win, sout, kbout);
     CKL("k_row_d");
     return NLINV_OK;
   }
@@ -468,7 +491,7 @@ struct Launch {
     const Ctx& C = pl->C;
     const int items = C.J * ((C.Gc + K::TW - 1) / K::TW);
     const int g = plan_grid(items, (C.N * C.N + K::BS - 1) / K::BS);
-    k_col_e<K><<<g, K::BS, K::SMEM, st>>>(C, mode, alpha, k, kbin, sin, p_old, p_new, out, hout, slot);
+    k_col_e<K><<<pick(g), K::BS, K::SMEM, st>>>(C, mode, alpha, k, kbin, sin, p_old, p_new, out, hout, slot);
     CKL("k_col_e");
     return NLINV_OK;
   }
@@ -476,7 +499,7 @@ struct Launch {
     const Ctx& C = pl->C;
     const int items = C.J * ((C.Gc + K::TW - 1) / K::TW);
     const int g = plan_grid(items, (C.N * C.N + K::BS - 1) / K::BS);
-    k_upd<K><<<g, K::BS, K::SMEM, st>>>(C, k, last, p);
+    k_upd<K><<<pick(g), K::BS, K::SMEM, st>>>(C, k, last, p);
     CKL("k_upd");
     return NLINV_OK;
   }
@@ -598,8 +621,8 @@ int nlinv_plan(nlinv_plan_t* out, const nlinv_params_t* p, const float* psf, nli
   take((size_t)J * N * N * f2);          // 8 s
   take((size_t)J * N * Gc * f2);         // 9 kb
   for (int i = 0; i < 7; ++i) take(nx * f2);  // 10..16 xn xref xcg r q p0 p1
-  take((size_t)NSLOT * kMaxPart * sizeof(double));  // 17 part
-  take(NSLOT * (sizeof(double) + sizeof(unsigned)));  // 18 tot, cnt
+  take((size_t)NSLOT * kMaxPart * sizeof(float2));  // 17 part
+  take(nx * f2);                         // 18 r1 (second residual buffer)
   for (int i = 0; i < 2; ++i) take((size_t)J * N * Gc * f2);  // 19..20 Hr Hp
   pl->fstride = tot - shared_bytes;
   tot = shared_bytes + pl->fstride * (size_t)pl->max_batch;
@@ -633,13 +656,12 @@ int nlinv_plan(nlinv_plan_t* out, const nlinv_params_t* p, const float* psf, nli
   C.xn = (float2*)(base + off[10]);
   C.xref = (float2*)(base + off[11]);
   C.xcg = (float2*)(base + off[12]);
-  C.r = (float2*)(base + off[13]);
+  C.rb[0] = (float2*)(base + off[13]);
+  C.rb[1] = (float2*)(base + off[18]);
   C.q = (float2*)(base + off[14]);
   C.pb[0] = (float2*)(base + off[15]);
   C.pb[1] = (float2*)(base + off[16]);
-  C.part = (double*)(base + off[17]);
-  C.tot = (double*)(base + off[18]);
-  C.cnt = (unsigned*)(C.tot + NSLOT);
+  C.part = (float2*)(base + off[17]);
   C.Hr = (float2*)(base + off[19]);
   C.Hp = (float2*)(base + off[20]);
   C.spin_limit = pl->prm.spin_limit;
@@ -869,7 +891,7 @@ int nlinv_frame(nlinv_plan_t pl, const void* Y, int turn, const void* x_prev, vo
                                      (size_t)K::SMEM, st));
       return NLINV_OK;
     }
-    Launch<K> L{pl, st};
+    Launch<K> L{pl, st, pl->coop_grid};
     const int ge = plan_grid((int)((C.nx + 255) / 256), 1);
     k_init<<<ge, 256, 0, st>>>(C, F.io.xprev, F.damping);
     CKL("k_init");
@@ -879,7 +901,7 @@ int nlinv_frame(nlinv_plan_t pl, const void* Y, int turn, const void* x_prev, vo
       RC(L.row_b(ROW_COIL, C.h, C.xn, nullptr, nullptr, C.v));
       RC(L.col_c(COL_RHS, F.io.P, F.io.Y, nullptr, C.v));
       RC(L.row_d(C.xn, C.v, C.s, C.kb));
-      RC(L.col_e(E_RHS, alpha, 0, C.kb, C.s, nullptr, nullptr, C.r, C.Hr, SLOT_RR0));
+      RC(L.col_e(E_RHS, alpha, 0, C.kb, C.s, nullptr, nullptr, C.rb[0], C.Hr, SLOT_RR0));
       for (int kk = 0; kk < F.K; ++kk) {
         float2* pk = C.pb[kk & 1];
         const float2* pm = C.pb[(kk + 1) & 1];
@@ -1080,8 +1102,8 @@ extern "C" int nlinv_apply_normal_static(int N, int J, int Gc, double w_a, doubl
   take((size_t)J * N * G * f2);
   take((size_t)J * N * N * f2);
   take((size_t)J * N * Gc * f2);
-  take((size_t)NSLOT * kMaxPart * sizeof(double));
-  take(NSLOT * (sizeof(double) + sizeof(unsigned)) + sizeof(int) + 2 * sizeof(unsigned));
+  take((size_t)NSLOT * kMaxPart * sizeof(float2));
+  take(sizeof(int) + 2 * sizeof(unsigned));
   if (tot > kStaticScratchBytes) return NLINV_EINVAL;
   void* base_v = nullptr;
   RC(static_scratch(&base_v));
@@ -1109,10 +1131,8 @@ extern "C" int nlinv_apply_normal_static(int N, int J, int Gc, double w_a, doubl
   C.v = (float2*)(base + off[4]);
   C.s = (float2*)(base + off[5]);
   C.kb = (float2*)(base + off[6]);
-  C.part = (double*)(base + off[7]);
-  C.tot = (double*)(base + off[8]);
-  C.cnt = (unsigned*)(C.tot + NSLOT);
-  C.err = (int*)(C.cnt + NSLOT);
+  C.part = (float2*)(base + off[7]);
+  C.err = (int*)(base + off[8]);
   C.bar = (unsigned*)(C.err + 1);
   C.spin_limit = 1LL << 22;
   const int nt = (G > Gc * Gc ? G : Gc * Gc);
@@ -1161,6 +1181,12 @@ __global__ void k_axpby(long long n, float2* y, const float2* x, float ahi, floa
   }
 }
 
+__device__ __forceinline__ double warp_sum_f64(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;   // valid in lane 0
+}
+
 // per-block FP64 partials of Re <u, v>
 __global__ void k_dot_part(long long n, const float2* u, const float2* v, double* part) {
   __shared__ double sw[32];
@@ -1169,7 +1195,7 @@ __global__ void k_dot_part(long long n, const float2* u, const float2* v, double
     const float2 a = u[i], b = v[i];
     acc = fma((double)a.x, (double)b.x, fma((double)a.y, (double)b.y, acc));
   }
-  acc = warp_sum(acc);
+  acc = warp_sum_f64(acc);
   if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = acc;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -1529,3 +1555,16 @@ extern "C" int nlinv_frame_vjp(nlinv_plan_t pl, const void* Y, int turn, const v
   CK(cudaStreamSynchronize(O.st));
   return NLINV_OK;
 }
+
+#ifdef NLINV_TIMELINE
+extern "C" int nlinv_debug_timeline(unsigned long long* host, int n) {
+  if (n > 160 * 1024) n = 160 * 1024;
+  CK(cudaMemcpyFromSymbol(host, g_timeline, (size_t)n * sizeof(unsigned long long)));
+  return NLINV_OK;
+}
+extern "C" int nlinv_debug_stages(unsigned long long* ns, unsigned long long* cnt) {
+  CK(cudaMemcpyFromSymbol(ns, nlinv::g_stage_ns, sizeof(unsigned long long) * 64));
+  CK(cudaMemcpyFromSymbol(cnt, nlinv::g_stage_n, sizeof(unsigned long long) * 64));
+  return NLINV_OK;
+}
+#endif

@@ -50,6 +50,30 @@
 
 namespace nlinv {
 
+#ifdef NLINV_TIMELINE
+// profiling builds: per (phase, stage) summed durations over all CTAs' items
+__device__ unsigned long long g_stage_ns[8][8];
+__device__ unsigned long long g_stage_n[8][8];
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+#define STG_BEGIN() unsigned long long stg_t0 = gtimer()
+#define STG(ph, st)                                                   \
+  do {                                                                \
+    if (threadIdx.x == 0) {                                           \
+      const unsigned long long t1 = gtimer();                         \
+      atomicAdd(&g_stage_ns[ph][st], t1 - stg_t0);                    \
+      atomicAdd(&g_stage_n[ph][st], 1ull);                            \
+      stg_t0 = t1;                                                    \
+    }                                                                 \
+  } while (0)
+#else
+#define STG_BEGIN()
+#define STG(ph, st)
+#endif
+
 constexpr int kMaxPart = 4096;     // max CTAs that deposit an FP64 partial
 enum { SLOT_PQ = 0, SLOT_RR0 = 1, SLOT_RR1 = 2, NSLOT = 4 };
 enum { DEV_ETIMEOUT = -4, DEV_ENUMERIC = -5 };
@@ -65,12 +89,11 @@ struct Ctx {
   const float* dinv;    // [Gc][Gc]
   const float* psf;     // [U][G][G]
   float2 *c, *h, *v, *s, *kb;
-  float2 *xn, *xref, *xcg, *r, *q;
+  float2 *xn, *xref, *xcg, *q;
+  float2* rb[2];        // CG residual r_k lives in rb[k & 1]
   float2* pb[2];        // CG direction p_k lives in pb[k & 1]
   float2 *Hr, *Hp;      // y pass of W^-1 applied to r, p: [J][N][Gc]
-  double* part;         // [NSLOT][kMaxPart] per-CTA partials
-  double* tot;          // [NSLOT] totals, written by the last CTA of the producer
-  unsigned* cnt;        // [NSLOT] arrival counters of the producer (self-resetting)
+  float2* part;         // [NSLOT][kMaxPart] per-CTA partials (float pairs hi, lo)
   int* err;             // latched device error
   unsigned* bar;        // grid barrier counter
   long long spin_limit;
@@ -86,7 +109,11 @@ template <int G1_, int G2_> struct Cfg {
   static constexpr int RS = G + MX;         // smem stride of one row (float2)
   static constexpr int SMEM = TW * RS * 8;  // dynamic smem bytes
   // CTAs per SM the persistent kernel is compiled for (caps registers)
+#ifdef NLINV_MINB
+  static constexpr int MINB = NLINV_MINB;
+#else
   static constexpr int MINB = BS <= 256 ? 2 : 1;
+#endif
   static_assert(G1 % 2 == 0 && G2 % 2 == 0, "G1, G2 must be even");
   // the FP64 block reductions use full-warp shuffles over blockDim / 32 warps
   static_assert(BS % 32 == 0, "threads per CTA must be a whole number of warps");
@@ -117,47 +144,105 @@ __device__ __forceinline__ int coef_index(int pos, int G, int Gc) {
 }
 
 // -------------------------------------------------------- reductions
-__device__ __forceinline__ double warp_sum(double v) {
+// Sums are carried as unevaluated float pairs hi + lo (~48 significant bits)
+// with Knuth's two-sum, so the hot path needs no FP64 instructions (FP64 runs
+// at a small fraction of the FP32 rate on this part).
+struct DF32 {
+  float hi, lo;
+};
+__device__ __forceinline__ DF32 df_add(DF32 a, DF32 b) {
+  const float s = a.hi + b.hi;
+  const float v = s - a.hi;
+  float e = (a.hi - (s - v)) + (b.hi - v);
+  e += a.lo + b.lo;
+  const float hi = s + e;
+  return DF32{hi, e - (hi - s)};
+}
+__device__ __forceinline__ DF32 df_shfl_down(DF32 a, int o) {
+  return DF32{__shfl_down_sync(0xffffffffu, a.hi, o), __shfl_down_sync(0xffffffffu, a.lo, o)};
+}
+__device__ __forceinline__ DF32 df_warp_sum(DF32 a) {   // fixed tree, valid in lane 0
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;   // valid in lane 0
+  for (int o = 16; o > 0; o >>= 1) a = df_add(a, df_shfl_down(a, o));
+  return a;
 }
 
-// Deterministic reduction of one FP64 scalar over the whole grid: each CTA
-// sums its threads (fixed warp trees) into part[slot][blockIdx]; the last CTA
-// to arrive adds the partials in index order and publishes tot[slot].  A
-// later phase (after a grid barrier or in a later kernel) reads the total
-// with a single load.
-__device__ __forceinline__ void block_partial(const Ctx& C, double v, int slot, double* sred) {
-  __shared__ int s_last;
-  v = warp_sum(v);
+// Deterministic grid reduction, producer side: this CTA's threads' values
+// (fixed warp trees) become part[slot][bid].  Consumers (a later phase,
+// after a barrier or in a later kernel with the same CTA count) add the nb
+// partials themselves with slot_total().
+__device__ __forceinline__ void block_partial(const Ctx& C, float v, int slot, float2* sred) {
+  DF32 a = df_warp_sum(DF32{v, 0.f});
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) sred[w] = v;
+  if (l == 0) sred[w] = make_float2(a.hi, a.lo);
   __syncthreads();
   if (threadIdx.x == 0) {
-    const int nw = blockDim.x >> 5;
-    double a = 0.0;
-    for (int i = 0; i < nw; ++i) a += sred[i];
-    C.part[slot * kMaxPart + C.bid] = a;
-    __threadfence();
-    s_last = (atomicAdd(C.cnt + slot, 1u) == (unsigned)C.nb - 1);
-  }
-  __syncthreads();
-  if (s_last && w == 0) {
-    __threadfence();
-    double a = 0.0;
-    for (int i = l; i < C.nb; i += 32) a += __ldcg(C.part + slot * kMaxPart + i);
-    a = warp_sum(a);
-    if (l == 0) {
-      C.tot[slot] = a;
-      C.cnt[slot] = 0u;
-    }
+    DF32 t{0.f, 0.f};
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t = df_add(t, DF32{sred[i].x, sred[i].y});
+    C.part[slot * kMaxPart + C.bid] = make_float2(t.hi, t.lo);
   }
   __syncthreads();
 }
 
-// the published total of `slot`
-__device__ __forceinline__ double slot_total(const Ctx& C, int slot) { return __ldcg(C.tot + slot); }
+// Consumer side: every warp adds the nb partials of `slot` in the same fixed
+// order (one round trip to L2, no block barrier) and gets the same total.
+__device__ __forceinline__ DF32 slot_sum(const Ctx& C, int slot) {
+  const int l = threadIdx.x & 31;
+  const float2* src = C.part + slot * kMaxPart;
+  DF32 a{0.f, 0.f};
+  for (int base = 0; base < C.nb; base += 32 * 8) {
+    float2 v[8];   // all loads of a round issued before any add (one L2 round trip)
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = base + u * 32 + l;
+      v[u] = (i < C.nb) ? __ldcg(src + i) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) a = df_add(a, DF32{v[u].x, v[u].y});
+  }
+  a = df_warp_sum(a);
+  return DF32{__shfl_sync(0xffffffffu, a.hi, 0), __shfl_sync(0xffffffffu, a.lo, 0)};
+}
+
+__device__ __forceinline__ double df_to_double(DF32 a) { return (double)a.hi + (double)a.lo; }
+
+// FP64 scalar computed by lane 0 of each warp, handed to the warp as a
+// float pair (FP64 instructions are slow on this part: one lane, not all)
+__device__ __forceinline__ Scal2 warp_scalar(double v, bool lane0) {
+  float hi = 0.f, lo = 0.f;
+  if (lane0) {
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+  }
+  return Scal2{__shfl_sync(0xffffffffu, hi, 0), __shfl_sync(0xffffffffu, lo, 0)};
+}
+
+// beta_k = |r_k|^2 / |r_{k-1}|^2 (0 for k == 0 or a zero old residual);
+// warp 0 reads the partials, the other warps get the value through shared
+// memory (one reader per CTA keeps the partials' cache lines cool)
+__device__ __forceinline__ Scal2 cg_beta(const Ctx& C, int k);
+__device__ __forceinline__ Scal2 cta_beta(const Ctx& C, int k) {
+  __shared__ Scal2 s_beta;
+  if (k == 0) return Scal2{0.f, 0.f};
+  if (threadIdx.x < 32) {
+    const Scal2 b = cg_beta(C, k);
+    if (threadIdx.x == 0) s_beta = b;
+  }
+  __syncthreads();
+  return s_beta;
+}
+__device__ __forceinline__ Scal2 cg_beta(const Ctx& C, int k) {
+  if (k == 0) return Scal2{0.f, 0.f};
+  const DF32 rk = slot_sum(C, (k & 1) ? SLOT_RR1 : SLOT_RR0);
+  const DF32 rm = slot_sum(C, (k & 1) ? SLOT_RR0 : SLOT_RR1);
+  const bool l0 = (threadIdx.x & 31) == 0;
+  double b = 0.0;
+  if (l0) {
+    const double d = df_to_double(rm);
+    b = d > 0.0 ? df_to_double(rk) / d : 0.0;
+  }
+  return warp_scalar(b, l0);
+}
 
 __device__ __forceinline__ void raise_err(const Ctx& C, int code) { atomicCAS(C.err, 0, code); }
 
@@ -329,18 +414,14 @@ __device__ NLINV_PHASE void phase_row_b(const Ctx& C, float2* sm, int mode, cons
 // (channel 0 stores it into p_new).  Then as ROW_LIN:
 //   u = c p_rho + rho (x pass of W^-1 of H p), forward row FFT.
 template <class K>
-__device__ NLINV_PHASE void phase_row_cg(const Ctx& C, float2* sm, double* sred, int k, const float2* p_old,
+__device__ NLINV_PHASE void phase_row_cg(const Ctx& C, float2* sm, float2* sred, int k, const float2* p_old,
                              float2* p_new, float2* vout) {
   constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW, RS = K::RS;
   const int N = C.N, Gc = C.Gc, J = C.J;
   const int t = threadIdx.x;
-  double beta64 = 0.0;
-  if (k > 0) {
-    const double rr_k = slot_total(C, (k & 1) ? SLOT_RR1 : SLOT_RR0);
-    const double rr_m = slot_total(C, (k & 1) ? SLOT_RR0 : SLOT_RR1);
-    beta64 = (rr_m > 0.0) ? rr_k / rr_m : 0.0;
-  }
-  const Scal2 beta = split(beta64);
+  STG_BEGIN();
+  const Scal2 beta = cta_beta(C, k);
+  STG(0, 0);
   const int groups = (N + TW - 1) / TW;
   const int items = J * groups;
   for (int it = C.bid; it < items; it += C.nb) {
@@ -351,16 +432,20 @@ __device__ NLINV_PHASE void phase_row_cg(const Ctx& C, float2* sm, double* sred,
       if (rr < TW && y < N) {
         float2 av[G2];
 #pragma unroll
-        for (int n2 = 0; n2 < G2; ++n2) {
+        for (int n2 = 0; n2 < G2; ++n2) {   // loads first ...
           const int ix = coef_index(n1 + G1 * n2, G, Gc);
           float2 hp = czero();
           if (ix >= 0) {
             const size_t e = ((size_t)j * N + y) * Gc + ix;
             const float2 hr = ldcg(C.Hr + e);
             hp = (k == 0) ? hr : axpy2(ldcg(C.Hp + e), beta, hr);
-            C.Hp[e] = hp;
           }
           av[n2] = hp;
+        }
+#pragma unroll
+        for (int n2 = 0; n2 < G2; ++n2) {   // ... then the stores
+          const int ix = coef_index(n1 + G1 * n2, G, Gc);
+          if (ix >= 0) C.Hp[((size_t)j * N + y) * Gc + ix] = av[n2];
         }
         dft<G2, true>(av);
 #pragma unroll
@@ -372,6 +457,7 @@ __device__ NLINV_PHASE void phase_row_cg(const Ctx& C, float2* sm, double* sred,
       }
     }
     __syncthreads();
+    STG(0, 1);
     // stage 2: thread (row, k2): inverse DFT over n1 -> dc at x = k2 + G2 k1;
     // u = c p_rho + rho dc; forward DFT over k1
     const int rr = t / G2, k2 = t % G2, y = y0 + rr;
@@ -382,17 +468,23 @@ __device__ NLINV_PHASE void phase_row_cg(const Ctx& C, float2* sm, double* sred,
 #pragma unroll
       for (int n1 = 0; n1 < G1; ++n1) b[n1] = sm[rr * RS + k2 * (G1 + 1) + n1];
       dft<G1, true>(b);
+      // every operand load of the row is issued before the first store
+      float2 pr[G1 / 2], cv[G1 / 2], rh[G1 / 2];
+#pragma unroll
+      for (int k1 = 0; k1 < G1 / 2; ++k1) {
+        const int x = k2 + G2 * k1;
+        const int ir = y * N + x;
+        const float2 rv = ldcg(C.rb[k & 1] + ir);
+        pr[k1] = (k == 0) ? rv : axpy2(ldcg(p_old + ir), beta, rv);
+        cv[k1] = ldcg(C.c + ((size_t)j * N + y) * N + x);
+        rh[k1] = ldcg(C.xn + ir);
+      }
 #pragma unroll
       for (int k1 = 0; k1 < G1; ++k1) {
         u[k1] = czero();
         if (k1 < G1 / 2) {
-          const int x = k2 + G2 * k1;
-          const size_t ic = ((size_t)j * N + y) * N + x;
-          const int ir = y * N + x;
-          const float2 rv = ldcg(C.r + ir);
-          const float2 pr = (k == 0) ? rv : axpy2(ldcg(p_old + ir), beta, rv);
-          if (j == 0) p_new[ir] = pr;
-          u[k1] = cadd(cmul(ldcg(C.c + ic), pr), cmul(ldcg(C.xn + ir), b[k1]));
+          if (j == 0) p_new[y * N + k2 + G2 * k1] = pr[k1];
+          u[k1] = cadd(cmul(cv[k1], pr[k1]), cmul(rh[k1], b[k1]));
         }
       }
       dft<G1, false>(u);
@@ -405,6 +497,7 @@ __device__ NLINV_PHASE void phase_row_cg(const Ctx& C, float2* sm, double* sred,
       for (int kb = 0; kb < G1; ++kb) sm[rr * RS + kb * (G2 + 1) + k2] = u[kb];
     }
     __syncthreads();
+    STG(0, 2);
     {  // stage 3: thread (row, kb): forward DFT over k2 -> kb + G1 ka
       const int r3 = t / G1, kb = t % G1, y3 = y0 + r3;
       if (r3 < TW && y3 < N) {
@@ -418,6 +511,7 @@ __device__ NLINV_PHASE void phase_row_cg(const Ctx& C, float2* sm, double* sred,
       }
     }
     __syncthreads();
+    STG(0, 3);
   }
 }
 
@@ -434,6 +528,7 @@ __device__ NLINV_PHASE void phase_col_c(const Ctx& C, float2* sm, int mode, cons
   const int t = threadIdx.x;
   constexpr int tiles = (G + TW - 1) / TW;
   const int items = J * tiles;
+  STG_BEGIN();
   for (int it = C.bid; it < items; it += C.nb) {
     const int j = it / tiles;
     const int x = (it - j * tiles) * TW + (t % TW);
@@ -455,6 +550,7 @@ __device__ NLINV_PHASE void phase_col_c(const Ctx& C, float2* sm, int mode, cons
       }
       __syncthreads();
     }
+    STG(1, 1);
     // stage 2: thread (k2, c): forward DFT over n1 -> k = k2 + G2 k1; the
     // pointwise step; inverse DFT over k1 (k = k2 + G2 k1 is the input index)
     const int k2 = t / TW, cc = t % TW;
@@ -499,6 +595,7 @@ __device__ NLINV_PHASE void phase_col_c(const Ctx& C, float2* sm, int mode, cons
       for (int m1 = 0; m1 < G1; ++m1) sm[(m1 * G2 + k2) * TW + cc] = b[m1];
     }
     __syncthreads();
+    STG(1, 2);
     {  // stage 3: thread (m1, c): inverse DFT over k2 -> y = m1 + G1 m2, keep y < N
       const int m1 = t / TW;
       if (m1 < G1 && colok) {
@@ -511,6 +608,7 @@ __device__ NLINV_PHASE void phase_col_c(const Ctx& C, float2* sm, int mode, cons
       }
     }
     __syncthreads();
+    STG(1, 3);
   }
 }
 
@@ -552,14 +650,19 @@ __device__ NLINV_PHASE void phase_row_d(const Ctx& C, float2* sm, const float2* 
 #pragma unroll
       for (int n1 = 0; n1 < G1; ++n1) b[n1] = sm[rr * RS + k2 * (G1 + 1) + n1];
       dft<G1, true>(b);
+      float2 cv[G1 / 2], rh[G1 / 2];
+#pragma unroll
+      for (int k1 = 0; k1 < G1 / 2; ++k1) {   // loads first, stores after
+        const int x = k2 + G2 * k1;
+        cv[k1] = ldcg(C.c + ((size_t)j * N + y) * N + x);
+        rh[k1] = ldcg(rho + y * N + x);
+      }
 #pragma unroll
       for (int k1 = 0; k1 < G1; ++k1) {
         g[k1] = czero();
         if (k1 < G1 / 2) {
-          const int x = k2 + G2 * k1;
-          const size_t ic = ((size_t)j * N + y) * N + x;
-          sout[ic] = cconjmul(ldcg(C.c + ic), b[k1]);
-          g[k1] = cconjmul(ldcg(rho + y * N + x), b[k1]);
+          sout[((size_t)j * N + y) * N + k2 + G2 * k1] = cconjmul(cv[k1], b[k1]);
+          g[k1] = cconjmul(rh[k1], b[k1]);
         }
       }
       dft<G1, false>(g);
@@ -600,20 +703,16 @@ __device__ NLINV_PHASE void phase_row_d(const Ctx& C, float2* sm, const float2* 
 // H is the y pass of W^-1 (as phase A computes it); for E_RHS the column
 // values are still in registers, so it costs one more exchange.
 template <class K>
-__device__ NLINV_PHASE void phase_col_e(const Ctx& C, float2* sm, double* sred, int mode, float alpha, int k,
+__device__ NLINV_PHASE void phase_col_e(const Ctx& C, float2* sm, float2* sred, int mode, float alpha, int k,
                             const float2* kbin, const float2* sin, const float2* p_old,
                             float2* p_new, float2* out, float2* hout, int slot) {
   constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW;
   const int N = C.N, Gc = C.Gc, J = C.J, NN = N * N;
   const int t = threadIdx.x;
   const bool withH = (mode == E_RHS);
-  double beta64 = 0.0;
-  if (mode == E_CG && k > 0) {
-    const double rr_k = slot_total(C, (k & 1) ? SLOT_RR1 : SLOT_RR0);
-    const double rr_m = slot_total(C, (k & 1) ? SLOT_RR0 : SLOT_RR1);
-    beta64 = (rr_m > 0.0) ? rr_k / rr_m : 0.0;
-  }
-  const Scal2 beta = split(beta64);
+  STG_BEGIN();
+  const Scal2 beta = (mode == E_CG) ? cta_beta(C, k) : Scal2{0.f, 0.f};
+  STG(2, 0);
   const int tiles = (Gc + TW - 1) / TW;
   const int items = J * tiles;
   float acc = 0.f;   // this thread's few terms; CTA and grid sums in FP64
@@ -639,6 +738,7 @@ __device__ NLINV_PHASE void phase_col_e(const Ctx& C, float2* sm, double* sred, 
       }
     }
     __syncthreads();
+    STG(2, 1);
     // stage 2: thread (k2, c): forward DFT over n1, crop rows to G_c, the
     // pointwise epilogue; then (E_CG/E_RHS) D_W^-1 and the inverse DFT over
     // k1 of the new column for H
@@ -649,6 +749,23 @@ __device__ NLINV_PHASE void phase_col_e(const Ctx& C, float2* sm, double* sred, 
 #pragma unroll
       for (int n1 = 0; n1 < G1; ++n1) b[n1] = sm[(k2 * G1 + n1) * TW + cc];
       dft<G1, false>(b);
+      // the operands of all kept rows are loaded before any store
+      float2 opd[G1];
+#pragma unroll
+      for (int k1 = 0; k1 < G1; ++k1) {
+        const int iy = coef_index(k2 + G2 * k1, G, Gc);
+        opd[k1] = czero();
+        if (iy < 0) continue;
+        const size_t e = (size_t)NN + ((size_t)j * Gc + iy) * Gc + fx;
+        if (mode == E_CG) {
+          const float2 rv = ldcg(C.rb[k & 1] + e);
+          opd[k1] = (k == 0) ? rv : axpy2(ldcg(p_old + e), beta, rv);
+        } else if (mode == E_RHS) {
+          opd[k1] = csub(ldcg(C.xn + e), ldcg(C.xref + e));
+        } else if (mode == E_NORMAL) {
+          opd[k1] = ldcg(p_new + e);
+        }
+      }
 #pragma unroll
       for (int k1 = 0; k1 < G1; ++k1) {
         const int iy = coef_index(k2 + G2 * k1, G, Gc);
@@ -661,19 +778,17 @@ __device__ NLINV_PHASE void phase_col_e(const Ctx& C, float2* sm, double* sred, 
         const float2 val = cscale(b[k1], C.inv_G * dv);
         float2 res;
         if (mode == E_CG) {
-          const float2 rv = ldcg(C.r + e);
-          const float2 p = (k == 0) ? rv : axpy2(ldcg(p_old + e), beta, rv);
+          const float2 p = opd[k1];
           p_new[e] = p;
           res = cfma(p, alpha, val);
           acc = fmaf(p.x, res.x, fmaf(p.y, res.y, acc));
         } else if (mode == E_RHS) {
-          const float2 d = csub(ldcg(C.xn + e), ldcg(C.xref + e));
-          res = cfma(d, -alpha, val);
+          res = cfma(opd[k1], -alpha, val);
           acc = fmaf(res.x, res.x, fmaf(res.y, res.y, acc));
         } else if (mode == E_DFH) {
           res = val;
         } else {
-          res = cfma(ldcg(p_new + e), alpha, val);
+          res = cfma(opd[k1], alpha, val);
         }
         out[e] = res;
         b[k1] = cscale(res, dv);
@@ -706,6 +821,7 @@ __device__ NLINV_PHASE void phase_col_e(const Ctx& C, float2* sm, double* sred, 
     }
     __syncthreads();
   }
+  STG(2, 2);
   // rho part: channel sum of s_j = conj(c_j) t_j
   for (int e = C.bid * blockDim.x + t; e < NN; e += C.nb * blockDim.x) {
     float2 sv = czero();
@@ -726,91 +842,142 @@ __device__ NLINV_PHASE void phase_col_e(const Ctx& C, float2* sm, double* sred, 
       out[e] = cfma(ldcg(p_new + e), alpha, sv);
     }
   }
-  if (mode == E_CG || mode == E_RHS) block_partial(C, (double)acc, slot, sred);
+  STG(2, 3);
+  if (mode == E_CG || mode == E_RHS) block_partial(C, acc, slot, sred);
+  STG(2, 4);
 }
 
 // -------------------------------------------------- F: CG vector update
-// a = |r_k|^2 / Re<p_k, A p_k> (FP64); x += a p_k; r -= a q; partial
+// a = |r_k|^2 / Re<p_k, A p_k> (FP64); x += a p_k; r_{k+1} = r_k - a q; partial
 // |r_{k+1}|^2; and H r_{k+1} (the y pass of W^-1 of the rounded new r) for
 // the next direction.  Coil columns are handled per (channel, column tile)
 // so the transform stays on chip; rho elementwise.  On the last iteration
 // x^_{n+1} = x^_n + x is applied and H is not needed.
 template <class K>
-__device__ NLINV_PHASE void phase_upd(const Ctx& C, float2* sm, double* sred, int k, bool last,
+__device__ NLINV_PHASE void phase_upd(const Ctx& C, float2* sm, float2* sred, int k, bool last,
                                        const float2* p) {
   constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW;
   const int N = C.N, Gc = C.Gc, J = C.J, NN = N * N;
   const int t = threadIdx.x;
-  const double rr = slot_total(C, (k & 1) ? SLOT_RR1 : SLOT_RR0);
-  const double pq = slot_total(C, SLOT_PQ);
-  const double a64 = cg_step(rr, pq);
-  if (rr > 0.0 && a64 == 0.0 && C.bid == 0 && t == 0) raise_err(C, DEV_ENUMERIC);
-  const Scal2 a = split(a64), na = split(-a64);
+  STG_BEGIN();
+  __shared__ Scal2 s_a;
+  if (t < 32) {
+    const DF32 rrs = slot_sum(C, (k & 1) ? SLOT_RR1 : SLOT_RR0);
+    const DF32 pqs = slot_sum(C, SLOT_PQ);
+    if (t == 0) {
+      const double rr = df_to_double(rrs);
+      const double a64 = cg_step(rr, df_to_double(pqs));
+      if (rr > 0.0 && a64 == 0.0 && C.bid == 0) raise_err(C, DEV_ENUMERIC);
+      const float hi = (float)a64;
+      s_a = Scal2{hi, (float)(a64 - (double)hi)};
+    }
+  }
+  __syncthreads();
+  const Scal2 a = s_a, na = Scal2{-s_a.hi, -s_a.lo};
+  STG(3, 0);
   float acc = 0.f;   // this thread's few terms; CTA and grid sums in FP64
-  auto update = [&](size_t e) -> float2 {
-    const float2 pv = ldcg(p + e);
-    const float2 xv = axpy2(pv, a, k > 0 ? ldcg(C.xcg + e) : czero());
-    const float2 rv = axpy2(ldcg(C.q + e), na, ldcg(C.r + e));
-    C.r[e] = rv;
-    acc = fmaf(rv.x, rv.x, fmaf(rv.y, rv.y, acc));
-    if (last) C.xn[e] = cadd(ldcg(C.xn + e), xv);
-    else C.xcg[e] = xv;
-    return rv;
-  };
+  // r_k is read from one buffer and r_{k+1} written to the other, so the
+  // column items below may read r_k while other CTAs already store r_{k+1}
+  const float2* rk = C.rb[k & 1];
+  float2* rk1 = C.rb[(k + 1) & 1];
+  // (1) H r_{k+1} per coil column tile: the new residual r - a q of the tile
+  //     is formed in registers exactly as the flat pass below stores it,
+  //     transformed, and only the transform is stored (loads only before it)
   const int tiles = (Gc + TW - 1) / TW;
-  const int items = J * tiles;
+  const int items = last ? 0 : J * tiles;
   for (int it = C.bid; it < items; it += C.nb) {
     const int j = it / tiles;
     const int fx = (it - j * tiles) * TW + (t % TW);
     const bool colok = fx < Gc;
-    {  // stage 1: thread (n1, c): update the column's entries, inverse DFT over n2
-      const int n1 = t / TW;
-      if (n1 < G1) {
-        float2 av[G2];
+    const int n1 = t / TW;
+    if (n1 < G1) {  // stage 1: thread (n1, c): new residual of the column, inverse DFT over n2
+      float2 av[G2];
 #pragma unroll
-        for (int n2 = 0; n2 < G2; ++n2) {
-          const int iy = coef_index(n1 + G1 * n2, G, Gc);
-          float2 val = czero();
-          if (colok && iy >= 0) {
-            const float2 rv = update((size_t)NN + ((size_t)j * Gc + iy) * Gc + fx);
-            val = cscale(rv, __ldg(C.dinv + iy * Gc + fx));
-          }
-          av[n2] = val;
-        }
-        if (!last) {
-          dft<G2, true>(av);
+      for (int n2 = 0; n2 < G2; ++n2) {
+        const int iy = coef_index(n1 + G1 * n2, G, Gc);
+        av[n2] = (colok && iy >= 0) ? ldcg(rk + (size_t)NN + ((size_t)j * Gc + iy) * Gc + fx) : czero();
+      }
 #pragma unroll
-          for (int k2 = 0; k2 < G2; ++k2) {
-            float2 x = av[k2];
-            if (k2) x = cmul(x, twg<true>(C.tw, n1 * k2));
-            sm[(k2 * G1 + n1) * TW + (t % TW)] = x;
-          }
+      for (int n2 = 0; n2 < G2; ++n2) {
+        const int iy = coef_index(n1 + G1 * n2, G, Gc);
+        if (colok && iy >= 0) {
+          const float2 qv = ldcg(C.q + (size_t)NN + ((size_t)j * Gc + iy) * Gc + fx);
+          av[n2] = cscale(axpy2(qv, na, av[n2]), __ldg(C.dinv + iy * Gc + fx));
         }
+      }
+      dft<G2, true>(av);
+#pragma unroll
+      for (int k2 = 0; k2 < G2; ++k2) {
+        float2 x = av[k2];
+        if (k2) x = cmul(x, twg<true>(C.tw, n1 * k2));
+        sm[(k2 * G1 + n1) * TW + (t % TW)] = x;
       }
     }
-    if (!last) {
-      __syncthreads();
-      const int k2 = t / TW, cc = t % TW;
-      if (k2 < G2 && colok) {  // stage 2: inverse DFT over n1, keep y < N
-        float2 b[G1];
+    STG(3, 1);
+    __syncthreads();
+    const int k2 = t / TW, cc = t % TW;
+    if (k2 < G2 && colok) {  // stage 2: inverse DFT over n1, keep y < N
+      float2 b[G1];
 #pragma unroll
-        for (int n1 = 0; n1 < G1; ++n1) b[n1] = sm[(k2 * G1 + n1) * TW + cc];
-        dft<G1, true>(b);
+      for (int q1 = 0; q1 < G1; ++q1) b[q1] = sm[(k2 * G1 + q1) * TW + cc];
+      dft<G1, true>(b);
 #pragma unroll
-        for (int k1 = 0; k1 < G1 / 2; ++k1)
-          C.Hr[((size_t)j * N + k2 + G2 * k1) * Gc + fx] = cscale(b[k1], C.inv_G);
+      for (int k1 = 0; k1 < G1 / 2; ++k1)
+        C.Hr[((size_t)j * N + k2 + G2 * k1) * Gc + fx] = cscale(b[k1], C.inv_G);
+    }
+    __syncthreads();
+  }
+  // (2) every element of x and r, all CTAs: loads of a batch before its stores
+  const int stride = C.nb * blockDim.x;
+  if (last) {  // x^_{n+1} = x^_n + x_K; r_K is not needed
+    for (int e0 = C.bid * blockDim.x + t; e0 < C.nx; e0 += 2 * stride) {
+      const int e1 = e0 + stride;
+      const bool h1 = e1 < C.nx;
+      const float2 p0 = ldcg(p + e0), x0 = k > 0 ? ldcg(C.xcg + e0) : czero(), n0 = ldcg(C.xn + e0);
+      float2 p1 = czero(), x1 = czero(), n1v = czero();
+      if (h1) {
+        p1 = ldcg(p + e1);
+        if (k > 0) x1 = ldcg(C.xcg + e1);
+        n1v = ldcg(C.xn + e1);
       }
-      __syncthreads();
+      C.xn[e0] = cadd(n0, axpy2(p0, a, x0));
+      if (h1) C.xn[e1] = cadd(n1v, axpy2(p1, a, x1));
+    }
+    STG(3, 2);
+    return;
+  }
+  for (int e0 = C.bid * blockDim.x + t; e0 < C.nx; e0 += 2 * stride) {
+    const int e1 = e0 + stride;
+    const bool h1 = e1 < C.nx;
+    const float2 p0 = ldcg(p + e0), q0 = ldcg(C.q + e0), r0 = ldcg(rk + e0);
+    const float2 x0 = k > 0 ? ldcg(C.xcg + e0) : czero();
+    float2 p1 = czero(), q1 = czero(), r1 = czero(), x1 = czero();
+    if (h1) {
+      p1 = ldcg(p + e1);
+      q1 = ldcg(C.q + e1);
+      r1 = ldcg(rk + e1);
+      if (k > 0) x1 = ldcg(C.xcg + e1);
+    }
+    const float2 rv0 = axpy2(q0, na, r0);
+    rk1[e0] = rv0;
+    acc = fmaf(rv0.x, rv0.x, fmaf(rv0.y, rv0.y, acc));
+    C.xcg[e0] = axpy2(p0, a, x0);
+    if (h1) {
+      const float2 rv1 = axpy2(q1, na, r1);
+      rk1[e1] = rv1;
+      acc = fmaf(rv1.x, rv1.x, fmaf(rv1.y, rv1.y, acc));
+      C.xcg[e1] = axpy2(p1, a, x1);
     }
   }
-  for (int e = C.bid * blockDim.x + t; e < NN; e += C.nb * blockDim.x) update((size_t)e);
-  block_partial(C, (double)acc, (k & 1) ? SLOT_RR0 : SLOT_RR1, sred);
+  STG(3, 2);
+  STG(3, 3);
+  block_partial(C, acc, (k & 1) ? SLOT_RR0 : SLOT_RR1, sred);
+  STG(3, 4);
 }
 
 // x^_0 = x_prev (or rho = 1, c^ = 0), x_ref = damping * x_prev
 __device__ __forceinline__ void phase_init(const Ctx& C, const float2* xprev, float damping) {
   const int NN = C.N * C.N;
-  if (C.bid == 0 && threadIdx.x < NSLOT) C.cnt[threadIdx.x] = 0u;   // fresh reductions
   for (int e = C.bid * blockDim.x + threadIdx.x; e < C.nx; e += C.nb * blockDim.x) {
     float2 v = xprev ? ldcg(xprev + e) : make_float2(e < NN ? 1.f : 0.f, 0.f);
     C.xn[e] = v;
