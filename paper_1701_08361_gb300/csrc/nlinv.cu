@@ -75,10 +75,10 @@ __global__ void __launch_bounds__(K::BS) k_row_b(Ctx C0, int mode, const float2*
 
 template <class K>
 __global__ void __launch_bounds__(K::BS) k_col_c(Ctx C0, int mode, const float* P, const float2* Yin,
-                                                 float2* zout, float2* vio) {
+                                                 float2* zout, float2* vio, int k) {
   const Ctx C = whole_grid(C0);
   extern __shared__ float2 sm[];
-  phase_col_c<K>(C, sm, mode, P, Yin, zout, vio);
+  phase_col_c<K>(C, sm, mode, P, Yin, zout, vio, k);
 }
 
 template <class K>
@@ -96,7 +96,12 @@ __global__ void __launch_bounds__(K::BS) k_col_e(Ctx C0, int mode, float alpha, 
   const Ctx C = whole_grid(C0);
   extern __shared__ float2 sm[];
   __shared__ float2 sred[32];
-  phase_col_e<K>(C, sm, sred, mode, alpha, k, kbin, sin, p_old, p_new, out, hout, slot);
+  switch (mode) {
+    case E_CG: phase_col_e<K, E_CG>(C, sm, sred, alpha, k, kbin, sin, p_old, p_new, out, hout, slot); break;
+    case E_RHS: phase_col_e<K, E_RHS>(C, sm, sred, alpha, k, kbin, sin, p_old, p_new, out, hout, slot); break;
+    case E_DFH: phase_col_e<K, E_DFH>(C, sm, sred, alpha, k, kbin, sin, p_old, p_new, out, hout, slot); break;
+    default: phase_col_e<K, E_NORMAL>(C, sm, sred, alpha, k, kbin, sin, p_old, p_new, out, hout, slot);
+  }
 }
 
 template <class K>
@@ -163,7 +168,7 @@ __host__ __device__ __forceinline__ Ctx frame_ctx(Ctx C, size_t off) {
   NLINV_ADV(float2, pb[1]);
   NLINV_ADV(float2, part);
   NLINV_ADV(float2, Hr);
-  NLINV_ADV(float2, Hp);
+  NLINV_ADV(float2, vold);
 #undef NLINV_ADV
   return C;
 }
@@ -212,18 +217,18 @@ __device__ __forceinline__ void frame_body(const Ctx& C, float2* sm, float2* sre
     NLINV_SYNC();
     phase_row_d<K>(C, sm, C.xn, C.v, C.s, C.kb);
     NLINV_SYNC();
-    phase_col_e<K>(C, sm, sred, E_RHS, al, 0, C.kb, C.s, nullptr, nullptr, C.rb[0], C.Hr, SLOT_RR0);
+    phase_col_e<K, E_RHS>(C, sm, sred, al, 0, C.kb, C.s, nullptr, nullptr, C.rb[0], C.Hr, SLOT_RR0);
     NLINV_SYNC();
     for (int k = 0; k < Kcg; ++k) {
       float2* pk = C.pb[k & 1];
       const float2* pm = C.pb[(k + 1) & 1];
       phase_row_cg<K>(C, sm, sred, k, pm, pk, C.v);
       NLINV_SYNC();
-      phase_col_c<K>(C, sm, COL_TOEP, io.P, nullptr, nullptr, C.v);
+      phase_col_c<K>(C, sm, COL_CG, io.P, nullptr, nullptr, C.v, k);
       NLINV_SYNC();
       phase_row_d<K>(C, sm, C.xn, C.v, C.s, C.kb);
       NLINV_SYNC();
-      phase_col_e<K>(C, sm, sred, E_CG, al, k, C.kb, C.s, pm, pk, C.q, nullptr, SLOT_PQ);
+      phase_col_e<K, E_CG>(C, sm, sred, al, k, C.kb, C.s, pm, pk, C.q, nullptr, SLOT_PQ);
       NLINV_SYNC();
       phase_upd<K>(C, sm, sred, k, k == Kcg - 1, pk);
       NLINV_SYNC();
@@ -472,10 +477,10 @@ struct Launch {
     CKL("k_row_b");
     return NLINV_OK;
   }
-  int col_c(int mode, const float* P, const float2* Yin, float2* zout, float2* vio) const {
+  int col_c(int mode, const float* P, const float2* Yin, float2* zout, float2* vio, int k = 0) const {
     const Ctx& C = pl->C;
     const int g = plan_grid(C.J * ((C.G + K::TW - 1) / K::TW), 1);
-    k_col_c<K><<<pick(g), K::BS, K::SMEM, st>>>(C, mode, P, Yin, zout, vio);
+    k_col_c<K><<<pick(g), K::BS, K::SMEM, st>>>(C, mode, P, Yin, zout, vio, k);
     CKL("k_col_c");
     return NLINV_OK;
   }
@@ -623,7 +628,8 @@ int nlinv_plan(nlinv_plan_t* out, const nlinv_params_t* p, const float* psf, nli
   for (int i = 0; i < 7; ++i) take(nx * f2);  // 10..16 xn xref xcg r q p0 p1
   take((size_t)NSLOT * kMaxPart * sizeof(float2));  // 17 part
   take(nx * f2);                         // 18 r1 (second residual buffer)
-  for (int i = 0; i < 2; ++i) take((size_t)J * N * Gc * f2);  // 19..20 Hr Hp
+  take((size_t)J * N * Gc * f2);         // 19 Hr
+  take((size_t)J * N * G * f2);          // 20 vold
   pl->fstride = tot - shared_bytes;
   tot = shared_bytes + pl->fstride * (size_t)pl->max_batch;
   e = cudaMalloc(&pl->mem, tot);
@@ -663,7 +669,7 @@ int nlinv_plan(nlinv_plan_t* out, const nlinv_params_t* p, const float* psf, nli
   C.pb[1] = (float2*)(base + off[16]);
   C.part = (float2*)(base + off[17]);
   C.Hr = (float2*)(base + off[19]);
-  C.Hp = (float2*)(base + off[20]);
+  C.vold = (float2*)(base + off[20]);
   C.spin_limit = pl->prm.spin_limit;
 
   // host tables in FP64, rounded once
@@ -906,7 +912,7 @@ int nlinv_frame(nlinv_plan_t pl, const void* Y, int turn, const void* x_prev, vo
         float2* pk = C.pb[kk & 1];
         const float2* pm = C.pb[(kk + 1) & 1];
         RC(L.row_cg(kk, pm, pk, C.v));
-        RC(L.col_c(COL_TOEP, F.io.P, nullptr, nullptr, C.v));
+        RC(L.col_c(COL_CG, F.io.P, nullptr, nullptr, C.v, kk));
         RC(L.row_d(C.xn, C.v, C.s, C.kb));
         RC(L.col_e(E_CG, alpha, kk, C.kb, C.s, pm, pk, C.q, nullptr, SLOT_PQ));
         RC(L.upd(kk, kk == F.K - 1, pk));

@@ -79,7 +79,7 @@ enum { SLOT_PQ = 0, SLOT_RR0 = 1, SLOT_RR1 = 2, NSLOT = 4 };
 enum { DEV_ETIMEOUT = -4, DEV_ENUMERIC = -5 };
 
 enum RowMode { ROW_COIL = 0, ROW_COILONLY = 1, ROW_LIN = 2, ROW_IMG = 3 };
-enum ColMode { COL_TOEP = 0, COL_RHS = 1, COL_FWD = 2, COL_INV = 3 };
+enum ColMode { COL_TOEP = 0, COL_RHS = 1, COL_FWD = 2, COL_INV = 3, COL_CG = 4 };
 enum EMode { E_CG = 0, E_RHS = 1, E_DFH = 2, E_NORMAL = 3 };
 
 struct Ctx {
@@ -92,7 +92,8 @@ struct Ctx {
   float2 *xn, *xref, *xcg, *q;
   float2* rb[2];        // CG residual r_k lives in rb[k & 1]
   float2* pb[2];        // CG direction p_k lives in pb[k & 1]
-  float2 *Hr, *Hp;      // y pass of W^-1 applied to r, p: [J][N][Gc]
+  float2* Hr;           // y pass of W^-1 applied to r: [J][N][Gc]
+  float2* vold;         // row pass of the previous CG direction p_{k-1}: [J][N][G]
   float2* part;         // [NSLOT][kMaxPart] per-CTA partials (float pairs hi, lo)
   int* err;             // latched device error
   unsigned* bar;        // grid barrier counter
@@ -305,6 +306,22 @@ __device__ __forceinline__ double cg_step(double rr, double pq) {
   return (rr > 0.0 && pq > 0.0 && isfinite(pq)) ? rr / pq : 0.0;
 }
 
+// Work split of the phases that have a few items and an elementwise part:
+// when at least kElemCTAs CTAs would be left over, CTAs [0, items) take one
+// item each and the others the elementwise part, so the two run side by
+// side; otherwise every CTA takes both in turn.
+constexpr int kElemCTAs = 32;
+struct Roles {
+  bool items, elems;    // what this CTA does
+  int istride;          // item stride
+  int ebid, enb;        // this CTA's index / the CTA count of the elementwise part
+};
+__device__ __forceinline__ Roles roles(const Ctx& C, int items) {
+  if (items > 0 && items + kElemCTAs <= C.nb)
+    return C.bid < items ? Roles{true, false, items, 0, 1} : Roles{false, true, items, C.bid - items, C.nb - items};
+  return Roles{true, true, C.nb, C.bid, C.nb};
+}
+
 // ------------------------------------- B: W^-1 along x, product, row FFT
 // mode ROW_COIL    : c = W^-1 c^ stored, u = rho c
 //      ROW_COILONLY: c stored, nothing else
@@ -404,89 +421,74 @@ __device__ NLINV_PHASE void phase_row_b(const Ctx& C, float2* sm, int mode, cons
   }
 }
 
-// --------------------------- B in a CG iteration: direction update fused in
-// The y pass of W^-1 (H) of the CG direction is not recomputed: H r_k comes
-// exactly from the update phase (which transforms the rounded r_k), and
-//   H p_k = H r_k + beta_k H p_{k-1},  H p_0 = H r_0,
-// an addition without cancellation.  (Recurring H r_k = H r_{k-1} - a H q
-// instead would cancel catastrophically when |r| drops sharply and drift
-// away from r.)  p_rho,k = r_rho,k + beta_k p_rho,k-1 is formed on the fly
-// (channel 0 stores it into p_new).  Then as ROW_LIN:
-//   u = c p_rho + rho (x pass of W^-1 of H p), forward row FFT.
+// --------------------------- B in a CG iteration: the row pass of r_k
+// The row pass T (x pass of W^-1 on the y-transformed coil part, the
+// product u = c d_rho + rho W^-1 d_c, forward row FFT) is linear, so
+// T(p_k) = T(r_k) + beta_k T(p_{k-1}): the items transform r_k alone (its
+// y pass H r_k comes exactly from the update phase) and the column phase
+// adds beta_k T(p_{k-1}), an addition without cancellation (p_{k-1} is
+// conjugate to r_k).  The items thus need no CG scalar.  The CTAs left over
+// form p_k = r_k + beta_k p_{k-1} elementwise for the later phases.
 template <class K>
 __device__ NLINV_PHASE void phase_row_cg(const Ctx& C, float2* sm, float2* sred, int k, const float2* p_old,
                              float2* p_new, float2* vout) {
   constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW, RS = K::RS;
+  constexpr int EU = 4;   // elements per thread per round of the elementwise part
   const int N = C.N, Gc = C.Gc, J = C.J;
   const int t = threadIdx.x;
+  const float2* rk = C.rb[k & 1];
   STG_BEGIN();
-  const Scal2 beta = cta_beta(C, k);
-  STG(0, 0);
   const int groups = (N + TW - 1) / TW;
   const int items = J * groups;
-  for (int it = C.bid; it < items; it += C.nb) {
+  const Roles R = roles(C, items);
+  if (R.items) for (int it = C.bid; it < items; it += R.istride) {
     const int j = it / groups;
     const int y0 = (it - j * groups) * TW;
-    {  // stage 1: thread (row, n1): direction update of H p, inverse DFT over n2
-      const int rr = t / G1, n1 = t % G1, y = y0 + rr;
-      if (rr < TW && y < N) {
+    // stage-2 operands (r_rho, c_j, rho rows) are requested with stage 1's
+    const int rr = t / G2, k2 = t % G2, y = y0 + rr;
+    const bool ok = rr < TW && y < N;
+    float2 rv[G1 / 2], cv[G1 / 2], rh[G1 / 2];
+#pragma unroll
+    for (int k1 = 0; k1 < G1 / 2; ++k1) {
+      rv[k1] = cv[k1] = rh[k1] = czero();
+      if (ok) {
+        const int ir = y * N + k2 + G2 * k1;
+        rv[k1] = ldcg(rk + ir);
+        cv[k1] = ldcg(C.c + (size_t)j * N * N + ir);
+        rh[k1] = ldcg(C.xn + ir);
+      }
+    }
+    {  // stage 1: thread (row, n1): inverse DFT over n2 of the band of H r
+      const int r1 = t / G1, n1 = t % G1, y1 = y0 + r1;
+      if (r1 < TW && y1 < N) {
         float2 av[G2];
 #pragma unroll
-        for (int n2 = 0; n2 < G2; ++n2) {   // loads first ...
+        for (int n2 = 0; n2 < G2; ++n2) {
           const int ix = coef_index(n1 + G1 * n2, G, Gc);
-          float2 hp = czero();
-          if (ix >= 0) {
-            const size_t e = ((size_t)j * N + y) * Gc + ix;
-            const float2 hr = ldcg(C.Hr + e);
-            hp = (k == 0) ? hr : axpy2(ldcg(C.Hp + e), beta, hr);
-          }
-          av[n2] = hp;
-        }
-#pragma unroll
-        for (int n2 = 0; n2 < G2; ++n2) {   // ... then the stores
-          const int ix = coef_index(n1 + G1 * n2, G, Gc);
-          if (ix >= 0) C.Hp[((size_t)j * N + y) * Gc + ix] = av[n2];
+          av[n2] = ix >= 0 ? ldcg(C.Hr + ((size_t)j * N + y1) * Gc + ix) : czero();
         }
         dft<G2, true>(av);
 #pragma unroll
-        for (int k2 = 0; k2 < G2; ++k2) {
-          float2 x = av[k2];
-          if (k2) x = cmul(x, twg<true>(C.tw, n1 * k2));
-          sm[rr * RS + k2 * (G1 + 1) + n1] = x;
+        for (int q2 = 0; q2 < G2; ++q2) {
+          float2 x = av[q2];
+          if (q2) x = cmul(x, twg<true>(C.tw, n1 * q2));
+          sm[r1 * RS + q2 * (G1 + 1) + n1] = x;
         }
       }
     }
     __syncthreads();
     STG(0, 1);
     // stage 2: thread (row, k2): inverse DFT over n1 -> dc at x = k2 + G2 k1;
-    // u = c p_rho + rho dc; forward DFT over k1
-    const int rr = t / G2, k2 = t % G2, y = y0 + rr;
-    const bool ok = rr < TW && y < N;
+    // u = c r_rho + rho dc; forward DFT over k1
     float2 u[G1];
     if (ok) {
       float2 b[G1];
 #pragma unroll
-      for (int n1 = 0; n1 < G1; ++n1) b[n1] = sm[rr * RS + k2 * (G1 + 1) + n1];
+      for (int q1 = 0; q1 < G1; ++q1) b[q1] = sm[rr * RS + k2 * (G1 + 1) + q1];
       dft<G1, true>(b);
-      // every operand load of the row is issued before the first store
-      float2 pr[G1 / 2], cv[G1 / 2], rh[G1 / 2];
 #pragma unroll
-      for (int k1 = 0; k1 < G1 / 2; ++k1) {
-        const int x = k2 + G2 * k1;
-        const int ir = y * N + x;
-        const float2 rv = ldcg(C.rb[k & 1] + ir);
-        pr[k1] = (k == 0) ? rv : axpy2(ldcg(p_old + ir), beta, rv);
-        cv[k1] = ldcg(C.c + ((size_t)j * N + y) * N + x);
-        rh[k1] = ldcg(C.xn + ir);
-      }
-#pragma unroll
-      for (int k1 = 0; k1 < G1; ++k1) {
-        u[k1] = czero();
-        if (k1 < G1 / 2) {
-          if (j == 0) p_new[y * N + k2 + G2 * k1] = pr[k1];
-          u[k1] = cadd(cmul(cv[k1], pr[k1]), cmul(rh[k1], b[k1]));
-        }
-      }
+      for (int k1 = 0; k1 < G1; ++k1)
+        u[k1] = (k1 < G1 / 2) ? cadd(cmul(cv[k1], rv[k1]), cmul(rh[k1], b[k1])) : czero();
       dft<G1, false>(u);
 #pragma unroll
       for (int kb = 1; kb < G1; ++kb) u[kb] = cmul(u[kb], twg<false>(C.tw, k2 * kb));
@@ -513,39 +515,99 @@ __device__ NLINV_PHASE void phase_row_cg(const Ctx& C, float2* sm, float2* sred,
     __syncthreads();
     STG(0, 3);
   }
+  // p_k = r_k + beta_k p_{k-1} (p_0 = r_0) over the whole vector
+  if (R.elems) {
+    Scal2 beta{0.f, 0.f};
+    bool need_beta = k > 0;
+    const int stride = R.enb * blockDim.x;
+    for (int base = R.ebid * blockDim.x; base < C.nx; base += EU * stride) {   // CTA-uniform
+      float2 rv[EU], pv[EU];
+#pragma unroll
+      for (int u = 0; u < EU; ++u) {
+        const int e = base + t + u * stride;
+        rv[u] = pv[u] = czero();
+        if (e < C.nx) {
+          rv[u] = ldcg(rk + e);
+          if (k > 0) pv[u] = ldcg(p_old + e);
+        }
+      }
+      if (need_beta) {
+        beta = cta_beta(C, k);
+        need_beta = false;
+      }
+#pragma unroll
+      for (int u = 0; u < EU; ++u) {
+        const int e = base + t + u * stride;
+        if (e < C.nx) p_new[e] = (k > 0) ? axpy2(pv[u], beta, rv[u]) : rv[u];
+      }
+    }
+  }
 }
 
 // ------------------------------------------ C: column pass (PSF convolution)
+// COL_CG  : v = T(r_k) + beta_k T(p_{k-1}) = T(p_k), kept as the next
+//           T(p_{k-1}), then as COL_TOEP (T: the row pass of the CG phase)
 // COL_TOEP: FFT_y, x P / G^2, iFFT_y, keep N rows (in place in v)
 // COL_RHS : FFT_y, z = (Y - P X / G) / G, iFFT_y, keep N rows
 // COL_FWD : FFT_y, zout = X / G (full G rows), stop
 // COL_INV : X = Yin / G (full G rows given), iFFT_y, keep N rows
 template <class K>
 __device__ NLINV_PHASE void phase_col_c(const Ctx& C, float2* sm, int mode, const float* P,
-                            const float2* Yin, float2* zout, float2* vio) {
+                            const float2* Yin, float2* zout, float2* vio, int k = 0) {
   constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW;
   const int N = C.N, J = C.J;
   const int t = threadIdx.x;
   constexpr int tiles = (G + TW - 1) / TW;
   const int items = J * tiles;
   STG_BEGIN();
+  const bool cg = (mode == COL_CG);
+  if (cg) mode = COL_TOEP;
+  bool need_beta = cg && k > 0;
+  Scal2 beta{0.f, 0.f};
   for (int it = C.bid; it < items; it += C.nb) {
     const int j = it / tiles;
     const int x = (it - j * tiles) * TW + (t % TW);
     const bool colok = x < G;
+    const int k2 = t / TW, cc = t % TW;
+    const bool ok = k2 < G2 && colok;
+    // the PSF (and data) of this thread's stage-2 points are requested first
+    float pv[G1];
+    float2 yv[G1];
+#pragma unroll
+    for (int k1 = 0; k1 < G1; ++k1) {
+      pv[k1] = 0.f;
+      yv[k1] = czero();
+      const size_t kk = (size_t)(k2 + G2 * k1) * G + x;
+      if (ok && (mode == COL_TOEP || mode == COL_RHS)) pv[k1] = __ldg(P + kk);
+      if (ok && mode == COL_RHS) yv[k1] = ldcg(Yin + (size_t)j * G * G + kk);
+    }
     if (mode != COL_INV) {  // stage 1: thread (n1, c): forward DFT over n2 (y = n1 + G1 n2 < N)
       const int n1 = t / TW;
-      if (n1 < G1 && colok) {
-        float2 a[G2];
+      const bool ld = n1 < G1 && colok;
+      float2 a[G2], ao[G2 / 2];
 #pragma unroll
-        for (int n2 = 0; n2 < G2; ++n2)
-          a[n2] = (n2 < G2 / 2) ? ldcg(vio + ((size_t)j * N + n1 + G1 * n2) * G + x) : czero();
+      for (int n2 = 0; n2 < G2; ++n2) {
+        a[n2] = (ld && n2 < G2 / 2) ? ldcg(vio + ((size_t)j * N + n1 + G1 * n2) * G + x) : czero();
+        if (n2 < G2 / 2) ao[n2] = (ld && cg && k > 0) ? ldcg(C.vold + ((size_t)j * N + n1 + G1 * n2) * G + x) : czero();
+      }
+      if (need_beta) {   // CTA-uniform: first item of this CTA
+        beta = cta_beta(C, k);
+        need_beta = false;
+      }
+      if (ld && cg) {
+#pragma unroll
+        for (int n2 = 0; n2 < G2 / 2; ++n2) {
+          if (k > 0) a[n2] = axpy2(ao[n2], beta, a[n2]);
+          C.vold[((size_t)j * N + n1 + G1 * n2) * G + x] = a[n2];
+        }
+      }
+      if (ld) {
         dft<G2, false>(a);
 #pragma unroll
-        for (int k2 = 0; k2 < G2; ++k2) {
-          float2 v = a[k2];
-          if (k2) v = cmul(v, twg<false>(C.tw, n1 * k2));
-          sm[(k2 * G1 + n1) * TW + (t % TW)] = v;
+        for (int q2 = 0; q2 < G2; ++q2) {
+          float2 v = a[q2];
+          if (q2) v = cmul(v, twg<false>(C.tw, n1 * q2));
+          sm[(q2 * G1 + n1) * TW + (t % TW)] = v;
         }
       }
       __syncthreads();
@@ -553,8 +615,6 @@ __device__ NLINV_PHASE void phase_col_c(const Ctx& C, float2* sm, int mode, cons
     STG(1, 1);
     // stage 2: thread (k2, c): forward DFT over n1 -> k = k2 + G2 k1; the
     // pointwise step; inverse DFT over k1 (k = k2 + G2 k1 is the input index)
-    const int k2 = t / TW, cc = t % TW;
-    const bool ok = k2 < G2 && colok;
     float2 b[G1];
     if (ok) {
       if (mode == COL_INV) {
@@ -569,11 +629,10 @@ __device__ NLINV_PHASE void phase_col_c(const Ctx& C, float2* sm, int mode, cons
         for (int k1 = 0; k1 < G1; ++k1) {
           const size_t kk = (size_t)(k2 + G2 * k1) * G + x;
           if (mode == COL_TOEP) {
-            b[k1] = cscale(b[k1], __ldg(P + kk) * C.inv_G2);
+            b[k1] = cscale(b[k1], pv[k1] * C.inv_G2);
           } else if (mode == COL_RHS) {
-            const float2 yv = ldcg(Yin + (size_t)j * G * G + kk);
-            const float pk = __ldg(P + kk) * C.inv_G;
-            b[k1] = cscale(make_float2(fmaf(-pk, b[k1].x, yv.x), fmaf(-pk, b[k1].y, yv.y)), C.inv_G);
+            const float pk = pv[k1] * C.inv_G;
+            b[k1] = cscale(make_float2(fmaf(-pk, b[k1].x, yv[k1].x), fmaf(-pk, b[k1].y, yv[k1].y)), C.inv_G);
           } else {  // COL_FWD
             zout[(size_t)j * G * G + kk] = cscale(b[k1], C.inv_G);
           }
@@ -624,39 +683,43 @@ __device__ NLINV_PHASE void phase_row_d(const Ctx& C, float2* sm, const float2* 
   for (int it = C.bid; it < items; it += C.nb) {
     const int j = it / groups;
     const int y0 = (it - j * groups) * TW;
+    // stage-2 operands (c_j and rho rows) requested before stage 1 waits
+    const int rr = t / G2, k2 = t % G2, y = y0 + rr;
+    const bool ok = rr < TW && y < N;
+    float2 cv[G1 / 2], rh[G1 / 2];
+#pragma unroll
+    for (int k1 = 0; k1 < G1 / 2; ++k1) {
+      cv[k1] = rh[k1] = czero();
+      if (ok) {
+        const int ir = y * N + k2 + G2 * k1;
+        cv[k1] = ldcg(C.c + (size_t)j * N * N + ir);
+        rh[k1] = ldcg(rho + ir);
+      }
+    }
     {  // stage 1: thread (row, n1): inverse DFT over n2
-      const int rr = t / G1, n1 = t % G1, y = y0 + rr;
-      if (rr < TW && y < N) {
+      const int r1 = t / G1, n1 = t % G1, y1 = y0 + r1;
+      if (r1 < TW && y1 < N) {
         float2 a[G2];
-        const float2* src = win + ((size_t)j * N + y) * G;
+        const float2* src = win + ((size_t)j * N + y1) * G;
 #pragma unroll
         for (int n2 = 0; n2 < G2; ++n2) a[n2] = ldcg(src + n1 + G1 * n2);
         dft<G2, true>(a);
 #pragma unroll
-        for (int k2 = 0; k2 < G2; ++k2) {
-          float2 x = a[k2];
-          if (k2) x = cmul(x, twg<true>(C.tw, n1 * k2));
-          sm[rr * RS + k2 * (G1 + 1) + n1] = x;
+        for (int q2 = 0; q2 < G2; ++q2) {
+          float2 x = a[q2];
+          if (q2) x = cmul(x, twg<true>(C.tw, n1 * q2));
+          sm[r1 * RS + q2 * (G1 + 1) + n1] = x;
         }
       }
     }
     __syncthreads();
     // stage 2: thread (row, k2): inverse DFT over n1 -> t_j at x = k2 + G2 k1
-    const int rr = t / G2, k2 = t % G2, y = y0 + rr;
-    const bool ok = rr < TW && y < N;
     float2 g[G1];
     if (ok) {
       float2 b[G1];
 #pragma unroll
       for (int n1 = 0; n1 < G1; ++n1) b[n1] = sm[rr * RS + k2 * (G1 + 1) + n1];
       dft<G1, true>(b);
-      float2 cv[G1 / 2], rh[G1 / 2];
-#pragma unroll
-      for (int k1 = 0; k1 < G1 / 2; ++k1) {   // loads first, stores after
-        const int x = k2 + G2 * k1;
-        cv[k1] = ldcg(C.c + ((size_t)j * N + y) * N + x);
-        rh[k1] = ldcg(rho + y * N + x);
-      }
 #pragma unroll
       for (int k1 = 0; k1 < G1; ++k1) {
         g[k1] = czero();
@@ -695,15 +758,14 @@ __device__ NLINV_PHASE void phase_row_d(const Ctx& C, float2* sm, const float2* 
 }
 
 // ----------------- E: W^-H along y, D_W^-1, channel sum, Tikhonov, Re<p,q>
-// E_CG    : p_k,c = r_c + beta_k p_{k-1},c formed on the fly (into p_new);
-//           q = A p_k + alpha p_k, partial Re<p_k, q>
+// E_CG    : q = A p_k + alpha p_k (p_k in p_new), partial Re<p_k, q>
 // E_RHS   : out = r = DF^H(...) - alpha (x_n - x_ref), partial |r|^2; hout = H r
 // E_DFH   : out = DF^H z
 // E_NORMAL: out = (DF^H P DF + alpha) dx                      (dx = p_new)
 // H is the y pass of W^-1 (as phase A computes it); for E_RHS the column
 // values are still in registers, so it costs one more exchange.
-template <class K>
-__device__ NLINV_PHASE void phase_col_e(const Ctx& C, float2* sm, float2* sred, int mode, float alpha, int k,
+template <class K, int mode>
+__device__ NLINV_PHASE void phase_col_e(const Ctx& C, float2* sm, float2* sred, float alpha, int k,
                             const float2* kbin, const float2* sin, const float2* p_old,
                             float2* p_new, float2* out, float2* hout, int slot) {
   constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW;
@@ -711,61 +773,63 @@ __device__ NLINV_PHASE void phase_col_e(const Ctx& C, float2* sm, float2* sred, 
   const int t = threadIdx.x;
   const bool withH = (mode == E_RHS);
   STG_BEGIN();
-  const Scal2 beta = (mode == E_CG) ? cta_beta(C, k) : Scal2{0.f, 0.f};
-  STG(2, 0);
   const int tiles = (Gc + TW - 1) / TW;
   const int items = J * tiles;
+  const Roles R = roles(C, items);
   float acc = 0.f;   // this thread's few terms; CTA and grid sums in FP64
-  for (int it = C.bid; it < items; it += C.nb) {
+  if (R.items) for (int it = C.bid; it < items; it += R.istride) {
     const int j = it / tiles;
     const int fx = (it - j * tiles) * TW + (t % TW);
     const bool colok = fx < Gc;
-    {  // stage 1: thread (n1, c): forward DFT over n2 (rows y < N)
-      const int n1 = t / TW;
-      if (n1 < G1) {
-        float2 a[G2];
+    // every operand of the item is requested before anything waits: the
+    // kb column (stage 1 mapping), then D_W^-1 and the CG / Tikhonov operands
+    // of the kept rows (stage 2 mapping); beta's partials after them
+    const int n1 = t / TW;
+    float2 a[G2];
 #pragma unroll
-        for (int n2 = 0; n2 < G2; ++n2)
-          a[n2] = (colok && n2 < G2 / 2) ? ldcg(kbin + ((size_t)j * N + n1 + G1 * n2) * Gc + fx)
-                                         : czero();
-        dft<G2, false>(a);
+    for (int n2 = 0; n2 < G2; ++n2)
+      a[n2] = (n1 < G1 && colok && n2 < G2 / 2) ? ldcg(kbin + ((size_t)j * N + n1 + G1 * n2) * Gc + fx)
+                                                 : czero();
+    const int k2 = t / TW, cc = t % TW;
+    const bool ok = k2 < G2 && colok;
+    float2 o1[G1], o2[G1];
+    float dv[G1];
 #pragma unroll
-        for (int k2 = 0; k2 < G2; ++k2) {
-          float2 v = a[k2];
-          if (k2) v = cmul(v, twg<false>(C.tw, n1 * k2));
-          sm[(k2 * G1 + n1) * TW + (t % TW)] = v;
+    for (int k1 = 0; k1 < G1; ++k1) {
+      const int iy = coef_index(k2 + G2 * k1, G, Gc);
+      o1[k1] = o2[k1] = czero();
+      dv[k1] = 0.f;
+      if (ok && iy >= 0) {
+        const size_t e = (size_t)NN + ((size_t)j * Gc + iy) * Gc + fx;
+        dv[k1] = __ldg(C.dinv + iy * Gc + fx);
+        if (mode == E_CG || mode == E_NORMAL) {
+          o1[k1] = ldcg(p_new + e);
+        } else if (mode == E_RHS) {
+          o1[k1] = ldcg(C.xn + e);
+          o2[k1] = ldcg(C.xref + e);
         }
+      }
+    }
+    STG(2, 0);
+    if (n1 < G1) {  // stage 1: thread (n1, c): forward DFT over n2 (rows y < N)
+      dft<G2, false>(a);
+#pragma unroll
+      for (int q2 = 0; q2 < G2; ++q2) {
+        float2 v = a[q2];
+        if (q2) v = cmul(v, twg<false>(C.tw, n1 * q2));
+        sm[(q2 * G1 + n1) * TW + (t % TW)] = v;
       }
     }
     __syncthreads();
     STG(2, 1);
     // stage 2: thread (k2, c): forward DFT over n1, crop rows to G_c, the
-    // pointwise epilogue; then (E_CG/E_RHS) D_W^-1 and the inverse DFT over
-    // k1 of the new column for H
-    const int k2 = t / TW, cc = t % TW;
-    const bool ok = k2 < G2 && colok;
+    // pointwise epilogue; then (E_RHS) D_W^-1 and the inverse DFT over k1 of
+    // the new column for H
     float2 b[G1];
     if (ok) {
 #pragma unroll
-      for (int n1 = 0; n1 < G1; ++n1) b[n1] = sm[(k2 * G1 + n1) * TW + cc];
+      for (int q1 = 0; q1 < G1; ++q1) b[q1] = sm[(k2 * G1 + q1) * TW + cc];
       dft<G1, false>(b);
-      // the operands of all kept rows are loaded before any store
-      float2 opd[G1];
-#pragma unroll
-      for (int k1 = 0; k1 < G1; ++k1) {
-        const int iy = coef_index(k2 + G2 * k1, G, Gc);
-        opd[k1] = czero();
-        if (iy < 0) continue;
-        const size_t e = (size_t)NN + ((size_t)j * Gc + iy) * Gc + fx;
-        if (mode == E_CG) {
-          const float2 rv = ldcg(C.rb[k & 1] + e);
-          opd[k1] = (k == 0) ? rv : axpy2(ldcg(p_old + e), beta, rv);
-        } else if (mode == E_RHS) {
-          opd[k1] = csub(ldcg(C.xn + e), ldcg(C.xref + e));
-        } else if (mode == E_NORMAL) {
-          opd[k1] = ldcg(p_new + e);
-        }
-      }
 #pragma unroll
       for (int k1 = 0; k1 < G1; ++k1) {
         const int iy = coef_index(k2 + G2 * k1, G, Gc);
@@ -774,24 +838,21 @@ __device__ NLINV_PHASE void phase_col_e(const Ctx& C, float2* sm, float2* sred, 
           continue;
         }
         const size_t e = (size_t)NN + ((size_t)j * Gc + iy) * Gc + fx;
-        const float dv = __ldg(C.dinv + iy * Gc + fx);
-        const float2 val = cscale(b[k1], C.inv_G * dv);
+        const float2 val = cscale(b[k1], C.inv_G * dv[k1]);
         float2 res;
         if (mode == E_CG) {
-          const float2 p = opd[k1];
-          p_new[e] = p;
-          res = cfma(p, alpha, val);
-          acc = fmaf(p.x, res.x, fmaf(p.y, res.y, acc));
+          res = cfma(o1[k1], alpha, val);
+          acc = fmaf(o1[k1].x, res.x, fmaf(o1[k1].y, res.y, acc));
         } else if (mode == E_RHS) {
-          res = cfma(opd[k1], -alpha, val);
+          res = cfma(csub(o1[k1], o2[k1]), -alpha, val);
           acc = fmaf(res.x, res.x, fmaf(res.y, res.y, acc));
         } else if (mode == E_DFH) {
           res = val;
         } else {
-          res = cfma(opd[k1], alpha, val);
+          res = cfma(o1[k1], alpha, val);
         }
         out[e] = res;
-        b[k1] = cscale(res, dv);
+        b[k1] = cscale(res, dv[k1]);
       }
       if (withH) {
         dft<G1, true>(b);
@@ -822,24 +883,29 @@ __device__ NLINV_PHASE void phase_col_e(const Ctx& C, float2* sm, float2* sred, 
     __syncthreads();
   }
   STG(2, 2);
-  // rho part: channel sum of s_j = conj(c_j) t_j
-  for (int e = C.bid * blockDim.x + t; e < NN; e += C.nb * blockDim.x) {
+  // rho part: channel sum of s_j = conj(c_j) t_j (needs no CG scalar)
+  if (R.elems) for (int e = R.ebid * blockDim.x + t; e < NN; e += R.enb * blockDim.x) {
+    float2 o = czero(), o2v = czero();
+    if (mode == E_CG || mode == E_NORMAL) o = ldcg(p_new + e);
+    if (mode == E_RHS) {
+      o = ldcg(C.xn + e);
+      o2v = ldcg(C.xref + e);
+    }
     float2 sv = czero();
+#pragma unroll 8
     for (int j = 0; j < J; ++j) sv = cadd(sv, ldcg(sin + (size_t)j * NN + e));
     if (mode == E_CG) {
-      const float2 p = ldcg(p_new + e);
-      const float2 qv = cfma(p, alpha, sv);
+      const float2 qv = cfma(o, alpha, sv);
       out[e] = qv;
-      acc = fmaf(p.x, qv.x, fmaf(p.y, qv.y, acc));
+      acc = fmaf(o.x, qv.x, fmaf(o.y, qv.y, acc));
     } else if (mode == E_RHS) {
-      const float2 d = csub(ldcg(C.xn + e), ldcg(C.xref + e));
-      const float2 bv = cfma(d, -alpha, sv);
+      const float2 bv = cfma(csub(o, o2v), -alpha, sv);
       out[e] = bv;
       acc = fmaf(bv.x, bv.x, fmaf(bv.y, bv.y, acc));
     } else if (mode == E_DFH) {
       out[e] = sv;
     } else {
-      out[e] = cfma(ldcg(p_new + e), alpha, sv);
+      out[e] = cfma(o, alpha, sv);
     }
   }
   STG(2, 3);
@@ -848,73 +914,84 @@ __device__ NLINV_PHASE void phase_col_e(const Ctx& C, float2* sm, float2* sred, 
 }
 
 // -------------------------------------------------- F: CG vector update
-// a = |r_k|^2 / Re<p_k, A p_k> (FP64); x += a p_k; r_{k+1} = r_k - a q; partial
-// |r_{k+1}|^2; and H r_{k+1} (the y pass of W^-1 of the rounded new r) for
-// the next direction.  Coil columns are handled per (channel, column tile)
-// so the transform stays on chip; rho elementwise.  On the last iteration
-// x^_{n+1} = x^_n + x is applied and H is not needed.
+// a = |r_k|^2 / Re<p_k, A p_k> (FP64); x += a p_k; r_{k+1} = r_k - a q;
+// partial |r_{k+1}|^2; and H r_{k+1} (the y pass of W^-1 of the rounded new
+// r) for the next direction.  r_k and r_{k+1} live in different buffers, so
+// the column items (per channel and column tile, transform on chip) form
+// r_{k+1} of their column in registers, exactly as the elementwise part
+// stores it, while other CTAs already store r_{k+1}.  On the last iteration
+// only x^_{n+1} = x^_n + x is applied.
 template <class K>
 __device__ NLINV_PHASE void phase_upd(const Ctx& C, float2* sm, float2* sred, int k, bool last,
                                        const float2* p) {
   constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW;
+  constexpr int EU = 4;   // elements per thread per round of the elementwise part
   const int N = C.N, Gc = C.Gc, J = C.J, NN = N * N;
   const int t = threadIdx.x;
-  STG_BEGIN();
-  __shared__ Scal2 s_a;
-  if (t < 32) {
-    const DF32 rrs = slot_sum(C, (k & 1) ? SLOT_RR1 : SLOT_RR0);
-    const DF32 pqs = slot_sum(C, SLOT_PQ);
-    if (t == 0) {
-      const double rr = df_to_double(rrs);
-      const double a64 = cg_step(rr, df_to_double(pqs));
-      if (rr > 0.0 && a64 == 0.0 && C.bid == 0) raise_err(C, DEV_ENUMERIC);
-      const float hi = (float)a64;
-      s_a = Scal2{hi, (float)(a64 - (double)hi)};
-    }
-  }
-  __syncthreads();
-  const Scal2 a = s_a, na = Scal2{-s_a.hi, -s_a.lo};
-  STG(3, 0);
-  float acc = 0.f;   // this thread's few terms; CTA and grid sums in FP64
-  // r_k is read from one buffer and r_{k+1} written to the other, so the
-  // column items below may read r_k while other CTAs already store r_{k+1}
   const float2* rk = C.rb[k & 1];
   float2* rk1 = C.rb[(k + 1) & 1];
-  // (1) H r_{k+1} per coil column tile: the new residual r - a q of the tile
-  //     is formed in registers exactly as the flat pass below stores it,
-  //     transformed, and only the transform is stored (loads only before it)
+  STG_BEGIN();
+  __shared__ Scal2 s_a;
+  Scal2 a{0.f, 0.f}, na{0.f, 0.f};
+  bool need_a = true;
+  // the step length, once per CTA and only after its first loads are issued
+  auto get_a = [&]() {
+    if (!need_a) return;
+    need_a = false;
+    if (t < 32) {
+      const DF32 rrs = slot_sum(C, (k & 1) ? SLOT_RR1 : SLOT_RR0);
+      const DF32 pqs = slot_sum(C, SLOT_PQ);
+      if (t == 0) {
+        const double rr = df_to_double(rrs);
+        const double a64 = cg_step(rr, df_to_double(pqs));
+        if (rr > 0.0 && a64 == 0.0) raise_err(C, DEV_ENUMERIC);
+        const float hi = (float)a64;
+        s_a = Scal2{hi, (float)(a64 - (double)hi)};
+      }
+    }
+    __syncthreads();
+    a = s_a;
+    na = Scal2{-a.hi, -a.lo};
+  };
   const int tiles = (Gc + TW - 1) / TW;
   const int items = last ? 0 : J * tiles;
-  for (int it = C.bid; it < items; it += C.nb) {
+  const Roles R = roles(C, items);
+  float acc = 0.f;   // this thread's few terms; CTA and grid sums in FP64
+  // (1) H r_{k+1} per coil column tile
+  if (R.items) for (int it = C.bid; it < items; it += R.istride) {
     const int j = it / tiles;
     const int fx = (it - j * tiles) * TW + (t % TW);
     const bool colok = fx < Gc;
     const int n1 = t / TW;
-    if (n1 < G1) {  // stage 1: thread (n1, c): new residual of the column, inverse DFT over n2
-      float2 av[G2];
+    float2 rv[G2], qv[G2];
+    float dv[G2];
 #pragma unroll
-      for (int n2 = 0; n2 < G2; ++n2) {
-        const int iy = coef_index(n1 + G1 * n2, G, Gc);
-        av[n2] = (colok && iy >= 0) ? ldcg(rk + (size_t)NN + ((size_t)j * Gc + iy) * Gc + fx) : czero();
-      }
-#pragma unroll
-      for (int n2 = 0; n2 < G2; ++n2) {
-        const int iy = coef_index(n1 + G1 * n2, G, Gc);
-        if (colok && iy >= 0) {
-          const float2 qv = ldcg(C.q + (size_t)NN + ((size_t)j * Gc + iy) * Gc + fx);
-          av[n2] = cscale(axpy2(qv, na, av[n2]), __ldg(C.dinv + iy * Gc + fx));
-        }
-      }
-      dft<G2, true>(av);
-#pragma unroll
-      for (int k2 = 0; k2 < G2; ++k2) {
-        float2 x = av[k2];
-        if (k2) x = cmul(x, twg<true>(C.tw, n1 * k2));
-        sm[(k2 * G1 + n1) * TW + (t % TW)] = x;
+    for (int n2 = 0; n2 < G2; ++n2) {
+      const int iy = coef_index(n1 + G1 * n2, G, Gc);
+      rv[n2] = qv[n2] = czero();
+      dv[n2] = 0.f;
+      if (n1 < G1 && colok && iy >= 0) {
+        const size_t e = (size_t)NN + ((size_t)j * Gc + iy) * Gc + fx;
+        rv[n2] = ldcg(rk + e);
+        qv[n2] = ldcg(C.q + e);
+        dv[n2] = __ldg(C.dinv + iy * Gc + fx);
       }
     }
-    STG(3, 1);
+    get_a();
+    STG(3, 0);
+    if (n1 < G1) {  // stage 1: thread (n1, c): D_W^-1 r_{k+1} of the column, inverse DFT over n2
+#pragma unroll
+      for (int n2 = 0; n2 < G2; ++n2) rv[n2] = cscale(axpy2(qv[n2], na, rv[n2]), dv[n2]);
+      dft<G2, true>(rv);
+#pragma unroll
+      for (int q2 = 0; q2 < G2; ++q2) {
+        float2 x = rv[q2];
+        if (q2) x = cmul(x, twg<true>(C.tw, n1 * q2));
+        sm[(q2 * G1 + n1) * TW + (t % TW)] = x;
+      }
+    }
     __syncthreads();
+    STG(3, 1);
     const int k2 = t / TW, cc = t % TW;
     if (k2 < G2 && colok) {  // stage 2: inverse DFT over n1, keep y < N
       float2 b[G1];
@@ -927,51 +1004,46 @@ __device__ NLINV_PHASE void phase_upd(const Ctx& C, float2* sm, float2* sred, in
     }
     __syncthreads();
   }
-  // (2) every element of x and r, all CTAs: loads of a batch before its stores
-  const int stride = C.nb * blockDim.x;
-  if (last) {  // x^_{n+1} = x^_n + x_K; r_K is not needed
-    for (int e0 = C.bid * blockDim.x + t; e0 < C.nx; e0 += 2 * stride) {
-      const int e1 = e0 + stride;
-      const bool h1 = e1 < C.nx;
-      const float2 p0 = ldcg(p + e0), x0 = k > 0 ? ldcg(C.xcg + e0) : czero(), n0 = ldcg(C.xn + e0);
-      float2 p1 = czero(), x1 = czero(), n1v = czero();
-      if (h1) {
-        p1 = ldcg(p + e1);
-        if (k > 0) x1 = ldcg(C.xcg + e1);
-        n1v = ldcg(C.xn + e1);
+  // (2) every element of x and r: a round's loads before the scalar and stores
+  if (R.elems) {
+    const int stride = R.enb * blockDim.x;
+    for (int base = R.ebid * blockDim.x; base < C.nx; base += EU * stride) {   // CTA-uniform
+      float2 pv[EU], qv[EU], rv[EU], xv[EU];
+#pragma unroll
+      for (int u = 0; u < EU; ++u) {
+        const int e = base + t + u * stride;
+        pv[u] = qv[u] = rv[u] = xv[u] = czero();
+        if (e < C.nx) {
+          pv[u] = ldcg(p + e);
+          if (k > 0) xv[u] = ldcg(C.xcg + e);
+          if (last) {
+            rv[u] = ldcg(C.xn + e);
+          } else {
+            qv[u] = ldcg(C.q + e);
+            rv[u] = ldcg(rk + e);
+          }
+        }
       }
-      C.xn[e0] = cadd(n0, axpy2(p0, a, x0));
-      if (h1) C.xn[e1] = cadd(n1v, axpy2(p1, a, x1));
-    }
-    STG(3, 2);
-    return;
-  }
-  for (int e0 = C.bid * blockDim.x + t; e0 < C.nx; e0 += 2 * stride) {
-    const int e1 = e0 + stride;
-    const bool h1 = e1 < C.nx;
-    const float2 p0 = ldcg(p + e0), q0 = ldcg(C.q + e0), r0 = ldcg(rk + e0);
-    const float2 x0 = k > 0 ? ldcg(C.xcg + e0) : czero();
-    float2 p1 = czero(), q1 = czero(), r1 = czero(), x1 = czero();
-    if (h1) {
-      p1 = ldcg(p + e1);
-      q1 = ldcg(C.q + e1);
-      r1 = ldcg(rk + e1);
-      if (k > 0) x1 = ldcg(C.xcg + e1);
-    }
-    const float2 rv0 = axpy2(q0, na, r0);
-    rk1[e0] = rv0;
-    acc = fmaf(rv0.x, rv0.x, fmaf(rv0.y, rv0.y, acc));
-    C.xcg[e0] = axpy2(p0, a, x0);
-    if (h1) {
-      const float2 rv1 = axpy2(q1, na, r1);
-      rk1[e1] = rv1;
-      acc = fmaf(rv1.x, rv1.x, fmaf(rv1.y, rv1.y, acc));
-      C.xcg[e1] = axpy2(p1, a, x1);
+      get_a();
+#pragma unroll
+      for (int u = 0; u < EU; ++u) {
+        const int e = base + t + u * stride;
+        if (e < C.nx) {
+          const float2 xn = axpy2(pv[u], a, xv[u]);
+          if (last) {
+            C.xn[e] = cadd(rv[u], xn);
+          } else {
+            const float2 r1 = axpy2(qv[u], na, rv[u]);
+            rk1[e] = r1;
+            acc = fmaf(r1.x, r1.x, fmaf(r1.y, r1.y, acc));
+            C.xcg[e] = xn;
+          }
+        }
+      }
     }
   }
   STG(3, 2);
-  STG(3, 3);
-  block_partial(C, acc, (k & 1) ? SLOT_RR0 : SLOT_RR1, sred);
+  if (!last) block_partial(C, acc, (k & 1) ? SLOT_RR0 : SLOT_RR1, sred);
   STG(3, 4);
 }
 
