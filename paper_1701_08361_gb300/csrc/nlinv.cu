@@ -224,7 +224,7 @@ __device__ __forceinline__ void frame_body(const Ctx& C, float2* sm, float2* sre
       const float2* pm = C.pb[(k + 1) & 1];
       phase_row_cg<K>(C, sm, sred, k, pm, pk, C.v);
       NLINV_SYNC();
-      phase_col_c<K>(C, sm, COL_CG, io.P, nullptr, nullptr, C.v, k);
+      phase_col_cg<K>(C, sm, io.P, C.v, k);
       NLINV_SYNC();
       phase_row_d<K>(C, sm, C.xn, C.v, C.s, C.kb);
       NLINV_SYNC();

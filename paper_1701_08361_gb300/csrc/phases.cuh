@@ -108,19 +108,40 @@ template <int G1_, int G2_> struct Cfg {
   static constexpr int TW = NLINV_TW;       // columns per tile / rows per group
   static constexpr int BS = TW * MX;        // threads per CTA
   static constexpr int RS = G + MX;         // smem stride of one row (float2)
-  static constexpr int SMEM = TW * RS * 8;  // dynamic smem bytes
+  static constexpr int NR = G / 2;          // image rows N (G = 2N)
+  static constexpr int SMEM_X = TW * RS * 8;  // exchange buffer bytes
   // CTAs per SM the persistent kernel is compiled for (caps registers)
 #ifdef NLINV_MINB
   static constexpr int MINB = NLINV_MINB;
 #else
   static constexpr int MINB = BS <= 256 ? 2 : 1;
 #endif
+  // staged operands of one column item of the CG column pass: T(r_k) and
+  // T(p_{k-1}) tiles [N][TW] and the PSF tile [G][TW].  One staging buffer:
+  // a second one (a full item ahead) measured slower, as the larger shared
+  // memory carve-out shrinks the L1 cache that holds the register spills.
+  static constexpr int CT = 2 * NR * TW * 8 + G * TW * 4;
+  static constexpr int SMEM_LIM = MINB == 1 ? 227 * 1024 : 228 * 1024 / MINB - 1024;
+  static constexpr int NBUF = 1;
+  static constexpr int SMEM = SMEM_X + NBUF * CT;  // dynamic smem bytes
+  static_assert(SMEM <= SMEM_LIM, "staging buffer does not fit");
+  static_assert(TW % 4 == 0 && (G % 4) == 0, "16-byte staging chunks");
   static_assert(G1 % 2 == 0 && G2 % 2 == 0, "G1, G2 must be even");
   // the FP64 block reductions use full-warp shuffles over blockDim / 32 warps
   static_assert(BS % 32 == 0, "threads per CTA must be a whole number of warps");
 };
 
 __device__ __forceinline__ float2 ldcg(const float2* p) { return __ldcg(p); }
+
+// The thread index as a value the compiler must read anew in every phase:
+// with all phases inlined into one persistent kernel, index arithmetic that
+// is invariant over the CG loop would otherwise be hoisted out of it and
+// held live (or spilled) across every phase.
+__device__ __forceinline__ int phase_tid() {
+  int t;
+  asm volatile("mov.u32 %0, %%tid.x;" : "=r"(t));
+  return t;
+}
 
 // A CG scalar (computed in FP64) as an unevaluated float pair hi + lo, so
 // that y + s x keeps s to ~48 bits at the cost of two FP32 FMAs (FP64
@@ -254,7 +275,7 @@ template <class K>
 __device__ NLINV_PHASE void phase_coil_y(const Ctx& C, float2* sm, const float2* src, float2* hout) {
   constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW;
   const int N = C.N, Gc = C.Gc, J = C.J;
-  const int t = threadIdx.x;
+  const int t = phase_tid();
   const int tiles = (Gc + TW - 1) / TW;
   const int items = J * tiles;
   for (int it = C.bid; it < items; it += C.nb) {
@@ -333,7 +354,7 @@ __device__ NLINV_PHASE void phase_row_b(const Ctx& C, float2* sm, int mode, cons
                             float2* vout) {
   constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW, RS = K::RS;
   const int N = C.N, Gc = C.Gc, J = C.J;
-  const int t = threadIdx.x;
+  const int t = phase_tid();
   const int groups = (N + TW - 1) / TW;
   const int items = J * groups;
   for (int it = C.bid; it < items; it += C.nb) {
@@ -435,7 +456,7 @@ __device__ NLINV_PHASE void phase_row_cg(const Ctx& C, float2* sm, float2* sred,
   constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW, RS = K::RS;
   constexpr int EU = 4;   // elements per thread per round of the elementwise part
   const int N = C.N, Gc = C.Gc, J = C.J;
-  const int t = threadIdx.x;
+  const int t = phase_tid();
   const float2* rk = C.rb[k & 1];
   STG_BEGIN();
   const int groups = (N + TW - 1) / TW;
@@ -544,6 +565,140 @@ __device__ NLINV_PHASE void phase_row_cg(const Ctx& C, float2* sm, float2* sred,
   }
 }
 
+// ------------------------------------------------- asynchronous staging
+// global -> shared copies in 16-byte chunks through L2 only (cp.async.cg),
+// grouped per column item so that later items' copies overlap earlier work
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int n>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(n) : "memory");
+}
+
+// ------------------------------ C in a CG iteration: staged column pass
+// Per (channel, column tile): T(p_k) = T(r_k) + beta_k T(p_{k-1}) (kept in
+// vold for the next iteration), FFT_y, x P / G^2, iFFT_y, keep N rows (in
+// place in v).  An item's operands are staged into shared memory with
+// asynchronous copies (the first item's at the start of the phase, while
+// beta's partials are read; the next item's as soon as the buffer is free,
+// overlapping the last transform stage).
+template <class K>
+__device__ NLINV_PHASE void phase_col_cg(const Ctx& C, float2* sm, const float* P, float2* vio, int k) {
+  constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW, NR = K::NR, BS = K::BS, NBUF = K::NBUF;
+  constexpr int tiles = (G + TW - 1) / TW;
+  constexpr int CTF = K::CT / 8;   // float2 per staging buffer
+  const int J = C.J;
+  const int t = phase_tid();
+  const int items = J * tiles;
+  float2* const stg = sm + K::SMEM_X / 8;
+  STG_BEGIN();
+  // copies of item number n of this CTA into buffer n % NBUF (an empty group
+  // when there is no such item, so the group count stays uniform)
+  auto stage = [&](int n) {
+    const int it = C.bid + n * C.nb;
+    if (it < items) {
+      const int j = it / tiles, x0 = (it - j * tiles) * TW;
+      const int wv = G - x0 < TW ? G - x0 : TW;   // valid columns, a multiple of 4
+      float2* sv = stg + (n % NBUF) * CTF;
+      float2* so = sv + NR * TW;
+      float* sp = (float*)(so + NR * TW);
+      constexpr int CPR = TW / 2;   // chunks per row of a complex tile
+      for (int i = t; i < NR * CPR; i += BS) {
+        const int r = i / CPR, c = (i % CPR) * 2;
+        if (c < wv) {
+          const size_t g = ((size_t)j * NR + r) * G + x0 + c;
+          cp_async16(sv + r * TW + c, vio + g);
+          if (k > 0) cp_async16(so + r * TW + c, C.vold + g);
+        }
+      }
+      constexpr int CPP = TW / 4;   // chunks per row of the PSF tile
+      for (int i = t; i < G * CPP; i += BS) {
+        const int r = i / CPP, c = (i % CPP) * 4;
+        if (c < wv) cp_async16(sp + r * TW + c, P + (size_t)r * G + x0 + c);
+      }
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int n = 0; n < NBUF; ++n) stage(n);
+  const Scal2 beta = (k > 0 && C.bid < items) ? cta_beta(C, k) : Scal2{0.f, 0.f};   // CTA-uniform
+  STG(1, 0);
+  for (int n = 0; C.bid + n * C.nb < items; ++n) {
+    const int it = C.bid + n * C.nb;
+    const int j = it / tiles, x0 = (it - j * tiles) * TW;
+    const float2* sv = stg + (n % NBUF) * CTF;
+    const float2* so = sv + NR * TW;
+    const float* sp = (const float*)(so + NR * TW);
+    cp_async_wait<NBUF - 1>();
+    __syncthreads();
+    STG(1, 1);
+    {  // stage 1: thread (n1, c): T(p_k) of the column (rows y = n1 + G1 n2 < N), forward DFT over n2
+      const int n1 = t / TW, c = t % TW;
+      if (n1 < G1 && x0 + c < G) {
+        float2 a[G2];
+#pragma unroll
+        for (int n2 = 0; n2 < G2; ++n2) {
+          a[n2] = czero();
+          if (n2 < G2 / 2) {
+            const int y = n1 + G1 * n2;
+            a[n2] = sv[y * TW + c];
+            if (k > 0) a[n2] = axpy2(so[y * TW + c], beta, a[n2]);
+            C.vold[((size_t)j * NR + y) * G + x0 + c] = a[n2];
+          }
+        }
+        dft<G2, false>(a);
+#pragma unroll
+        for (int q2 = 0; q2 < G2; ++q2) {
+          float2 v = a[q2];
+          if (q2) v = cmul(v, twg<false>(C.tw, n1 * q2));
+          sm[(q2 * G1 + n1) * TW + c] = v;
+        }
+      }
+    }
+    __syncthreads();
+    // stage 2: thread (k2, c): forward DFT over n1 -> k = k2 + G2 k1, x P / G^2,
+    // inverse DFT over k1
+    const int k2 = t / TW, cc = t % TW;
+    const bool ok = k2 < G2 && x0 + cc < G;
+    float2 b[G1];
+    if (ok) {
+#pragma unroll
+      for (int q1 = 0; q1 < G1; ++q1) b[q1] = sm[(k2 * G1 + q1) * TW + cc];
+      dft<G1, false>(b);
+#pragma unroll
+      for (int k1 = 0; k1 < G1; ++k1) b[k1] = cscale(b[k1], sp[(k2 + G2 * k1) * TW + cc] * C.inv_G2);
+      dft<G1, true>(b);
+#pragma unroll
+      for (int m1 = 1; m1 < G1; ++m1) b[m1] = cmul(b[m1], twg<true>(C.tw, k2 * m1));
+    }
+    __syncthreads();
+    if (ok) {
+#pragma unroll
+      for (int m1 = 0; m1 < G1; ++m1) sm[(m1 * G2 + k2) * TW + cc] = b[m1];
+    }
+    __syncthreads();
+    STG(1, 2);
+    stage(n + NBUF);   // this item's staging buffer is free again
+    {  // stage 3: thread (m1, c): inverse DFT over k2 -> y = m1 + G1 m2, keep y < N
+      const int m1 = t / TW, c = t % TW;
+      if (m1 < G1 && x0 + c < G) {
+        float2 d[G2];
+#pragma unroll
+        for (int a2 = 0; a2 < G2; ++a2) d[a2] = sm[(m1 * G2 + a2) * TW + c];
+        dft<G2, true>(d);
+#pragma unroll
+        for (int m2 = 0; m2 < G2 / 2; ++m2) vio[((size_t)j * NR + m1 + G1 * m2) * G + x0 + c] = d[m2];
+      }
+    }
+    __syncthreads();
+    STG(1, 3);
+  }
+  cp_async_wait<0>();
+}
+
 // ------------------------------------------ C: column pass (PSF convolution)
 // COL_CG  : v = T(r_k) + beta_k T(p_{k-1}) = T(p_k), kept as the next
 //           T(p_{k-1}), then as COL_TOEP (T: the row pass of the CG phase)
@@ -556,7 +711,7 @@ __device__ NLINV_PHASE void phase_col_c(const Ctx& C, float2* sm, int mode, cons
                             const float2* Yin, float2* zout, float2* vio, int k = 0) {
   constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW;
   const int N = C.N, J = C.J;
-  const int t = threadIdx.x;
+  const int t = phase_tid();
   constexpr int tiles = (G + TW - 1) / TW;
   const int items = J * tiles;
   STG_BEGIN();
@@ -677,7 +832,7 @@ __device__ NLINV_PHASE void phase_row_d(const Ctx& C, float2* sm, const float2* 
                             float2* sout, float2* kbout) {
   constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW, RS = K::RS;
   const int N = C.N, Gc = C.Gc, J = C.J;
-  const int t = threadIdx.x;
+  const int t = phase_tid();
   const int groups = (N + TW - 1) / TW;
   const int items = J * groups;
   for (int it = C.bid; it < items; it += C.nb) {
@@ -770,7 +925,7 @@ __device__ NLINV_PHASE void phase_col_e(const Ctx& C, float2* sm, float2* sred, 
                             float2* p_new, float2* out, float2* hout, int slot) {
   constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW;
   const int N = C.N, Gc = C.Gc, J = C.J, NN = N * N;
-  const int t = threadIdx.x;
+  const int t = phase_tid();
   const bool withH = (mode == E_RHS);
   STG_BEGIN();
   const int tiles = (Gc + TW - 1) / TW;
@@ -927,7 +1082,7 @@ __device__ NLINV_PHASE void phase_upd(const Ctx& C, float2* sm, float2* sred, in
   constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW;
   constexpr int EU = 4;   // elements per thread per round of the elementwise part
   const int N = C.N, Gc = C.Gc, J = C.J, NN = N * N;
-  const int t = threadIdx.x;
+  const int t = phase_tid();
   const float2* rk = C.rb[k & 1];
   float2* rk1 = C.rb[(k + 1) & 1];
   STG_BEGIN();
