@@ -292,13 +292,18 @@ def newton_rhs(x: XVec, x_ref: XVec, Y: np.ndarray, P: np.ndarray, alpha: float,
 
 
 def nlinv_frame(Y: np.ndarray, P: np.ndarray, x_init: XVec, x_ref: XVec,
-                geom: Geometry, prm: Params = Params(), trace: list | None = None) -> XVec:
+                geom: Geometry, prm: Params = Params(), trace: list | None = None,
+                x_ref_last: XVec | None = None) -> XVec:
     """One frame of NLINV: M Newton steps from x^_0 = x_init, each solving
-    (DF^H P DF + alpha_n I) delta = rhs by CG and setting x^_{n+1} = x^_n + delta."""
+    (DF^H P DF + alpha_n I) delta = rhs by CG and setting x^_{n+1} = x^_n + delta.
+    x_ref_last, if given, replaces x_ref in the last Newton step (the
+    exception of the temporal decomposition, Sec. 3.3, Eq. (10))."""
     x = x_init.copy()
-    for n in range(prm.newton_steps):
+    M = prm.newton_steps
+    for n in range(M):
         alpha = prm.alpha0 * prm.q ** n
-        b = newton_rhs(x, x_ref, Y, P, alpha, geom)
+        xr = x_ref_last if (x_ref_last is not None and n == M - 1) else x_ref
+        b = newton_rhs(x, xr, Y, P, alpha, geom)
         delta = cg(lambda d: normal(x, d, P, alpha, geom), b, prm.cg_iters,
                    trace=None if trace is None else trace)
         x = x + delta
@@ -325,15 +330,21 @@ def source_frame(n: int, delay: int, warmup: int) -> int:
 
 
 def nlinv_stream(frames, geom: Geometry, prm: Params = Params(),
-                 delay: int = 1, warmup: int = 0):
+                 delay: int = 1, warmup: int = 0, last_from_prev: bool = False):
     """Reconstruct a stream of (Y, P) frames in order; frame n starts from
-    and is regularised towards damping * x^ of source_frame(n)."""
+    and is regularised towards damping * x^ of source_frame(n).  With
+    last_from_prev, Eq. (10)'s exception holds as well: the last Newton step
+    of every frame n > 0 is regularised towards damping * x^_{n-1}, so that
+    step of frame n follows the end of frame n - 1."""
     xs = []
     init = XVec.initial(geom)
     for n, (Y, P) in enumerate(frames):
         s = source_frame(n, delay, warmup)
         xp = init if s < 0 else xs[s]
-        xs.append(nlinv_frame(Y, P, xp, xp.scale(prm.damping), geom, prm))
+        xl = None
+        if last_from_prev and n > 0:
+            xl = xs[n - 1].scale(prm.damping)
+        xs.append(nlinv_frame(Y, P, xp, xp.scale(prm.damping), geom, prm, x_ref_last=xl))
     return xs
 
 

@@ -162,3 +162,39 @@ def test_stream_delay_one_is_sequential():
     for n, (Y, P) in enumerate(frames):
         x = O.nlinv_frame(Y, P, x, x.scale(0.9), g, prm)
         np.testing.assert_array_equal(x.flat(), xs[n].flat())
+
+
+def test_stream_last_step_regulariser_exception():
+    """Eq. (10)'s exception: frames after the in-order warm-up start from the
+    group's source frame, but their last Newton step is regularised towards
+    x^_{n-1}.  With delay 1 this is the sequential stream; otherwise a frame's
+    first M-1 steps match the simplified schedule exactly and only the last
+    step differs, by a Newton step taken from the same point towards another
+    regulariser."""
+    g = O.Geometry(N=8, J=2)
+    prm = O.Params(newton_steps=3, cg_iters=4, damping=0.9)
+    frames = [S.cartesian_frame(8, 2, seed=17, sigma=1e-3, frame=n)[:2] for n in range(6)]
+    seq = O.nlinv_stream(frames, g, prm, delay=1)
+    ex1 = O.nlinv_stream(frames, g, prm, delay=1, last_from_prev=True)
+    for a, b in zip(seq, ex1):
+        np.testing.assert_array_equal(a.flat(), b.flat())
+    D, WU = 3, 1
+    simp = O.nlinv_stream(frames, g, prm, delay=D, warmup=WU)
+    ex = O.nlinv_stream(frames, g, prm, delay=D, warmup=WU, last_from_prev=True)
+    first = min(n for n in range(6) if O.source_frame(n, D, WU) != n - 1)
+    for n in range(first):   # identical up to the first frame the exception touches
+        np.testing.assert_array_equal(ex[n].flat(), simp[n].flat())
+    assert np.linalg.norm((ex[first] - simp[first]).flat()) > 1e-6 * np.linalg.norm(simp[first].flat())
+    for n in range(1, 6):
+        s = O.source_frame(n, D, WU)
+        xs = ex[s]
+        if s == n - 1:        # both regularisers are x^_{n-1}: a plain frame
+            ref = O.nlinv_frame(*frames[n], xs, xs.scale(0.9), g, prm)
+            np.testing.assert_array_equal(ex[n].flat(), ref.flat())
+            continue
+        # brute force: M-1 steps towards the source, then one step towards n-1
+        y = O.nlinv_frame(*frames[n], xs, xs.scale(0.9), g, O.Params(newton_steps=2, cg_iters=4, damping=0.9))
+        alpha = prm.alpha0 * prm.q ** 2
+        b = O.newton_rhs(y, ex[n - 1].scale(0.9), frames[n][0], frames[n][1], alpha, g)
+        d = O.cg(lambda v: O.normal(y, v, frames[n][1], alpha, g), b, 4)
+        np.testing.assert_allclose((y + d).flat(), ex[n].flat(), rtol=0, atol=1e-13)
