@@ -174,19 +174,27 @@ typedef struct {
   void* x_out;          /* device [n_x]; may alias this frame's x_prev, not another's */
   void* rho_out;        /* device [N][N] or NULL */
   void* img_out;        /* device [N][N] rho * sqrt(sum_j |c_j|^2) or NULL */
+  const void* x_last;   /* device [n_x] or NULL: regulariser of the LAST Newton step
+                           (x_ref = damping * x_last there; Eq. 10's exception:
+                           frame n's last step uses x^_{n-1}).  It may be the x_out
+                           of an EARLIER frame of the same plan in this call: that
+                           step then waits (bounded, NLINV_ETIMEOUT) until the
+                           earlier frame is written.  Any other frame's x_out of
+                           this call is rejected (NLINV_EINVAL). */
 } nlinv_frame_desc_t;
 
-/* Independent frames in flight together (the temporal decomposition of
- * Sec. 3.3, Eq. 10: frames whose initial/regularisation values are already
- * available are reconstructed at the same time).  Each frame is exactly
- * nlinv_frame with its own inputs; frames may belong to different plans
- * (grid sizes, channel counts).  Frames of one plan (at most its max_batch)
- * run in one persistent cooperative launch whose CTAs are split into one
- * group per frame; different plans run concurrently on the plans' own
- * streams, each on a share of the SMs proportional to its work, and the
- * call is ordered on `stream` before and after.  Which frame serves as
- * whose x_prev (the schedule) is the caller's choice: no frame may read
- * another frame's x_out of the same call. */
+/* Frames in flight together (the temporal decomposition of Sec. 3.3,
+ * Eq. 10: frames whose initial/regularisation values are already available
+ * are reconstructed at the same time).  Each frame is nlinv_frame with its
+ * own inputs (and, with x_last, another regulariser in its last Newton
+ * step); frames may belong to different plans (grid sizes, channel counts).
+ * Frames of one plan (at most its max_batch) run in one persistent
+ * cooperative launch whose CTAs are split into one group per frame, each
+ * group with its own barrier; different plans run concurrently on the plans'
+ * own streams, each on a share of the SMs proportional to its work, and the
+ * call is ordered on `stream` before and after.  Which frame serves as whose
+ * x_prev (the schedule) is the caller's choice: no frame's x_prev may be
+ * another frame's x_out of the same call (x_last may, see above). */
 int nlinv_batch(const nlinv_frame_desc_t* frames, int nframes, nlinv_stream_t stream);
 
 /* Change alpha_0 of the plan's schedule alpha_n = alpha0 q^n (alpha0 > 0);

@@ -133,7 +133,14 @@ struct FrameIO {
   float2* xout;
   float2* rho_out;
   float2* img_out;
+  const float2* xlast;    // regulariser of the last Newton step (x ref = damping * xlast), or null
+  const unsigned* wait;   // before the last Newton step: wait until *wait != 0, or null
+  unsigned* done;         // set to 1 once xout is written, or null
 };
+
+// barrier counter and completion flag of the frame group f of a launch, one
+// 128-byte line each so that groups do not contend
+constexpr int kBarStride = 32;   // unsigned words per frame group
 
 struct FrameArgs {
   FrameIO io;
@@ -208,6 +215,22 @@ __device__ __forceinline__ void frame_body(const Ctx& C, float2* sm, float2* sre
   NLINV_SYNC();
   for (int n = 0; n < M; ++n) {
     const float al = alpha[n];
+    const bool lastreg = (n == M - 1) && io.xlast != nullptr;
+    if (lastreg && io.wait) {   // Eq. (10): the last step waits for frame n - 1
+      if (threadIdx.x == 0) {
+        long long it = 0;
+        while (ld_acquire(io.wait) == 0u) {
+          if (*(volatile int*)C.err != 0) break;
+          if (++it > C.spin_limit) {
+            raise_err(C, DEV_ETIMEOUT);
+            break;
+          }
+          __nanosleep(64);
+        }
+      }
+      __syncthreads();
+      if (*(volatile int*)C.err != 0) return;
+    }
     // Newton right-hand side: DF^H (Y - P F^(x^_n)) - alpha_n (x^_n - x_ref)
     phase_coil_y<K>(C, sm, C.xn + NN, C.h);
     NLINV_SYNC();
@@ -217,7 +240,8 @@ __device__ __forceinline__ void frame_body(const Ctx& C, float2* sm, float2* sre
     NLINV_SYNC();
     phase_row_d<K>(C, sm, C.xn, C.v, C.s, C.kb);
     NLINV_SYNC();
-    phase_col_e<K, E_RHS>(C, sm, sred, al, 0, C.kb, C.s, nullptr, nullptr, C.rb[0], C.Hr, SLOT_RR0);
+    phase_col_e<K, E_RHS>(C, sm, sred, al, 0, C.kb, C.s, nullptr, nullptr, C.rb[0], C.Hr, SLOT_RR0,
+                          lastreg ? io.xlast : nullptr, lastreg ? damping : 1.f);
     NLINV_SYNC();
     for (int k = 0; k < Kcg; ++k) {
       float2* pk = C.pb[k & 1];
@@ -239,6 +263,10 @@ __device__ __forceinline__ void frame_body(const Ctx& C, float2* sm, float2* sre
   phase_row_b<K>(C, sm, ROW_COILONLY, C.h, nullptr, nullptr, nullptr, nullptr);
   NLINV_SYNC();
   phase_final(C, io.xout, io.rho_out, io.img_out);
+  if (io.done) {   // publish x_out to a frame waiting on this one
+    NLINV_SYNC();
+    if (C.bid == 0 && threadIdx.x == 0) st_release(io.done, 1u);
+  }
 #undef NLINV_SYNC
 }
 
@@ -251,9 +279,11 @@ __global__ void __launch_bounds__(K::BS, K::MINB) k_frame(Ctx C0, FrameArgs F) {
   frame_body<K>(C, sm, sred, F.io, F.M, F.K, F.damping, F.alpha);
 }
 
-// Several independent frames of one size in one cooperative launch: the CTAs
-// are split into one contiguous group per frame; each group runs its frame
-// on its own workspace, all groups step through the phases together.
+// Several frames of one size in one cooperative launch: the CTAs are split
+// into one contiguous group per frame; each group runs its frame on its own
+// workspace with its own barrier, so the groups progress independently (a
+// frame whose last Newton step waits for an earlier frame of the launch
+// cannot hold the others up: all groups are co-resident).
 template <class K>
 __global__ void __launch_bounds__(K::BS, K::MINB) k_batch(Ctx C0, BatchArgs B) {
   extern __shared__ float2 sm[];
@@ -265,6 +295,7 @@ __global__ void __launch_bounds__(K::BS, K::MINB) k_batch(Ctx C0, BatchArgs B) {
   Ctx C = frame_ctx(C0, (size_t)f * B.fstride);
   C.bid = blockIdx.x - lo;
   C.nb = hi - lo;
+  C.bar = C0.bar + (size_t)f * kBarStride;   // this group's own barrier
   frame_body<K>(C, sm, sred, B.io[f], B.M, B.K, B.damping, B.alpha);
 }
 
@@ -618,7 +649,7 @@ int nlinv_plan(nlinv_plan_t* out, const nlinv_params_t* p, const float* psf, nli
   take((size_t)Gc * Gc * sizeof(float)); // 1 dinv
   take((size_t)pl->U * G * G * sizeof(float));  // 2 psf
   take(sizeof(int));                     // 3 err
-  take(2 * sizeof(unsigned));            // 4 bar
+  take((size_t)kMaxBatch * kBarStride * sizeof(unsigned));  // 4 barrier counters and flags
   const size_t shared_bytes = tot;
   take((size_t)J * N * N * f2);          // 5 c
   take((size_t)J * N * Gc * f2);         // 6 h
@@ -947,6 +978,21 @@ int nlinv_batch(const nlinv_frame_desc_t* frames, int nframes, nlinv_stream_t st
     }
     members[g].push_back(i);
   }
+  // x_last dependencies: an earlier frame of the same plan in this call, or
+  // a buffer that no frame of this call writes
+  std::vector<int> dep(nframes, -1);
+  for (int i = 0; i < nframes; ++i) {
+    const nlinv_frame_desc_t& d = frames[i];
+    if (d.x_last && !aligned8(d.x_last)) return NLINV_EINVAL;
+    for (int j = 0; j < nframes; ++j) {
+      if (j == i) continue;
+      if (d.x_prev && d.x_prev == frames[j].x_out) return NLINV_EINVAL;
+      if (d.x_last && d.x_last == frames[j].x_out) {
+        if (j > i || frames[j].plan != d.plan) return NLINV_EINVAL;
+        dep[i] = j;
+      }
+    }
+  }
   double wsum = 0.0;
   std::vector<double> w(plans.size());
   for (size_t g = 0; g < plans.size(); ++g) {
@@ -979,6 +1025,15 @@ int nlinv_batch(const nlinv_frame_desc_t* frames, int nframes, nlinv_stream_t st
       B.io[f].xout = (float2*)d.x_out;
       B.io[f].rho_out = (float2*)d.rho_out;
       B.io[f].img_out = (float2*)d.img_out;
+      B.io[f].xlast = (const float2*)d.x_last;
+    }
+    for (int f = 0; f < B.nf; ++f) {   // completion flags of the frames others wait on
+      const int i = members[g][f];
+      if (dep[i] < 0) continue;
+      int fd = 0;
+      while (members[g][fd] != dep[i]) ++fd;
+      B.io[fd].done = pl->C.bar + (size_t)fd * kBarStride + 1;
+      B.io[f].wait = pl->C.bar + (size_t)fd * kBarStride + 1;
     }
     // this group's share of the SMs, at least one CTA per frame
     int sms = fork ? (int)std::lround(nsm * w[g] / wsum) : nsm;
@@ -992,7 +1047,7 @@ int nlinv_batch(const nlinv_frame_desc_t* frames, int nframes, nlinv_stream_t st
     Ctx C = pl->C;
     const int rc = dispatch(pl->G, [&](auto k) -> int {
       using K = decltype(k);
-      CK(cudaMemsetAsync(C.bar, 0, 2 * sizeof(unsigned), gs));
+      CK(cudaMemsetAsync(C.bar, 0, (size_t)B.nf * kBarStride * sizeof(unsigned), gs));
       void* args[] = {(void*)&C, (void*)&B};
       CK(cudaLaunchCooperativeKernel((const void*)k_batch<K>, dim3(grid), dim3(K::BS), args,
                                      (size_t)K::SMEM, gs));

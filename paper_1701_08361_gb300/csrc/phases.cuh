@@ -96,7 +96,7 @@ struct Ctx {
   float2* vold;         // row pass of the previous CG direction p_{k-1}: [J][N][G]
   float2* part;         // [NSLOT][kMaxPart] per-CTA partials (float pairs hi, lo)
   int* err;             // latched device error
-  unsigned* bar;        // grid barrier counter
+  unsigned* bar;        // barrier counter of the CTAs working on this frame
   long long spin_limit;
   int bid, nb;          // this CTA's index within the CTAs working on this frame, and their count
 };
@@ -914,7 +914,8 @@ __device__ NLINV_PHASE void phase_row_d(const Ctx& C, float2* sm, const float2* 
 
 // ----------------- E: W^-H along y, D_W^-1, channel sum, Tikhonov, Re<p,q>
 // E_CG    : q = A p_k + alpha p_k (p_k in p_new), partial Re<p_k, q>
-// E_RHS   : out = r = DF^H(...) - alpha (x_n - x_ref), partial |r|^2; hout = H r
+// E_RHS   : out = r = DF^H(...) - alpha (x_n - x_ref), partial |r|^2; hout = H r;
+//           x_ref = xr_s * xr_in when xr_in is given (else the plan's x_ref)
 // E_DFH   : out = DF^H z
 // E_NORMAL: out = (DF^H P DF + alpha) dx                      (dx = p_new)
 // H is the y pass of W^-1 (as phase A computes it); for E_RHS the column
@@ -922,7 +923,9 @@ __device__ NLINV_PHASE void phase_row_d(const Ctx& C, float2* sm, const float2* 
 template <class K, int mode>
 __device__ NLINV_PHASE void phase_col_e(const Ctx& C, float2* sm, float2* sred, float alpha, int k,
                             const float2* kbin, const float2* sin, const float2* p_old,
-                            float2* p_new, float2* out, float2* hout, int slot) {
+                            float2* p_new, float2* out, float2* hout, int slot,
+                            const float2* xr_in = nullptr, float xr_s = 1.f) {
+  const float2* xr = xr_in ? xr_in : C.xref;   // E_RHS: regulariser xr_s * xr
   constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW;
   const int N = C.N, Gc = C.Gc, J = C.J, NN = N * N;
   const int t = phase_tid();
@@ -961,7 +964,7 @@ __device__ NLINV_PHASE void phase_col_e(const Ctx& C, float2* sm, float2* sred, 
           o1[k1] = ldcg(p_new + e);
         } else if (mode == E_RHS) {
           o1[k1] = ldcg(C.xn + e);
-          o2[k1] = ldcg(C.xref + e);
+          o2[k1] = ldcg(xr + e);
         }
       }
     }
@@ -999,7 +1002,7 @@ __device__ NLINV_PHASE void phase_col_e(const Ctx& C, float2* sm, float2* sred, 
           res = cfma(o1[k1], alpha, val);
           acc = fmaf(o1[k1].x, res.x, fmaf(o1[k1].y, res.y, acc));
         } else if (mode == E_RHS) {
-          res = cfma(csub(o1[k1], o2[k1]), -alpha, val);
+          res = cfma(cfma(o2[k1], -xr_s, o1[k1]), -alpha, val);
           acc = fmaf(res.x, res.x, fmaf(res.y, res.y, acc));
         } else if (mode == E_DFH) {
           res = val;
@@ -1044,7 +1047,7 @@ __device__ NLINV_PHASE void phase_col_e(const Ctx& C, float2* sm, float2* sred, 
     if (mode == E_CG || mode == E_NORMAL) o = ldcg(p_new + e);
     if (mode == E_RHS) {
       o = ldcg(C.xn + e);
-      o2v = ldcg(C.xref + e);
+      o2v = ldcg(xr + e);
     }
     float2 sv = czero();
 #pragma unroll 8
@@ -1054,7 +1057,7 @@ __device__ NLINV_PHASE void phase_col_e(const Ctx& C, float2* sm, float2* sred, 
       out[e] = qv;
       acc = fmaf(o.x, qv.x, fmaf(o.y, qv.y, acc));
     } else if (mode == E_RHS) {
-      const float2 bv = cfma(csub(o, o2v), -alpha, sv);
+      const float2 bv = cfma(cfma(o2v, -xr_s, o), -alpha, sv);
       out[e] = bv;
       acc = fmaf(bv.x, bv.x, fmaf(bv.y, bv.y, acc));
     } else if (mode == E_DFH) {
@@ -1233,15 +1236,19 @@ __device__ __forceinline__ void phase_final(const Ctx& C, float2* xout, float2* 
 }
 
 // ------------------------------------------------------- grid barrier
-// Monotone-counter barrier for the cooperative persistent kernel: arrival is
-// an acq_rel atomic add on one counter (zeroed before each launch); barrier
-// number e is passed once the counter reaches e * gridDim.x.  Every wait is
+// Monotone-counter barrier of the CTAs working on one frame (the whole grid,
+// or one frame group of a batch launch): arrival is an acq_rel atomic add on
+// the group's counter (zeroed before each launch); barrier number e is passed
+// once the counter reaches e * nb.  Every wait is
 // bounded by spin_limit polls; on expiry the error word is set and all CTAs
 // leave at their next barrier.
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
+}
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 __device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
   unsigned o;
@@ -1253,7 +1260,7 @@ __device__ __forceinline__ bool grid_sync(const Ctx& C, unsigned& epoch) {
   __syncthreads();
   if (threadIdx.x == 0) {
     epoch += 1;
-    const unsigned target = epoch * gridDim.x;
+    const unsigned target = epoch * (unsigned)C.nb;
     const unsigned prev = atom_add_acq_rel(C.bar, 1u);
     if (prev + 1 != target) {
       long long it = 0;

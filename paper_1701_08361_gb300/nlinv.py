@@ -49,7 +49,7 @@ class nlinv_frame_desc_t(ctypes.Structure):
     _fields_ = [
         ("plan", ctypes.c_void_p), ("Y", ctypes.c_void_p), ("turn", ctypes.c_int),
         ("x_prev", ctypes.c_void_p), ("x_out", ctypes.c_void_p), ("rho_out", ctypes.c_void_p),
-        ("img_out", ctypes.c_void_p),
+        ("img_out", ctypes.c_void_p), ("x_last", ctypes.c_void_p),
     ]
 
 
@@ -248,7 +248,9 @@ def nlinv_frame(plan: Plan, Y, turn: int, x_prev, x_out, rho_out=None, img_out=N
 
 def nlinv_batch(frames, stream=None):
     """frames: list of dicts with keys plan, Y, turn, x_prev (tensor or None),
-    x_out, and optionally rho_out, img_out."""
+    x_out, and optionally rho_out, img_out, x_last (regulariser of the last
+    Newton step: an earlier frame's x_out of the same plan, or any finished
+    buffer)."""
     arr = (nlinv_frame_desc_t * len(frames))()
     for i, f in enumerate(frames):
         pl = f["plan"]
@@ -260,6 +262,7 @@ def nlinv_batch(frames, stream=None):
         arr[i].x_out = _ptr(f["x_out"], numel=pl.nx, name="x_out")
         arr[i].rho_out = _ptr(f.get("rho_out"), numel=NN, name="rho_out")
         arr[i].img_out = _ptr(f.get("img_out"), numel=NN, name="img_out")
+        arr[i].x_last = _ptr(f.get("x_last"), numel=pl.nx, name="x_last")
     _check(_lib().nlinv_batch(arr, len(frames), _stream(stream)), "nlinv_batch")
 
 

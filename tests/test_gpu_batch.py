@@ -103,6 +103,56 @@ def test_scheduled_radial_stream_matches_oracle_stream():
         assert rel(to_np(xs[n]), ref[n].flat()) <= TOL, n
 
 
+def test_stream_with_last_step_regularised_to_previous_frame():
+    """Eq. (10) with its exception: 3 frames in flight, each from the last
+    frame of the previous group, but the last Newton step of frame n
+    regularised towards x^_{n-1}: inside a launch that step waits for the
+    frame before it (per-group barriers, device completion flags)."""
+    from paper_1701_08361_gb300 import nlinv as L
+    from paper_1701_08361_gb300 import stream as ST
+    N, J, K, U, NF, D, WU = 128, 4, 13, 5, 8, 3, 2
+    g = O.Geometry(N=N, J=J)
+    plan = make_plan(N, J, turns=U, max_batch=D)
+    frames_o, Ys, turns = [], [], []
+    coils = S.coil_maps(N, J, 9)
+    for n in range(NF):
+        kx, ky, y, _, _ = S.radial_frame(N, J, K, U, n, seed=9, coils=coils)
+        frames_o.append((O.grid_data(kx, ky, y, N, g.G), O.psf_kernel(kx, ky, N, g.G).real))
+        kxy = torch.tensor(np.stack([kx, ky], 1), dtype=torch.float64, device="cuda")
+        if n < U:
+            L.nlinv_psf(plan, n, kxy)
+        Yd = torch.empty(J * g.G * g.G, dtype=torch.complex64, device="cuda")
+        L.nlinv_grid(plan, kxy, to_dev(y), Yd)
+        Ys.append(Yd)
+        turns.append(n % U)
+    xs = torch.empty((NF, plan.nx), dtype=torch.complex64, device="cuda")
+    ST.run([dict(plan=plan, Y=Ys, turns=turns, delay=D, warmup=WU, x=xs, last_from_prev=True)])
+    assert L.nlinv_sync(plan) == 0
+    ref = O.nlinv_stream(frames_o, g, O.Params(), delay=D, warmup=WU, last_from_prev=True)
+    simp = O.nlinv_stream(frames_o, g, O.Params(), delay=D, warmup=WU)
+    for n in range(NF):
+        assert rel(to_np(xs[n]), ref[n].flat()) <= TOL, n
+    # the exception changes the frames it touches by more than the bar
+    assert max(rel(ref[n].flat(), simp[n].flat()) for n in range(NF)) > 10 * TOL
+
+
+def test_batch_rejects_reading_another_frames_output():
+    from paper_1701_08361_gb300 import nlinv as L
+    plan = make_plan(8, 2, psf=np.ones((16, 16)), max_batch=2)
+    Y = torch.zeros(2 * 16 * 16, dtype=torch.complex64, device="cuda")
+    xa = torch.empty(plan.nx, dtype=torch.complex64, device="cuda")
+    xb = torch.empty(plan.nx, dtype=torch.complex64, device="cuda")
+    a = dict(plan=plan, Y=Y, turn=0, x_prev=None, x_out=xa)
+    b = dict(plan=plan, Y=Y, turn=0, x_prev=None, x_out=xb)
+    for frames in ([dict(a, x_last=xb), b],       # last step on a LATER frame
+                   [a, dict(b, x_prev=xa)]):      # initial value from this call
+        with pytest.raises(L.NlinvError) as e:
+            L.nlinv_batch(frames)
+        assert e.value.code == L.NLINV_EINVAL
+    L.nlinv_batch([a, dict(b, x_last=xa)])        # an earlier frame: allowed
+    assert L.nlinv_sync(plan) == 0
+
+
 def test_batch_rejects_more_frames_than_the_plan_holds():
     from paper_1701_08361_gb300 import nlinv as L
     plan = make_plan(8, 2, psf=np.ones((16, 16)), max_batch=2)
