@@ -111,3 +111,28 @@ def test_radial_frame_C2_size():
     (x, rho, img), = run_frames(plan, [(to_np(Yd), 0)])
     assert rel(x, ref.flat()) <= TOL
     assert rel(img, O.image(ref, g)) <= TOL
+
+
+@pytest.mark.slow
+def test_frame_C4_size_modes_agree():
+    """A whole frame at the high-channel-count size (N=256 / 512 grid, 64
+    channels, 9 spokes, 7 x 10): the persistent launch and the one-launch-
+    per-phase path (separate kernels, same arithmetic) agree, and the output
+    is finite.  (The FP64 oracle needs minutes per frame at this size; its
+    parity is checked per operator application in test_gpu_ops.)"""
+    from paper_1701_08361_gb300 import nlinv as L
+    N, J, K, U = 256, 64, 9, 5
+    g = O.Geometry(N=N, J=J)
+    kx, ky = S.radial_trajectory(N, K, U, 0)
+    xs = []
+    for mode in (0, 1):
+        plan = make_plan(N, J, turns=1, exec_mode=mode)
+        kxy = torch.tensor(np.stack([kx, ky], 1), dtype=torch.float64, device="cuda")
+        L.nlinv_psf(plan, 0, kxy)
+        Yd = to_dev(S.random_complex((J, g.G, g.G), 77) * 1e-2)
+        x = torch.empty(plan.nx, dtype=torch.complex64, device="cuda")
+        L.nlinv_frame(plan, Yd, 0, None, x)
+        assert L.nlinv_sync(plan) == 0
+        xs.append(to_np(x))
+    assert np.all(np.isfinite(xs[0]))
+    assert rel(xs[0], xs[1]) <= 1e-5

@@ -137,3 +137,21 @@ def test_bounded_wait_reports_timeout():
     flag.fill_(1)
     L.nlinv_wait_flag(plan, flag, 1, 1000)
     assert L.nlinv_sync(plan) == 0
+
+
+@pytest.mark.slow
+def test_apply_normal_C4_size():
+    """The high-channel-count configuration at full size: N=256 on the 512
+    grid, 64 channels (Gc = 128), radial 9-spoke PSF; the 64-channel sum of
+    the adjoint and every coil column pass in one application."""
+    from paper_1701_08361_gb300 import nlinv as L
+    N, J = 256, 64
+    P, _, _ = radial_psf(N, 9, 5, 0)
+    plan = make_plan(N, J, turns=1, psf=P)
+    g = geometry(plan)
+    x, d = random_xhat(g, 41), random_xhat(g, 43)
+    out = torch.empty(plan.nx, dtype=torch.complex64, device="cuda")
+    L.nlinv_apply_normal(plan, to_dev(x.flat()), to_dev(d.flat()), 0, 0.0625, out)
+    assert L.nlinv_sync(plan) == 0
+    e_rho, e_c = split_err(to_np(out), O.normal(x, d, P, 0.0625, g).flat(), g)
+    assert e_rho <= TOL and e_c <= TOL, (e_rho, e_c)
