@@ -313,6 +313,8 @@ def run_ours(args):
         out["batched_c3"] = batched_c3(args)
     if rank == 0 and args.c4_frames > 0:
         out["high_channel_c4"] = high_channel_c4(args)
+    if rank == 0 and args.c5_steps > 0:
+        out["differentiable_c5"] = differentiable_c5(args)
     plan.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -453,6 +455,64 @@ def high_channel_c4(args):
             "frames": F, "achieved_tflops": round(achieved, 3), "frac_fp32": round(achieved / fp32_peak, 4),
             "workload": "N=256 / 512^2 grid, 64 channels, 9 spokes x 5 turns, 7x10, sequential frames, "
                         "seeded random gridded k-space (data-independent work)"}
+
+
+# ------------------------------------ differentiable unrolled NLINV (C5)
+def differentiable_c5(args):
+    """A batch of 8 frames of the real-time stream's size (N=160 / 320 grid,
+    10 channels, 13 spokes, 7 x 10) through the torch.autograd.Function:
+    forward (nlinv_batch) and the hand-written backward (per frame, per
+    Newton step recomputed from its checkpoint) for L = Re<g, x^_M>, with
+    gradients w.r.t. the gridded data and alpha_0.  Time per training step."""
+    import torch
+    from paper_1701_08361_gb300 import nlinv as L
+    from paper_1701_08361_gb300 import autograd as AG
+    dev = torch.device("cuda")
+    N, J, U, B = CFG["N"], CFG["J"], CFG["U"], 8
+    G = 2 * N
+    p = L.nlinv_default_params(N, J)
+    p.n_turns = U
+    p.max_batch = B
+    plan = L.nlinv_plan(p)
+    raw = make_raw_frames(B, CFG["seed"] + 5)
+    Ys = torch.empty((B, J * G * G), dtype=torch.complex64, device=dev)
+    for n, (kx, ky, y) in enumerate(raw):
+        kxy = torch.tensor(np.stack([kx, ky], 1), dtype=torch.float64, device=dev)
+        if n < U:
+            L.nlinv_psf(plan, n, kxy)
+        L.nlinv_grid(plan, kxy, torch.tensor(y, dtype=torch.complex64, device=dev), Ys[n])
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(5000)
+    gv = torch.randn((B, plan.nx), dtype=torch.complex64, device=dev, generator=gen)
+    turns = [n % U for n in range(B)]
+    st = torch.cuda.current_stream()
+
+    def step():
+        Yt = Ys.detach().requires_grad_(True)
+        a0 = torch.tensor(1.0, dtype=torch.float64, device=dev, requires_grad=True)
+        xs = AG.nlinv_batch(Yt, a0, plan, turns)
+        (gv.conj() * xs).real.sum().backward()
+        return Yt.grad, a0.grad
+
+    step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record(st)
+    for _ in range(args.c5_steps):
+        yg, ag = step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    wall = (time.perf_counter() - t0) / args.c5_steps * 1e3
+    ms = e0.elapsed_time(e1) / args.c5_steps
+    rc = L.nlinv_sync(plan)
+    plan.close()
+    if rc != 0 or not bool(torch.isfinite(yg).all()) or not math.isfinite(float(ag)):
+        raise RuntimeError("C5 step failed")
+    return {"value": round(B / (ms / 1e3), 2), "unit": "frames/s (forward + backward)",
+            "ms_per_step": round(ms, 3), "wall_ms_per_step": round(wall, 3), "batch": B, "steps": args.c5_steps,
+            "workload": "8 frames N=160 / 320^2 grid, 10 channels, 13 spokes, 7x10 unrolled; "
+                        "d/dY and d/dalpha_0 of Re<g, x^_M> through torch.autograd"}
 
 
 # --------------------------------------------------- CPU oracle baseline
@@ -631,6 +691,7 @@ def main():
     ap.add_argument("--plain-frames", type=int, default=10)
     ap.add_argument("--c3-groups", type=int, default=4)
     ap.add_argument("--c4-frames", type=int, default=3)
+    ap.add_argument("--c5-steps", type=int, default=1)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
