@@ -64,3 +64,33 @@ def test_null_arguments_are_rejected(lib):
     assert lib.nlinv_frame(None, None, 0, None, None, None, None, None) == -1
     assert lib.nlinv_apply_DF(None, None, None, None, None) == -1
     assert lib.nlinv_plan(None, None, None, None) == -1
+
+
+def test_ctypes_structs_match_the_header(tmp_path):
+    """The binding's nlinv_params_t and nlinv_frame_desc_t have the C layout
+    of include/nlinv.h: sizes and every field offset, from a C program
+    compiled against the header (gcc, host only)."""
+    import shutil
+    import subprocess
+    from paper_1701_08361_gb300 import nlinv as L
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"nlinv_params_t": L.nlinv_params_t, "nlinv_frame_desc_t": L.nlinv_frame_desc_t}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "nlinv.h"', "int main(void) {"]
+    for sname, cls in structs.items():
+        lines.append(f'  printf("{sname} size %zu\\n", sizeof({sname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{sname} {fname} %zu\\n", offsetof({sname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for sname, cls in structs.items():
+        assert got[(sname, "size")] == ctypes.sizeof(cls), sname
+        for fname, _ in cls._fields_:
+            assert got[(sname, fname)] == getattr(cls, fname).offset, (sname, fname)
