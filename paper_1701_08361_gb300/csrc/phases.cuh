@@ -44,6 +44,14 @@
 #else
 #define NLINV_PHASE __forceinline__
 #endif
+// elementwise parts: elements per thread per round, and the fewest CTAs left
+// over for them before a phase splits its CTAs between items and elements
+#ifndef NLINV_EU
+#define NLINV_EU 4
+#endif
+#ifndef NLINV_ELEM_CTAS
+#define NLINV_ELEM_CTAS 32
+#endif
 #ifndef NLINV_BAR_SLEEP_NS
 #define NLINV_BAR_SLEEP_NS 0
 #endif
@@ -149,10 +157,6 @@ __device__ __forceinline__ int phase_tid() {
 struct Scal2 {
   float hi, lo;
 };
-__device__ __forceinline__ Scal2 split(double s) {
-  const float hi = (float)s;
-  return Scal2{hi, (float)(s - (double)hi)};
-}
 __device__ __forceinline__ float2 axpy2(float2 x, Scal2 s, float2 y) {
   return make_float2(fmaf(s.hi, x.x, fmaf(s.lo, x.x, y.x)), fmaf(s.hi, x.y, fmaf(s.lo, x.y, y.y)));
 }
@@ -331,7 +335,7 @@ __device__ __forceinline__ double cg_step(double rr, double pq) {
 // when at least kElemCTAs CTAs would be left over, CTAs [0, items) take one
 // item each and the others the elementwise part, so the two run side by
 // side; otherwise every CTA takes both in turn.
-constexpr int kElemCTAs = 32;
+constexpr int kElemCTAs = NLINV_ELEM_CTAS;
 struct Roles {
   bool items, elems;    // what this CTA does
   int istride;          // item stride
@@ -454,7 +458,7 @@ template <class K>
 __device__ NLINV_PHASE void phase_row_cg(const Ctx& C, float2* sm, float2* sred, int k, const float2* p_old,
                              float2* p_new, float2* vout) {
   constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW, RS = K::RS;
-  constexpr int EU = 4;   // elements per thread per round of the elementwise part
+  constexpr int EU = NLINV_EU;   // elements per thread per round of the elementwise part
   const int N = C.N, Gc = C.Gc, J = C.J;
   const int t = phase_tid();
   const float2* rk = C.rb[k & 1];
@@ -1083,7 +1087,7 @@ template <class K>
 __device__ NLINV_PHASE void phase_upd(const Ctx& C, float2* sm, float2* sred, int k, bool last,
                                        const float2* p) {
   constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW;
-  constexpr int EU = 4;   // elements per thread per round of the elementwise part
+  constexpr int EU = NLINV_EU;   // elements per thread per round of the elementwise part
   const int N = C.N, Gc = C.Gc, J = C.J, NN = N * N;
   const int t = phase_tid();
   const float2* rk = C.rb[k & 1];
