@@ -1280,11 +1280,24 @@ __global__ void k_dot_part(long long n, const float2* u, const float2* v, double
   }
 }
 
+// one warp: lane l adds partials l, l + 32, ... (all loads issued first),
+// then a fixed shuffle tree (a single thread adding them in turn spent
+// ~19 us per call on dependent FP64 adds and loads)
 __global__ void k_dot_final(int np, const double* part, double* out) {
-  if (threadIdx.x != 0) return;
+  const int l = threadIdx.x;
   double a = 0.0;
-  for (int i = 0; i < np; ++i) a += part[i];
-  *out = a;
+  for (int base = 0; base < np; base += 32 * 8) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = base + u * 32 + l;
+      v[u] = i < np ? part[i] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) a += v[u];
+  }
+  a = warp_sum_f64(a);
+  if (l == 0) *out = a;
 }
 
 // z <- s P z on [J][G][G]
