@@ -52,6 +52,12 @@
 #ifndef NLINV_ELEM_CTAS
 #define NLINV_ELEM_CTAS 32
 #endif
+// the CG column pass stages T(r_k), T(p_{k-1}) in shared memory; the PSF
+// tile is read into registers (staging it too measured 1 % slower: the
+// larger carve-out leaves less L1 for register spills)
+#ifndef NLINV_STAGE_PSF
+#define NLINV_STAGE_PSF 0
+#endif
 #ifndef NLINV_BAR_SLEEP_NS
 #define NLINV_BAR_SLEEP_NS 0
 #endif
@@ -125,10 +131,10 @@ template <int G1_, int G2_> struct Cfg {
   static constexpr int MINB = BS <= 256 ? 2 : 1;
 #endif
   // staged operands of one column item of the CG column pass: T(r_k) and
-  // T(p_{k-1}) tiles [N][TW] and the PSF tile [G][TW].  One staging buffer:
+  // T(p_{k-1}) tiles [N][TW] (and the PSF tile [G][TW] if staged).  One staging buffer:
   // a second one (a full item ahead) measured slower, as the larger shared
   // memory carve-out shrinks the L1 cache that holds the register spills.
-  static constexpr int CT = 2 * NR * TW * 8 + G * TW * 4;
+  static constexpr int CT = 2 * NR * TW * 8 + (NLINV_STAGE_PSF ? G * TW * 4 : 0);
   static constexpr int SMEM_LIM = MINB == 1 ? 227 * 1024 : 228 * 1024 / MINB - 1024;
   static constexpr int NBUF = 1;
   static constexpr int SMEM = SMEM_X + NBUF * CT;  // dynamic smem bytes
@@ -618,10 +624,12 @@ __device__ NLINV_PHASE void phase_col_cg(const Ctx& C, float2* sm, const float* 
           if (k > 0) cp_async16(so + r * TW + c, C.vold + g);
         }
       }
-      constexpr int CPP = TW / 4;   // chunks per row of the PSF tile
-      for (int i = t; i < G * CPP; i += BS) {
-        const int r = i / CPP, c = (i % CPP) * 4;
-        if (c < wv) cp_async16(sp + r * TW + c, P + (size_t)r * G + x0 + c);
+      if (NLINV_STAGE_PSF) {
+        constexpr int CPP = TW / 4;   // chunks per row of the PSF tile
+        for (int i = t; i < G * CPP; i += BS) {
+          const int r = i / CPP, c = (i % CPP) * 4;
+          if (c < wv) cp_async16(sp + r * TW + c, P + (size_t)r * G + x0 + c);
+        }
       }
     }
     cp_async_commit();
@@ -636,6 +644,13 @@ __device__ NLINV_PHASE void phase_col_cg(const Ctx& C, float2* sm, const float* 
     const float2* sv = stg + (n % NBUF) * CTF;
     const float2* so = sv + NR * TW;
     const float* sp = (const float*)(so + NR * TW);
+    const int k2 = t / TW, cc = t % TW;
+    const bool ok = k2 < G2 && x0 + cc < G;
+    float pv[G1];   // the PSF of this thread's stage-2 points, when not staged
+    if (!NLINV_STAGE_PSF) {
+#pragma unroll
+      for (int k1 = 0; k1 < G1; ++k1) pv[k1] = ok ? __ldg(P + (size_t)(k2 + G2 * k1) * G + x0 + cc) : 0.f;
+    }
     cp_async_wait<NBUF - 1>();
     __syncthreads();
     STG(1, 1);
@@ -665,15 +680,14 @@ __device__ NLINV_PHASE void phase_col_cg(const Ctx& C, float2* sm, const float* 
     __syncthreads();
     // stage 2: thread (k2, c): forward DFT over n1 -> k = k2 + G2 k1, x P / G^2,
     // inverse DFT over k1
-    const int k2 = t / TW, cc = t % TW;
-    const bool ok = k2 < G2 && x0 + cc < G;
     float2 b[G1];
     if (ok) {
 #pragma unroll
       for (int q1 = 0; q1 < G1; ++q1) b[q1] = sm[(k2 * G1 + q1) * TW + cc];
       dft<G1, false>(b);
 #pragma unroll
-      for (int k1 = 0; k1 < G1; ++k1) b[k1] = cscale(b[k1], sp[(k2 + G2 * k1) * TW + cc] * C.inv_G2);
+      for (int k1 = 0; k1 < G1; ++k1)
+        b[k1] = cscale(b[k1], (NLINV_STAGE_PSF ? sp[(k2 + G2 * k1) * TW + cc] : pv[k1]) * C.inv_G2);
       dft<G1, true>(b);
 #pragma unroll
       for (int m1 = 1; m1 < G1; ++m1) b[m1] = cmul(b[m1], twg<true>(C.tw, k2 * m1));
