@@ -1300,6 +1300,56 @@ __global__ void k_dot_final(int np, const double* part, double* out) {
   if (l == 0) *out = a;
 }
 
+// several Re<u_j, v_j> in one pass over n elements (per-block FP64 partials,
+// [MD][kDotBlocks]), reduced per product by one warp each in k_dots_final
+constexpr int kMaxDots = 8;
+struct DotSet {
+  const float2* u[kMaxDots];
+  const float2* v[kMaxDots];
+};
+template <int MD>
+__global__ void k_dots_part(long long n, DotSet S, double* part) {
+  __shared__ double sw[MD][32];
+  double acc[MD];
+#pragma unroll
+  for (int j = 0; j < MD; ++j) acc[j] = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int j = 0; j < MD; ++j) {
+      const float2 a = S.u[j][i], b = S.v[j][i];
+      acc[j] = fma((double)a.x, (double)b.x, fma((double)a.y, (double)b.y, acc[j]));
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < MD; ++j) {
+    const double v = warp_sum_f64(acc[j]);
+    if ((threadIdx.x & 31) == 0) sw[j][threadIdx.x >> 5] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < MD) {
+    double a = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += sw[threadIdx.x][w];
+    part[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = a;
+  }
+}
+__global__ void k_dots_final(int np, const double* part, double* out) {
+  const int l = threadIdx.x;
+  const double* src = part + (size_t)blockIdx.x * np;
+  double a = 0.0;
+  for (int base = 0; base < np; base += 32 * 8) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = base + u * 32 + l;
+      v[u] = i < np ? src[i] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) a += v[u];
+  }
+  a = warp_sum_f64(a);
+  if (l == 0) out[blockIdx.x] = a;
+}
+
 // z <- s P z on [J][G][G]
 __global__ void k_psf_scale(int J, int G, float2* z, const float* __restrict__ P, float s) {
   const long long n = (long long)J * G * G, g2 = (long long)G * G;
@@ -1356,6 +1406,16 @@ struct GradOps {
     k_dot_final<<<1, 32, 0, st>>>(kDotBlocks, part, dres);
     CKL("k_dot_final");
     CK(cudaMemcpyAsync(out, dres, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return NLINV_OK;
+  }
+  // kMaxDots products Re<u_j, v_j> with one read-back
+  int dots(const DotSet& S, double* out) const {
+    k_dots_part<kMaxDots><<<kDotBlocks, 256, 0, st>>>(nx, S, part);
+    CKL("k_dots_part");
+    k_dots_final<<<kMaxDots, 32, 0, st>>>(kDotBlocks, part, dres);
+    CKL("k_dots_final");
+    CK(cudaMemcpyAsync(out, dres, kMaxDots * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     return NLINV_OK;
   }
@@ -1417,7 +1477,8 @@ int grad_workspace(nlinv_plan_s* pl, GradWS& w) {
   const int M = pl->prm.newton_steps, Kc = pl->prm.cg_iters;
   const size_t nx = (size_t)pl->nx, nk = (size_t)pl->J * pl->G * pl->G;
   const size_t vb = align_up(nx * sizeof(float2)), kb = align_up(nk * sizeof(float2));
-  const size_t need = vb * ((M + 1) + 1 + Kc + Kc + (Kc + 1) + 10) + 2 * kb + align_up((kDotBlocks + 1) * sizeof(double));
+  const size_t need = vb * ((M + 1) + 1 + Kc + Kc + (Kc + 1) + 10) + 2 * kb +
+                      align_up((size_t)kMaxDots * (kDotBlocks + 1) * sizeof(double));
   RC(ensure_prep(pl, need));
   char* p = (char*)pl->prep;
   auto vec = [&](size_t count) {
@@ -1445,7 +1506,7 @@ int grad_workspace(nlinv_plan_s* pl, GradWS& w) {
   w.zt = (float2*)p;
   p += kb;
   w.part = (double*)p;
-  w.dres = w.part + kDotBlocks;
+  w.dres = w.part + (size_t)kMaxDots * kDotBlocks;
   return NLINV_OK;
 }
 
@@ -1572,21 +1633,31 @@ extern "C" int nlinv_frame_vjp(nlinv_plan_t pl, const void* Y, int turn, const v
       const float2* r1 = w.tr + (size_t)(k + 1) * (size_t)nx;
       const double a = T.a[k], beta = T.beta[k], gamma = T.gamma[k];
       const double rk = T.rho[k], rk1 = T.rho[k + 1];
+      // every inner product this step needs, from the vectors as they enter
+      // it (the updates below are linear in them): one read-back per step
+      //   D0 <p, pbar>  D1 <q, rbar>  D2 <q, pbar>  D3 <q, r1>
+      //   D4 <p, xb>    D5 <p, rbar>  D6 <p, r1>    D7 <p, p>
+      DotSet S;
+      const float2* U[kMaxDots] = {p, q, q, q, p, p, p, p};
+      const float2* V[kMaxDots] = {w.pbar, w.rbar, w.pbar, r1, w.xb, w.rbar, r1, p};
+      for (int j = 0; j < kMaxDots; ++j) {
+        S.u[j] = U[j];
+        S.v[j] = V[j];
+      }
+      double D[kMaxDots];
+      RC(O.dots(S, D));
       RC(O.axpby(w.rbar, w.pbar, 1.0, 1.0, nx));      // p_{k+1} = r_{k+1} + beta p_k
-      double betabar = 0.0;
-      RC(O.dot(p, w.pbar, nx, &betabar));
+      const double betabar = D[0];
       RC(O.copy(w.pb, w.pbar, nx));
       RC(O.axpby(w.pb, w.pb, 0.0, beta, nx));
       rhobar[k + 1] += betabar / rk;                  // beta = rho_{k+1} / rho_k
       rhobar[k] -= betabar * rk1 / (rk * rk);
-      RC(O.axpby(w.rbar, r1, 2.0 * rhobar[k + 1], 1.0, nx));  // rho_{k+1} = <r, r>
-      double t = 0.0;
-      RC(O.dot(q, w.rbar, nx, &t));                   // r_{k+1} = r_k - a q_k
-      double abar = -t;
+      const double c = 2.0 * rhobar[k + 1];
+      RC(O.axpby(w.rbar, r1, c, 1.0, nx));            // rho_{k+1} = <r, r>
+      double abar = -(D[1] + D[2] + c * D[3]);        // r_{k+1} = r_k - a q_k
       RC(O.copy(w.qbar, w.rbar, nx));
       RC(O.axpby(w.qbar, w.qbar, 0.0, -a, nx));
-      RC(O.dot(p, w.xb, nx, &t));                     // x_{k+1} = x_k + a p_k
-      abar += t;
+      abar += D[4];                                   // x_{k+1} = x_k + a p_k
       RC(O.axpby(w.pb, w.xb, a, 1.0, nx));
       rhobar[k] += abar / gamma;                      // a = rho_k / gamma_k
       const double gammabar = -abar * rk / (gamma * gamma);
@@ -1594,8 +1665,8 @@ extern "C" int nlinv_frame_vjp(nlinv_plan_t pl, const void* Y, int turn, const v
       RC(O.axpby(w.qbar, p, gammabar, 1.0, nx));
       RC(O.normal(x, w.qbar, alpha, w.t1));           // q = A p
       RC(O.axpby(w.pb, w.t1, 1.0, 1.0, nx));
-      RC(O.dot(p, w.qbar, nx, &t));                   // A depends on alpha and x^_n
-      alpha_bar += t;
+      // A depends on alpha and x^_n: <p, qbar>, qbar = -a rbar' + gammabar p
+      alpha_bar += -a * (D[5] + D[0] + c * D[6]) + gammabar * D[7];
       RC(O.DF(x, p, w.zt));
       RC(O.psf(w.zt, 1.f));
       RC(O.DFH(w.qbar, w.zt, w.t1));
