@@ -1379,8 +1379,20 @@ struct GradOps {
   cudaStream_t st;
   const float* P;
   long long nx, nk;
-  double* part;   // [kDotBlocks]
-  double* dres;   // device scalar
+  double* part;   // [kMaxDots][kDotBlocks]
+  double* dres;   // device scalars [kMaxDots]
+  // The plan's coil-map buffer holds W^-1 of lin's coil part when
+  // coils_at == lin.  lin is the Newton step's checkpoint x^_n, which is not
+  // written while it is the linearisation point; maps of any other point
+  // (a buffer that may change between calls) are never reused.
+  const float2* lin = nullptr;
+  mutable const float2* coils_at = nullptr;
+  template <class Lc>
+  int coils(const Lc& L, const float2* w) const {
+    if (w != nullptr && w == lin && coils_at == lin) return NLINV_OK;
+    coils_at = (w == lin) ? lin : nullptr;
+    return L.coils(w);
+  }
 
   int grid(long long n) const {
     long long g = (n + 255) / 256;
@@ -1425,7 +1437,7 @@ struct GradOps {
     return dispatch(pl->G, [&](auto k) -> int {
       using K = decltype(k);
       Launch<K> L{pl, st};
-      RC(L.coils(x));
+      RC(coils(L, x));
       RC(L.coil_y(d + NN, pl->C.h));
       RC(L.row_b(ROW_LIN, pl->C.h, x, d, nullptr, pl->C.v));
       return L.col_c(COL_FWD, nullptr, nullptr, z, pl->C.v);
@@ -1436,7 +1448,7 @@ struct GradOps {
     return dispatch(pl->G, [&](auto k) -> int {
       using K = decltype(k);
       Launch<K> L{pl, st};
-      RC(L.coils(w));
+      RC(coils(L, w));
       RC(L.col_c(COL_INV, nullptr, z, nullptr, pl->C.v));
       RC(L.row_d(w, pl->C.v, pl->C.s, pl->C.kb));
       return L.col_e(E_DFH, 0.f, 0, pl->C.kb, pl->C.s, nullptr, nullptr, out, nullptr, SLOT_PQ);
@@ -1448,7 +1460,7 @@ struct GradOps {
     return dispatch(pl->G, [&](auto k) -> int {
       using K = decltype(k);
       Launch<K> L{pl, st};
-      RC(L.coils(x));
+      RC(coils(L, x));
       RC(L.coil_y(d + NN, pl->C.h));
       RC(L.row_b(ROW_LIN, pl->C.h, x, d, nullptr, pl->C.v));
       RC(L.col_c(COL_TOEP, P, nullptr, nullptr, pl->C.v));
@@ -1469,7 +1481,7 @@ struct GradOps {
 };
 
 struct GradWS {
-  float2 *ck, *b, *z, *zt, *tp, *tq, *tr, *xb, *xbn, *pbar, *rbar, *qbar, *pb, *t1, *xref, *xrefbar, *xcg;
+  float2 *ck, *b, *z, *zt, *zt2, *tp, *tq, *tr, *xb, *xbn, *pbar, *rbar, *qbar, *pb, *t1, *xref, *xrefbar, *xcg;
   double *part, *dres;
 };
 
@@ -1477,7 +1489,7 @@ int grad_workspace(nlinv_plan_s* pl, GradWS& w) {
   const int M = pl->prm.newton_steps, Kc = pl->prm.cg_iters;
   const size_t nx = (size_t)pl->nx, nk = (size_t)pl->J * pl->G * pl->G;
   const size_t vb = align_up(nx * sizeof(float2)), kb = align_up(nk * sizeof(float2));
-  const size_t need = vb * ((M + 1) + 1 + Kc + Kc + (Kc + 1) + 10) + 2 * kb +
+  const size_t need = vb * ((M + 1) + 1 + Kc + Kc + (Kc + 1) + 10) + 3 * kb +
                       align_up((size_t)kMaxDots * (kDotBlocks + 1) * sizeof(double));
   RC(ensure_prep(pl, need));
   char* p = (char*)pl->prep;
@@ -1504,6 +1516,8 @@ int grad_workspace(nlinv_plan_s* pl, GradWS& w) {
   w.z = (float2*)p;
   p += kb;
   w.zt = (float2*)p;
+  p += kb;
+  w.zt2 = (float2*)p;
   p += kb;
   w.part = (double*)p;
   w.dres = w.part + (size_t)kMaxDots * kDotBlocks;
@@ -1606,6 +1620,7 @@ extern "C" int nlinv_frame_vjp(nlinv_plan_t pl, const void* Y, int turn, const v
     const float2* x = w.ck + (size_t)n * (size_t)nx;
     float2* x1 = w.ck + (size_t)(n + 1) * (size_t)nx;
     const double alpha = prm.alpha0 * std::pow(prm.q, n);
+    O.lin = x;
     RC(grad_rhs(O, w, Yd, x, alpha, w.b));
     RC(grad_cg(O, w, x, alpha, w.b, Kc, T));
     RC(O.copy(x1, x, nx));
@@ -1620,6 +1635,7 @@ extern "C" int nlinv_frame_vjp(nlinv_plan_t pl, const void* Y, int turn, const v
   for (int n = M - 1; n >= 0; --n) {
     const float2* x = w.ck + (size_t)n * (size_t)nx;
     const double alpha = prm.alpha0 * std::pow(prm.q, n);
+    O.lin = x;
     RC(grad_rhs(O, w, Yd, x, alpha, w.b));            // residual z stays in w.z
     RC(grad_cg(O, w, x, alpha, w.b, Kc, T));
     double alpha_bar = 0.0;
@@ -1667,13 +1683,14 @@ extern "C" int nlinv_frame_vjp(nlinv_plan_t pl, const void* Y, int turn, const v
       RC(O.axpby(w.pb, w.t1, 1.0, 1.0, nx));
       // A depends on alpha and x^_n: <p, qbar>, qbar = -a rbar' + gammabar p
       alpha_bar += -a * (D[5] + D[0] + c * D[6]) + gammabar * D[7];
+      // both DF at x^_n first, while its coil maps are current
       RC(O.DF(x, p, w.zt));
       RC(O.psf(w.zt, 1.f));
+      RC(O.DF(x, w.qbar, w.zt2));
+      RC(O.psf(w.zt2, 1.f));
       RC(O.DFH(w.qbar, w.zt, w.t1));
       RC(O.axpby(w.xbn, w.t1, 1.0, 1.0, nx));
-      RC(O.DF(x, w.qbar, w.zt));
-      RC(O.psf(w.zt, 1.f));
-      RC(O.DFH(p, w.zt, w.t1));
+      RC(O.DFH(p, w.zt2, w.t1));
       RC(O.axpby(w.xbn, w.t1, 1.0, 1.0, nx));
       std::swap(w.pbar, w.pb);
     }
