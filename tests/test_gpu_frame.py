@@ -1,6 +1,7 @@
 """GPU parity of whole NLINV frames (IRGNM + CG, Eqs. (2)-(3)) against the
 FP64 oracle through the C ABI: final x^, rho and the coil-combined image
-within relative L2 1e-3 (spec tolerance), in both execution modes."""
+within relative L2 1e-3 (FP32 arithmetic against FP64 through 7 x 10
+Newton/CG steps), in both execution modes."""
 import numpy as np
 import pytest
 import torch
@@ -136,3 +137,19 @@ def test_frame_C4_size_modes_agree():
         xs.append(to_np(x))
     assert np.all(np.isfinite(xs[0]))
     assert rel(xs[0], xs[1]) <= 1e-5
+
+
+@pytest.mark.parametrize("M,K,mode", [(1, 1, 0), (1, 0, 0), (2, 1, 1), (1, 3, 1), (3, 0, 1)])
+def test_degenerate_iteration_counts(M, K, mode):
+    """One Newton step, one CG iteration, or none (x^ stays the initial value):
+    the drivers' edge cases against the oracle, ragged N=20 grid."""
+    N, J = 20, 3
+    g = O.Geometry(N=N, J=J)
+    Y, P, _, _ = S.cartesian_frame(N, J, seed=61, sigma=1e-3)
+    prm = O.Params(newton_steps=M, cg_iters=K)
+    ref = O.nlinv_frame(Y, P, O.XVec.initial(g), O.XVec.initial(g), g, prm)
+    plan = make_plan(N, J, psf=P, newton_steps=M, cg_iters=K, exec_mode=mode)
+    (x, rho, img), = run_frames(plan, [(Y, 0)])
+    if K == 0:
+        np.testing.assert_array_equal(x, O.XVec.initial(g).flat().astype(np.complex64))
+    assert rel(x, ref.flat()) <= TOL
