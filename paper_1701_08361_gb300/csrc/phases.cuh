@@ -7,7 +7,6 @@
 // phase and every pass keeps its 1-D FFTs in registers (see fft.cuh):
 //
 //   A  coil_y : W^-1 along y.  c^_j columns (G_c nonzero of G) -> N rows.
-//               In CG it first forms p = r + beta p (the CG direction update).
 //   B  row_b  : W^-1 along x, then u_j = c_j drho + rho dc_j, then the
 //               forward FFT of the zero-padded row (N nonzero of G).
 //   C  col_c  : along y: FFT (N nonzero of G), x P / G^2, inverse FFT, keep
@@ -17,9 +16,15 @@
 //               cropped to the G_c coil band.
 //   E  col_e  : FFT along y, crop to G_c, x D_W^-1: the W^-H part; plus the
 //               channel sum  sum_j s_j  for the rho part; plus the Tikhonov
-//               term and the CG inner product Re<p, q> (FP64 partials).
-//   F  upd    : x += a p, r -= a q, |r|^2 (FP64 partials).
+//               term and the CG inner product Re<p, q> (partials).
 //
+// A CG iteration runs B as row_cg (the row pass of the residual r_k, whose y
+// pass H r_k the previous update produced; the direction p_k is formed
+// elementwise by CTAs without a row item), C as col_cg (T(p_k) = T(r_k) +
+// beta_k T(p_{k-1}) from the stored T(p_{k-1}), then the PSF column pass),
+// D, E, and
+//   F  upd    : x += a p, r_{k+1} = r_k - a q, |r_{k+1}|^2 (partials), and
+//               H r_{k+1} for the next row pass.
 // Data layouts (complex64 interleaved, row-major):
 //   x^ vector   : rho [N][N] followed by c^ [J][Gc][Gc]        (n_x elements)
 //   c  (coils)  : [J][N][N]      h  : [J][N][Gc]   (after the y pass of W^-1)
@@ -88,7 +93,7 @@ __device__ __forceinline__ unsigned long long gtimer() {
 #define STG(ph, st)
 #endif
 
-constexpr int kMaxPart = 4096;     // max CTAs that deposit an FP64 partial
+constexpr int kMaxPart = 4096;     // max CTAs that deposit a reduction partial
 enum { SLOT_PQ = 0, SLOT_RR0 = 1, SLOT_RR1 = 2, NSLOT = 4 };
 enum { DEV_ETIMEOUT = -4, DEV_ENUMERIC = -5 };
 
@@ -141,7 +146,7 @@ template <int G1_, int G2_> struct Cfg {
   static_assert(SMEM <= SMEM_LIM, "staging buffer does not fit");
   static_assert(TW % 4 == 0 && (G % 4) == 0, "16-byte staging chunks");
   static_assert(G1 % 2 == 0 && G2 % 2 == 0, "G1, G2 must be even");
-  // the FP64 block reductions use full-warp shuffles over blockDim / 32 warps
+  // the block reductions use full-warp shuffles over blockDim / 32 warps
   static_assert(BS % 32 == 0, "threads per CTA must be a whole number of warps");
 };
 
@@ -202,7 +207,7 @@ __device__ __forceinline__ DF32 df_warp_sum(DF32 a) {   // fixed tree, valid in 
 // Deterministic grid reduction, producer side: this CTA's threads' values
 // (fixed warp trees) become part[slot][bid].  Consumers (a later phase,
 // after a barrier or in a later kernel with the same CTA count) add the nb
-// partials themselves with slot_total().
+// partials themselves with slot_sum().
 __device__ __forceinline__ void block_partial(const Ctx& C, float v, int slot, float2* sred) {
   DF32 a = df_warp_sum(DF32{v, 0.f});
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -952,7 +957,7 @@ __device__ NLINV_PHASE void phase_col_e(const Ctx& C, float2* sm, float2* sred, 
   const int tiles = (Gc + TW - 1) / TW;
   const int items = J * tiles;
   const Roles R = roles(C, items);
-  float acc = 0.f;   // this thread's few terms; CTA and grid sums in FP64
+  float acc = 0.f;   // this thread's few terms; CTA and grid sums in float pairs
   if (R.items) for (int it = C.bid; it < items; it += R.istride) {
     const int j = it / tiles;
     const int fx = (it - j * tiles) * TW + (t % TW);
@@ -1132,7 +1137,7 @@ __device__ NLINV_PHASE void phase_upd(const Ctx& C, float2* sm, float2* sred, in
   const int tiles = (Gc + TW - 1) / TW;
   const int items = last ? 0 : J * tiles;
   const Roles R = roles(C, items);
-  float acc = 0.f;   // this thread's few terms; CTA and grid sums in FP64
+  float acc = 0.f;   // this thread's few terms; CTA and grid sums in float pairs
   // (1) H r_{k+1} per coil column tile
   if (R.items) for (int it = C.bid; it < items; it += R.istride) {
     const int j = it / tiles;
