@@ -304,7 +304,9 @@ def run_ours(args):
     }
     if args.exec_mode == 1:
         M, C = CFG["M"], CFG["CG"]
-        out["gpu_launches"] = K * F * (1 + M * (5 + 6 * C) + 2 + 1)
+        # init, per Newton step 5 right-hand-side and 5 per CG iteration,
+        # the final coil maps (2) and the outputs
+        out["gpu_launches"] = K * F * (1 + M * (5 + 5 * C) + 2 + 1)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_frames)
     if rank == 0 and args.plain_loop:
