@@ -63,8 +63,10 @@
 #ifndef NLINV_STAGE_PSF
 #define NLINV_STAGE_PSF 0
 #endif
+// pause between two polls of a barrier counter: fewer reads of the counter's
+// line while CTAs arrive (32 ns measured 1.7 % faster per frame than none)
 #ifndef NLINV_BAR_SLEEP_NS
-#define NLINV_BAR_SLEEP_NS 0
+#define NLINV_BAR_SLEEP_NS 32
 #endif
 
 namespace nlinv {
