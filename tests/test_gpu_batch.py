@@ -72,15 +72,19 @@ def test_batch_mixes_grid_sizes_and_channel_counts():
         assert rel(to_np(d["x_out"]), ref.flat()) <= TOL
 
 
-def test_scheduled_radial_stream_matches_oracle_stream():
-    """8 radial frames (N=128, 4 coils, 13 spokes, 5 turns): frames 0..2 in
-    order, then 3 in flight at a time, each from the most recent finished
-    frame (Eq. (10) with o = 3).  At N=64 the same trajectory sits on the FP32
-    floor of the 1e-3 bar (FP32 operator rounding alone moves the FP64
-    trajectory by about 1e-3 there), so the stream is checked at N=128."""
+# radial stream of the schedule tests: 8 frames N=128, 4 coils, 13 spokes,
+# 5 turns; frames 0..2 in order, then 3 in flight (Eq. (10) with o = 3).  At
+# N=64 the same trajectory sits on the FP32 floor of the 1e-3 bar (FP32
+# operator rounding alone moves the FP64 trajectory by about 1e-3 there).
+STREAM = dict(N=128, J=4, K=13, U=5, NF=8, D=3, WU=2)
+
+
+def radial_stream_on_gpu(last_from_prev):
+    """Run the stream through the scheduler; returns (GPU x^ per frame,
+    oracle (Y, P) per frame, geometry)."""
     from paper_1701_08361_gb300 import nlinv as L
     from paper_1701_08361_gb300 import stream as ST
-    N, J, K, U, NF, D, WU = 128, 4, 13, 5, 8, 3, 2
+    N, J, K, U, NF, D, WU = (STREAM[k] for k in ("N", "J", "K", "U", "NF", "D", "WU"))
     g = O.Geometry(N=N, J=J)
     plan = make_plan(N, J, turns=U, max_batch=D)
     frames_o, Ys, turns = [], [], []
@@ -96,44 +100,32 @@ def test_scheduled_radial_stream_matches_oracle_stream():
         Ys.append(Yd)
         turns.append(n % U)
     xs = torch.empty((NF, plan.nx), dtype=torch.complex64, device="cuda")
-    ST.run([dict(plan=plan, Y=Ys, turns=turns, delay=D, warmup=WU, x=xs)])
+    ST.run([dict(plan=plan, Y=Ys, turns=turns, delay=D, warmup=WU, x=xs, last_from_prev=last_from_prev)])
     assert L.nlinv_sync(plan) == 0
-    ref = O.nlinv_stream(frames_o, g, O.Params(), delay=D, warmup=WU)
-    for n in range(NF):
-        assert rel(to_np(xs[n]), ref[n].flat()) <= TOL, n
+    return [to_np(xs[n]) for n in range(NF)], frames_o, g
+
+
+def test_scheduled_radial_stream_matches_oracle_stream():
+    """Each frame after the warm-up starts from, and is regularised towards,
+    the most recent frame finished when its group starts."""
+    xs, frames_o, g = radial_stream_on_gpu(False)
+    ref = O.nlinv_stream(frames_o, g, O.Params(), delay=STREAM["D"], warmup=STREAM["WU"])
+    for n, x in enumerate(xs):
+        assert rel(x, ref[n].flat()) <= TOL, n
 
 
 def test_stream_with_last_step_regularised_to_previous_frame():
-    """Eq. (10) with its exception: 3 frames in flight, each from the last
-    frame of the previous group, but the last Newton step of frame n
-    regularised towards x^_{n-1}: inside a launch that step waits for the
+    """Eq. (10) with its exception: the last Newton step of frame n is
+    regularised towards x^_{n-1}; inside a launch that step waits for the
     frame before it (per-group barriers, device completion flags)."""
-    from paper_1701_08361_gb300 import nlinv as L
-    from paper_1701_08361_gb300 import stream as ST
-    N, J, K, U, NF, D, WU = 128, 4, 13, 5, 8, 3, 2
-    g = O.Geometry(N=N, J=J)
-    plan = make_plan(N, J, turns=U, max_batch=D)
-    frames_o, Ys, turns = [], [], []
-    coils = S.coil_maps(N, J, 9)
-    for n in range(NF):
-        kx, ky, y, _, _ = S.radial_frame(N, J, K, U, n, seed=9, coils=coils)
-        frames_o.append((O.grid_data(kx, ky, y, N, g.G), O.psf_kernel(kx, ky, N, g.G).real))
-        kxy = torch.tensor(np.stack([kx, ky], 1), dtype=torch.float64, device="cuda")
-        if n < U:
-            L.nlinv_psf(plan, n, kxy)
-        Yd = torch.empty(J * g.G * g.G, dtype=torch.complex64, device="cuda")
-        L.nlinv_grid(plan, kxy, to_dev(y), Yd)
-        Ys.append(Yd)
-        turns.append(n % U)
-    xs = torch.empty((NF, plan.nx), dtype=torch.complex64, device="cuda")
-    ST.run([dict(plan=plan, Y=Ys, turns=turns, delay=D, warmup=WU, x=xs, last_from_prev=True)])
-    assert L.nlinv_sync(plan) == 0
-    ref = O.nlinv_stream(frames_o, g, O.Params(), delay=D, warmup=WU, last_from_prev=True)
-    simp = O.nlinv_stream(frames_o, g, O.Params(), delay=D, warmup=WU)
-    for n in range(NF):
-        assert rel(to_np(xs[n]), ref[n].flat()) <= TOL, n
+    xs, frames_o, g = radial_stream_on_gpu(True)
+    kw = dict(delay=STREAM["D"], warmup=STREAM["WU"])
+    ref = O.nlinv_stream(frames_o, g, O.Params(), last_from_prev=True, **kw)
+    simp = O.nlinv_stream(frames_o, g, O.Params(), **kw)
+    for n, x in enumerate(xs):
+        assert rel(x, ref[n].flat()) <= TOL, n
     # the exception changes the frames it touches by more than the bar
-    assert max(rel(ref[n].flat(), simp[n].flat()) for n in range(NF)) > 10 * TOL
+    assert max(rel(ref[n].flat(), simp[n].flat()) for n in range(len(xs))) > 10 * TOL
 
 
 def test_batch_rejects_reading_another_frames_output():
