@@ -53,19 +53,30 @@ def source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(name="k_frame_c2_stream.md"):
-    """DRAM read+write bytes per launch from the committed ncu summary, or
-    None when the kernel sources changed since that capture."""
-    p = os.path.join(ROOT, "profiles", name)
+def profiled_traffic(kernel):
+    """DRAM read + write bytes per launch of `kernel` from the record of the
+    last ncu capture (profiles/traffic.json: kernel, source hash, bytes), or
+    None when there is none or the kernel sources changed since it was taken."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
-    txt = open(p).read()
-    import re
-    m = re.search(r"kernel-source-sha256-16:\s*([0-9a-f]+)", txt)
-    t = re.search(r"traffic \(read \+ write\) per launch[^|]*\|\s*([0-9.]+) MB", txt)
-    if not m or not t or m.group(1) != source_hash():
+    try:
+        rec = json.load(open(p)).get(kernel)
+    except Exception:
         return None
-    return float(t.group(1)) * 1e6
+    if not rec or rec.get("source_sha16") != source_hash():
+        return None
+    return float(rec["dram_bytes_per_launch"])
+
+
+def sm_count():
+    import torch
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+
+
+def fp32_peak_tflops(pk):
+    """FP32 ALU roof: SMs x 128 FP32 lanes x 2 flop (FMA) x the maximum SM clock."""
+    return sm_count() * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
 
 
 def flops_per_frame(N, G, Gc, J, M, K):
@@ -196,10 +207,11 @@ def run_ours(args):
     Gc = plan.Gc
     dev = torch.device("cuda")
     Yall = torch.empty((F, J * G * G), dtype=torch.complex64, device=dev)
+    Ps = torch.empty((U, G * G), dtype=torch.float32, device=dev)
     for n, (kx, ky, y) in enumerate(raw):
         kxy = torch.tensor(np.stack([kx, ky], 1), dtype=torch.float64, device=dev)
         if n < U:
-            L.nlinv_psf(plan, n % U, kxy)
+            L.nlinv_psf(plan, n % U, kxy, Ps[n])
         L.nlinv_grid(plan, kxy, torch.tensor(y, dtype=torch.complex64, device=dev), Yall[n])
     assert L.nlinv_sync(plan) == 0
     x = torch.empty(plan.nx, dtype=torch.complex64, device=dev)
@@ -273,7 +285,7 @@ def run_ours(args):
     fl = flops_per_frame(N, G, Gc, J, CFG["M"], CFG["CG"])
     by = bytes_per_frame(N, G, Gc, J, CFG["M"], CFG["CG"])
     mean_frame_s = statistics.mean(t_frames) / 1e3
-    fp32_peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12   # TFLOP/s
+    fp32_peak = fp32_peak_tflops(pk)   # TFLOP/s
     achieved = fl / mean_frame_s / 1e12
     hbm = by / mean_frame_s / 1e9
 
@@ -291,9 +303,9 @@ def run_ours(args):
         "latency_ms": {"p50": round(statistics.median(lat), 4), "min": round(lat[0], 4)},
         "roofline": {"bound": "alu", "achieved": round(achieved, 3),
                      "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
-                     "frac": round(achieved / fp32_peak, 4), "traffic": profiled_traffic(),
+                     "frac": round(achieved / fp32_peak, 4), "traffic": profiled_traffic("k_frame_c2_stream"),
                      "kernel": "k_frame (persistent, one launch per frame)",
-                     "peak_source": "FP32: 152 SMs x 128 lanes x 2 flop x sm_max_mhz (%s)" % pk_src},
+                     "peak_source": "FP32: %d SMs x 128 lanes x 2 flop x sm_max_mhz (%s)" % (sm_count(), pk_src)},
         "hbm": {"achieved_gbs": round(hbm, 1), "peak_gbs": pk["hbm_gbs"],
                 "frac": round(hbm / pk["hbm_gbs"], 4), "peak_source": pk_src},
         "e2e": {"value": round(frames / (e2e_ms / 1e3), 2), "unit": "frames/s",
@@ -311,6 +323,8 @@ def run_ours(args):
         out["cpu_baseline"] = cpu_baseline(args.cpu_frames)
     if rank == 0 and args.plain_loop:
         out["plain_gpu_loop"] = plain_gpu_loop(raw, args)
+    if rank == 0 and args.unfused_frames > 0 and args.exec_mode == 0:
+        out["unfused_own_kernels"] = unfused_own_kernels(Yall, Ps, args)
     if rank == 0 and args.c3_groups > 0:
         out["batched_c3"] = batched_c3(args)
     if rank == 0 and args.c4_frames > 0:
@@ -323,6 +337,44 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+# ------------------------------ own kernels unfused, one frame at a time
+def unfused_own_kernels(Yall, Ps, args):
+    """The same frames through the library's per-phase execution mode (one
+    launch per fused phase, no persistent kernel): the project's own kernels
+    without the whole-frame fusion, one frame at a time."""
+    import torch
+    from paper_1701_08361_gb300 import nlinv as L
+    N, J, U = CFG["N"], CFG["J"], CFG["U"]
+    p = L.nlinv_default_params(N, J)
+    p.n_turns = U
+    p.newton_steps, p.cg_iters = CFG["M"], CFG["CG"]
+    p.exec_mode = 1
+    plan = L.nlinv_plan(p)
+    for u in range(U):
+        L.nlinv_set_psf(plan, u, Ps[u])
+    x = torch.empty(plan.nx, dtype=torch.complex64, device=Yall.device)
+    st = torch.cuda.current_stream()
+    nf = min(args.unfused_frames, Yall.shape[0])
+    for n in range(3):
+        L.nlinv_frame(plan, Yall[n], n % U, None if n == 0 else x, x)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for n in range(nf):
+        L.nlinv_frame(plan, Yall[n], n % U, x, x)
+    e1.record(st)
+    torch.cuda.synchronize()
+    rc = L.nlinv_sync(plan)
+    plan.close()
+    if rc != 0:
+        raise RuntimeError(L.nlinv_strerror(rc))
+    ms = e0.elapsed_time(e1)
+    M, C = CFG["M"], CFG["CG"]
+    return {"value": round(nf / (ms / 1e3), 2), "unit": "frames/s", "frames": nf,
+            "kind": "own kernels, one launch per fused phase (exec_mode 1), one frame at a time",
+            "launches_per_frame": 1 + M * (5 + 5 * C) + 2 + 1}
 
 
 # ------------------------------------------- batched uneven frames (C3)
@@ -398,7 +450,7 @@ def batched_c3(args):
                 for c in C3)
     achieved = flops * args.c3_groups / (ms / 1e3) / 1e12
     pk, _ = peaks()
-    fp32_peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    fp32_peak = fp32_peak_tflops(pk)
     for s in streams:
         s["plan"].close()
     return {"value": round(nframes / (ms / 1e3), 2), "unit": "frames/s",
@@ -452,7 +504,7 @@ def high_channel_c4(args):
     flops = flops_per_frame(N, G, G // 4, J, CFG["M"], CFG["CG"])
     achieved = flops / (ms / 1e3) / 1e12
     pk, _ = peaks()
-    fp32_peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    fp32_peak = fp32_peak_tflops(pk)
     return {"value": round(1e3 / ms, 2), "unit": "frames/s", "ms_per_frame": round(ms, 3),
             "frames": F, "achieved_tflops": round(achieved, 3), "frac_fp32": round(achieved / fp32_peak, 4),
             "workload": "N=256 / 512^2 grid, 64 channels, 9 spokes x 5 turns, 7x10, sequential frames, "
@@ -575,20 +627,23 @@ def plain_gpu_loop(raw, args):
     k2 = (2.0 * f / G).double()
     D = ((1 + 220.0 * (k2[:, None] ** 2 + k2[None, :] ** 2)) ** -16).float()
 
+    # padded grids allocated once: only the coil band (zc) or the FOV (zi)
+    # is ever written, so the rest stays zero without a memset per call
+    zc = torch.zeros((J, G, G), dtype=torch.complex64, device=dev)
+    zi = torch.zeros((J, G, G), dtype=torch.complex64, device=dev)
+    band = (slice(None), idx[:, None], idx[None, :])
+
     def Winv(ch):
-        z = torch.zeros((J, G, G), dtype=torch.complex64, device=dev)
-        z[:, idx[:, None], idx[None, :]] = D * ch
-        return torch.fft.ifft2(z, norm="ortho")[:, :N, :N]
+        zc[band] = D * ch
+        return torch.fft.ifft2(zc, norm="ortho")[:, :N, :N]
 
     def WinvH(v):
-        z = torch.zeros((J, G, G), dtype=torch.complex64, device=dev)
-        z[:, :N, :N] = v
-        return D * torch.fft.fft2(z, norm="ortho")[:, idx[:, None], idx[None, :]]
+        zi[:, :N, :N] = v
+        return D * torch.fft.fft2(zi, norm="ortho")[band]
 
     def pad(v):
-        z = torch.zeros((J, G, G), dtype=torch.complex64, device=dev)
-        z[:, :N, :N] = v
-        return z
+        zi[:, :N, :N] = v
+        return zi
 
     def frame(Y, P, rho0, ch0, rhor, chr_):
         rho, ch = rho0.clone(), ch0.clone()
@@ -634,7 +689,8 @@ def plain_gpu_loop(raw, args):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     return {"value": round(nf / (ms / 1e3), 2), "unit": "frames/s",
-            "kind": "plain torch.fft/cuFFT eager loop, FP32, one frame at a time",
+            "kind": "plain torch.fft/cuFFT eager loop, FP32, one frame at a time, padded grids "
+                    "allocated once",
             "frames": nf}
 
 
@@ -687,10 +743,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--frames-per-step", type=int, default=25)
     ap.add_argument("--exec-mode", type=int, default=0, choices=[0, 1])
-    ap.add_argument("--cpu-frames", type=int, default=2)
+    ap.add_argument("--cpu-frames", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-loop", type=int, default=1)
     ap.add_argument("--plain-frames", type=int, default=10)
+    ap.add_argument("--unfused-frames", type=int, default=10)
     ap.add_argument("--c3-groups", type=int, default=4)
     ap.add_argument("--c4-frames", type=int, default=3)
     ap.add_argument("--c5-steps", type=int, default=1)

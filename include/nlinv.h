@@ -148,7 +148,9 @@ int nlinv_apply_normal(nlinv_plan_t plan, const void* xhat, const void* dx, int 
  * All calls share the one array, so calls that overlap on the GPU (other
  * streams, other threads) race and must be serialised by the caller; each
  * call writes every intermediate before reading it, so nothing has to be
- * cleared between calls. */
+ * cleared between calls.  The twiddle and D_W^-1 tables in the array are
+ * kept from the previous call on the device when G, Gc, w_a and w_l are
+ * unchanged (only a change of them rewrites the tables). */
 int nlinv_apply_normal_static(int N, int J, int Gc, double w_a, double w_l,
                               const void* xhat, const void* dx, const float* psf,
                               double alpha, void* out, nlinv_stream_t stream);
@@ -196,6 +198,54 @@ typedef struct {
  * x_prev (the schedule) is the caller's choice: no frame's x_prev may be
  * another frame's x_out of the same call (x_last may, see above). */
 int nlinv_batch(const nlinv_frame_desc_t* frames, int nframes, nlinv_stream_t stream);
+
+/* Temporal decomposition of Sec. 3.3 (Eq. 10): *src_out = the frame whose
+ * x^ starts (and regularises) frame n of a stream reconstructed with `delay`
+ * frames in flight after `warmup` frames in order.  Frames n <= warmup use
+ * n - 1; later frames go in groups of `delay` and each uses the last frame of
+ * the previous group (frame `warmup` for the first group), which lies in
+ * [n - delay, n - 1]; -1 stands for the initial value (rho = 1, c^ = 0).
+ * Returns NLINV_OK, or NLINV_EINVAL for n < 0, delay < 1, warmup < 0 or a
+ * NULL src_out.  Host-only: launches nothing. */
+int nlinv_stream_source(int n, int delay, int warmup, int* src_out);
+
+/* The whole schedule of one stream of nframes frames (host arrays of
+ * nframes ints, each may be NULL): group_out[n] = the launch group of frame
+ * n (0..warmup in order, then groups of `delay`), source_out[n] =
+ * the source of nlinv_stream_source, last_out[n] = the frame whose x^ regularises the
+ * last Newton step of frame n when last_from_prev is set and differs from
+ * the source (n - 1), else -1.  Returns the number of groups, or
+ * NLINV_EINVAL.  Host-only: launches nothing. */
+int nlinv_stream_schedule(int nframes, int delay, int warmup, int last_from_prev, int* group_out,
+                          int* source_out, int* last_out);
+
+/* One stream of frames for nlinv_run_streams (host arrays of device
+ * pointers, each of length nframes). */
+typedef struct {
+  nlinv_plan_t plan;        /* size class of every frame of the stream; its
+                               max_batch must be >= delay, and no other
+                               stream of the call may use the same plan */
+  int nframes;
+  const void* const* Y;     /* device complex64 [J][G][G] per frame */
+  const int* turns;         /* PSF slot per frame (host ints) */
+  void* const* x_out;       /* device [n_x] per frame: frame n's x^ */
+  void* const* img_out;     /* device [N][N] per frame, or NULL (none) */
+  const void* x_init;       /* device [n_x]: x^ of the frame before frame 0,
+                               or NULL (rho = 1, c^ = 0) */
+  int delay;                /* frames in flight after the warm-up (>= 1; 1 = in order) */
+  int warmup;               /* frames 0..warmup are reconstructed in order (>= 0) */
+  int last_from_prev;       /* nonzero: Eq. 10's exception, the last Newton
+                               step of frame n regularised towards x^_{n-1}
+                               (waiting for it when it is in the same group) */
+} nlinv_stream_desc_t;
+
+/* Reconstruct several independent streams with the temporal decomposition
+ * of Sec. 3.3 (Eq. 10): the library forms each stream's launch groups
+ * (nlinv_stream_source) and issues group g of every stream together as one
+ * nlinv_batch call, g = 0, 1, ...; frame n starts from and is regularised
+ * towards damping * x^ of its source frame.  Everything is asynchronous on
+ * `stream`; device errors are latched in the plans (nlinv_sync). */
+int nlinv_run_streams(const nlinv_stream_desc_t* streams, int nstreams, nlinv_stream_t stream);
 
 /* Change alpha_0 of the plan's schedule alpha_n = alpha0 q^n (alpha0 > 0);
  * applies to calls issued afterwards. */

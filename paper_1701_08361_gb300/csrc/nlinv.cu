@@ -407,18 +407,28 @@ __global__ void k_adj_ndft(int N, int S, const float2* __restrict__ yv, const fl
 }
 
 // ----------------------------------------------------- size dispatch
+// NLINV_ONLY_G=<G> compiles one grid size only (quick profiling builds)
+#ifdef NLINV_ONLY_G
+#define NLINV_CASE(g, a, b)                          \
+  case g:                                            \
+    if constexpr (g == NLINV_ONLY_G) return f(Cfg<a, b>{}); \
+    else return NLINV_EUNSUPPORTED;
+#else
+#define NLINV_CASE(g, a, b) \
+  case g: return f(Cfg<a, b>{});
+#endif
 template <class F>
 int dispatch(int G, F&& f) {
   switch (G) {
-    case 16: return f(Cfg<4, 4>{});
-    case 24: return f(Cfg<4, 6>{});
-    case 40: return f(Cfg<4, 10>{});
-    case 64: return f(Cfg<8, 8>{});
-    case 128: return f(Cfg<8, 16>{});
-    case 256: return f(Cfg<16, 16>{});
-    case 320: return f(Cfg<16, 20>{});
-    case 384: return f(Cfg<16, 24>{});
-    case 512: return f(Cfg<16, 32>{});
+    NLINV_CASE(16, 4, 4)
+    NLINV_CASE(24, 4, 6)
+    NLINV_CASE(40, 4, 10)
+    NLINV_CASE(64, 8, 8)
+    NLINV_CASE(128, 8, 16)
+    NLINV_CASE(256, 16, 16)
+    NLINV_CASE(320, 16, 20)
+    NLINV_CASE(384, 16, 24)
+    NLINV_CASE(512, 16, 32)
     default: return NLINV_EUNSUPPORTED;
   }
 }
@@ -1076,6 +1086,72 @@ int nlinv_batch(const nlinv_frame_desc_t* frames, int nframes, nlinv_stream_t st
   return NLINV_OK;
 }
 
+int nlinv_stream_source(int n, int delay, int warmup, int* src_out) {
+  if (n < 0 || delay < 1 || warmup < 0 || !src_out) return NLINV_EINVAL;
+  *src_out = n <= warmup ? n - 1 : warmup + ((n - warmup - 1) / delay) * delay;
+  return NLINV_OK;
+}
+
+int nlinv_stream_schedule(int nframes, int delay, int warmup, int last_from_prev, int* group_out,
+                          int* source_out, int* last_out) {
+  if (nframes < 0 || delay < 1 || warmup < 0) return NLINV_EINVAL;
+  int ngroups = 0;
+  for (int n = 0; n < nframes; ++n) {
+    // launch groups: 0, 1, ..., warmup one frame each, then runs of `delay`
+    const int g = n <= warmup ? n : warmup + 1 + (n - warmup - 1) / delay;
+    int src = -1;
+    nlinv_stream_source(n, delay, warmup, &src);
+    if (group_out) group_out[n] = g;
+    if (source_out) source_out[n] = src;
+    if (last_out) last_out[n] = (last_from_prev && n > 0 && src != n - 1) ? n - 1 : -1;
+    ngroups = g + 1;
+  }
+  return ngroups;
+}
+
+int nlinv_run_streams(const nlinv_stream_desc_t* streams, int nstreams, nlinv_stream_t stream) {
+  if (!streams || nstreams <= 0) return NLINV_EINVAL;
+  std::vector<std::vector<int>> grp(nstreams), src(nstreams), last(nstreams);
+  int ngroups = 0;
+  for (int s = 0; s < nstreams; ++s) {
+    const nlinv_stream_desc_t& d = streams[s];
+    if (!d.plan || d.nframes < 0) return NLINV_EINVAL;
+    if (d.nframes > 0 && (!d.Y || !d.turns || !d.x_out)) return NLINV_EINVAL;
+    if (d.delay > d.plan->max_batch) return NLINV_EINVAL;
+    for (int t = 0; t < s; ++t)
+      if (streams[t].plan == d.plan) return NLINV_EINVAL;
+    grp[s].resize(d.nframes);
+    src[s].resize(d.nframes);
+    last[s].resize(d.nframes);
+    const int ng = nlinv_stream_schedule(d.nframes, d.delay, d.warmup, d.last_from_prev, grp[s].data(),
+                                         src[s].data(), last[s].data());
+    if (ng < 0) return ng;
+    if (ng > ngroups) ngroups = ng;
+  }
+  std::vector<nlinv_frame_desc_t> fr;
+  for (int g = 0; g < ngroups; ++g) {
+    fr.clear();
+    for (int s = 0; s < nstreams; ++s) {
+      const nlinv_stream_desc_t& d = streams[s];
+      for (int n = 0; n < d.nframes; ++n) {
+        if (grp[s][n] != g) continue;
+        nlinv_frame_desc_t f;
+        std::memset(&f, 0, sizeof(f));
+        f.plan = d.plan;
+        f.Y = d.Y[n];
+        f.turn = d.turns[n];
+        f.x_prev = src[s][n] < 0 ? d.x_init : d.x_out[src[s][n]];
+        f.x_out = d.x_out[n];
+        f.img_out = d.img_out ? d.img_out[n] : nullptr;
+        f.x_last = last[s][n] >= 0 ? d.x_out[last[s][n]] : nullptr;
+        fr.push_back(f);
+      }
+    }
+    if (!fr.empty()) RC(nlinv_batch(fr.data(), (int)fr.size(), stream));
+  }
+  return NLINV_OK;
+}
+
 int nlinv_sync(nlinv_plan_t pl, nlinv_stream_t stream) {
   RC(check_plan(pl));
   CK(cudaStreamSynchronize((cudaStream_t)stream));
@@ -1111,6 +1187,14 @@ static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBy
 
 std::mutex g_static_mu;
 void* g_static_ptr[64] = {};
+// the (G, Gc, w_a, w_l) whose twiddle and D_W^-1 tables the array holds, per
+// device: a call with the same sizes and weight constants skips the table
+// kernel (the tables stay valid until a call with other values rewrites them)
+struct StaticKey {
+  int G = 0, Gc = 0;
+  double w_a = 0.0, w_l = 0.0;
+};
+StaticKey g_static_key[64];
 
 // twiddles w_G^k and the D_W^-1 table, computed on the device in FP64
 __global__ void k_static_tables(int G, int Gc, double w_a, double w_l, float2* tw, float* dinv) {
@@ -1130,8 +1214,10 @@ __global__ void k_static_tables(int G, int Gc, double w_a, double w_l, float2* t
 }
 
 // set-up once per device (with that device current): the device address of
-// the scratch array and the constant twiddle table
-int static_scratch(void** out) {
+// the scratch array and the constant twiddle table.  *fresh is set when the
+// array's tables do not hold (G, Gc, w_a, w_l); static_tables_written()
+// records them once the table kernel is enqueued.
+int static_scratch(void** out, int G, int Gc, double w_a, double w_l, bool* fresh) {
   int dev = 0;
   CK(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return NLINV_EINVAL;
@@ -1142,8 +1228,21 @@ int static_scratch(void** out) {
     CK(cudaGetSymbolAddress(&p, g_static_scratch));
     g_static_ptr[dev] = p;
   }
+  const StaticKey& k = g_static_key[dev];
+  *fresh = !(k.G == G && k.Gc == Gc && k.w_a == w_a && k.w_l == w_l);
   *out = g_static_ptr[dev];
   return NLINV_OK;
+}
+
+void static_tables_written(int G, int Gc, double w_a, double w_l) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  StaticKey& k = g_static_key[dev];
+  k.G = G;
+  k.Gc = Gc;
+  k.w_a = w_a;
+  k.w_l = w_l;
 }
 
 }  // namespace
@@ -1181,7 +1280,8 @@ extern "C" int nlinv_apply_normal_static(int N, int J, int Gc, double w_a, doubl
   take(sizeof(int) + 2 * sizeof(unsigned));
   if (tot > kStaticScratchBytes) return NLINV_EINVAL;
   void* base_v = nullptr;
-  RC(static_scratch(&base_v));
+  bool fresh = true;
+  RC(static_scratch(&base_v, G, Gc, w_a, w_l, &fresh));
   char* base = (char*)base_v;
   cudaStream_t st = (cudaStream_t)stream;
 
@@ -1210,9 +1310,12 @@ extern "C" int nlinv_apply_normal_static(int N, int J, int Gc, double w_a, doubl
   C.err = (int*)(base + off[8]);
   C.bar = (unsigned*)(C.err + 1);
   C.spin_limit = 1LL << 22;
-  const int nt = (G > Gc * Gc ? G : Gc * Gc);
-  k_static_tables<<<(nt + 255) / 256, 256, 0, st>>>(G, Gc, w_a, w_l, tw, dinv);
-  CKL("k_static_tables");
+  if (fresh) {
+    const int nt = (G > Gc * Gc ? G : Gc * Gc);
+    k_static_tables<<<(nt + 255) / 256, 256, 0, st>>>(G, Gc, w_a, w_l, tw, dinv);
+    CKL("k_static_tables");
+    static_tables_written(G, Gc, w_a, w_l);
+  }
   const float2* xh = (const float2*)xhat;
   const float2* d = (const float2*)dx;
   const size_t NN = (size_t)N * N;

@@ -53,6 +53,16 @@ class nlinv_frame_desc_t(ctypes.Structure):
     ]
 
 
+class nlinv_stream_desc_t(ctypes.Structure):
+    _fields_ = [
+        ("plan", ctypes.c_void_p), ("nframes", ctypes.c_int),
+        ("Y", ctypes.POINTER(ctypes.c_void_p)), ("turns", ctypes.POINTER(ctypes.c_int)),
+        ("x_out", ctypes.POINTER(ctypes.c_void_p)), ("img_out", ctypes.POINTER(ctypes.c_void_p)),
+        ("x_init", ctypes.c_void_p), ("delay", ctypes.c_int), ("warmup", ctypes.c_int),
+        ("last_from_prev", ctypes.c_int),
+    ]
+
+
 _L = None
 _VP = ctypes.c_void_p
 _I = ctypes.c_int
@@ -73,6 +83,9 @@ _SIGS = {
     "nlinv_apply_normal_static": (_I, [_I, _I, _I, ctypes.c_double, ctypes.c_double, _VP, _VP, _VP,
                                        ctypes.c_double, _VP, _VP]),
     "nlinv_batch": (_I, [ctypes.POINTER(nlinv_frame_desc_t), _I, _VP]),
+    "nlinv_stream_source": (_I, [_I, _I, _I, ctypes.POINTER(_I)]),
+    "nlinv_stream_schedule": (_I, [_I, _I, _I, _I, _VP, _VP, _VP]),
+    "nlinv_run_streams": (_I, [ctypes.POINTER(nlinv_stream_desc_t), _I, _VP]),
     "nlinv_wait_flag": (_I, [_VP, _VP, _I, ctypes.c_longlong, _VP]),
     "nlinv_set_alpha0": (_I, [_VP, ctypes.c_double]),
     "nlinv_frame_vjp": (_I, [_VP, _VP, _I, _VP, _VP, _VP, ctypes.POINTER(ctypes.c_double), _VP, _VP]),
@@ -264,6 +277,53 @@ def nlinv_batch(frames, stream=None):
         arr[i].img_out = _ptr(f.get("img_out"), numel=NN, name="img_out")
         arr[i].x_last = _ptr(f.get("x_last"), numel=pl.nx, name="x_last")
     _check(_lib().nlinv_batch(arr, len(frames), _stream(stream)), "nlinv_batch")
+
+
+def nlinv_stream_source(n: int, delay: int, warmup: int) -> int:
+    """Source frame of frame n under Eq. (10)'s schedule (-1: initial value)."""
+    src = ctypes.c_int()
+    _check(_lib().nlinv_stream_source(n, delay, warmup, ctypes.byref(src)), "nlinv_stream_source")
+    return src.value
+
+
+def nlinv_stream_schedule(nframes: int, delay: int, warmup: int, last_from_prev: bool = False):
+    """(group, source, last) per frame of one stream, as the library runs it."""
+    g, s, l = (ctypes.c_int * max(1, nframes))(), (ctypes.c_int * max(1, nframes))(), (ctypes.c_int * max(1, nframes))()
+    rc = _lib().nlinv_stream_schedule(nframes, delay, warmup, 1 if last_from_prev else 0, g, s, l)
+    if rc < 0:
+        raise NlinvError(rc, "nlinv_stream_schedule")
+    return list(g)[:nframes], list(s)[:nframes], list(l)[:nframes]
+
+
+def nlinv_run_streams(streams, stream=None):
+    """streams: list of dicts {plan, Y: list of device tensors, turns: list of
+    ints, x: device tensor [nframes, n_x] (or list of [n_x] tensors) for the
+    outputs, img: optional [nframes, N*N], x_init: optional [n_x], delay,
+    warmup, last_from_prev: optional bool}."""
+    keep = []
+    arr = (nlinv_stream_desc_t * len(streams))()
+    for i, s in enumerate(streams):
+        pl = s["plan"]
+        nf = len(s["Y"])
+        NN = pl.N * pl.N
+        Y = (ctypes.c_void_p * nf)(*[_ptr(y, numel=pl.J * pl.G * pl.G, name="Y") for y in s["Y"]])
+        T = (ctypes.c_int * nf)(*[int(t) for t in s["turns"]])
+        X = (ctypes.c_void_p * nf)(*[_ptr(s["x"][n], numel=pl.nx, name="x") for n in range(nf)])
+        keep += [Y, T, X]
+        arr[i].plan = pl.handle
+        arr[i].nframes = nf
+        arr[i].Y = ctypes.cast(Y, ctypes.POINTER(ctypes.c_void_p))
+        arr[i].turns = ctypes.cast(T, ctypes.POINTER(ctypes.c_int))
+        arr[i].x_out = ctypes.cast(X, ctypes.POINTER(ctypes.c_void_p))
+        if s.get("img") is not None:
+            I = (ctypes.c_void_p * nf)(*[_ptr(s["img"][n], numel=NN, name="img") for n in range(nf)])
+            keep.append(I)
+            arr[i].img_out = ctypes.cast(I, ctypes.POINTER(ctypes.c_void_p))
+        arr[i].x_init = _ptr(s.get("x_init"), numel=pl.nx, name="x_init")
+        arr[i].delay = int(s["delay"])
+        arr[i].warmup = int(s["warmup"])
+        arr[i].last_from_prev = 1 if s.get("last_from_prev") else 0
+    _check(_lib().nlinv_run_streams(arr, len(streams), _stream(stream)), "nlinv_run_streams")
 
 
 def nlinv_set_alpha0(plan: Plan, alpha0: float):

@@ -67,7 +67,7 @@ def test_null_arguments_are_rejected(lib):
 
 
 def test_ctypes_structs_match_the_header(tmp_path):
-    """The binding's nlinv_params_t and nlinv_frame_desc_t have the C layout
+    """The binding's nlinv_params_t, nlinv_frame_desc_t and nlinv_stream_desc_t have the C layout
     of include/nlinv.h: sizes and every field offset, from a C program
     compiled against the header (gcc, host only)."""
     import shutil
@@ -76,7 +76,8 @@ def test_ctypes_structs_match_the_header(tmp_path):
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")
-    structs = {"nlinv_params_t": L.nlinv_params_t, "nlinv_frame_desc_t": L.nlinv_frame_desc_t}
+    structs = {"nlinv_params_t": L.nlinv_params_t, "nlinv_frame_desc_t": L.nlinv_frame_desc_t,
+               "nlinv_stream_desc_t": L.nlinv_stream_desc_t}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "nlinv.h"', "int main(void) {"]
     for sname, cls in structs.items():
         lines.append(f'  printf("{sname} size %zu\\n", sizeof({sname}));')

@@ -1,6 +1,11 @@
-"""The host scheduler of the temporal decomposition matches the oracle's
-schedule and never reads a frame finished in the same launch (CPU only)."""
+"""The library's schedule of the temporal decomposition (Sec. 3.3, Eq. 10;
+nlinv_stream_source / nlinv_stream_schedule, host-only C functions) matches
+the oracle's schedule and never reads a frame finished in the same launch
+(CPU only: the library loads without a GPU and these calls launch nothing)."""
+import pytest
+
 import oracle as O
+from paper_1701_08361_gb300 import nlinv as L
 from paper_1701_08361_gb300 import stream as ST
 
 
@@ -8,6 +13,7 @@ def test_sources_match_oracle():
     for D in (1, 2, 3, 11):
         for l in (0, 2, 5):
             for n in range(40):
+                assert L.nlinv_stream_source(n, D, l) == O.source_frame(n, D, l)
                 assert ST.source(n, D, l) == O.source_frame(n, D, l)
 
 
@@ -27,33 +33,30 @@ def test_groups_cover_frames_once_and_respect_dependencies():
                     done.update(g)
 
 
-def test_run_passes_the_last_step_regulariser(monkeypatch):
-    """With last_from_prev, every frame whose source is not n - 1 gets
-    x_last = x^_{n-1}, which is then either a finished frame of an earlier
-    launch or an EARLIER frame of the same launch (the only in-call reference
-    the library accepts); x_prev never refers to the same launch."""
-    from paper_1701_08361_gb300 import nlinv as L
-    calls = []
-    monkeypatch.setattr(L, "nlinv_batch", lambda frames, stream=None: calls.append(frames))
-    NF, D, WU = 14, 3, 2
-    xs = [f"x{n}" for n in range(NF)]        # stand-ins for the output buffers
-    ST.run([dict(plan="P", Y=[None] * NF, turns=[0] * NF, delay=D, warmup=WU, x=xs,
-                 last_from_prev=True)])
-    assert [len(c) for c in calls] == [len(g) for g in ST.groups(NF, D, WU)]
-    done = set()
-    for frames in calls:
-        outs = [f["x_out"] for f in frames]
-        for i, f in enumerate(frames):
-            n = xs.index(f["x_out"])
-            s = ST.source(n, D, WU)
-            assert f["x_prev"] == (None if s < 0 else xs[s]) and f["x_prev"] not in outs
-            if s == n - 1:
-                assert f["x_last"] is None
-            else:
-                assert f["x_last"] == xs[n - 1]
-                assert f["x_last"] in done or f["x_last"] in outs[:i]
-        done.update(outs)
-    # without the option nothing changes
-    calls.clear()
-    ST.run([dict(plan="P", Y=[None] * NF, turns=[0] * NF, delay=D, warmup=WU, x=xs)])
-    assert all(f["x_last"] is None for c in calls for f in c)
+@pytest.mark.parametrize("NF,D,WU", [(14, 3, 2), (40, 11, 5), (9, 1, 0), (8, 4, 0)])
+def test_last_step_regulariser_is_the_previous_frame(NF, D, WU):
+    """With last_from_prev, every frame whose source is not n - 1 is given
+    x^_{n-1} for its last Newton step, and that frame is either finished in an
+    earlier launch group or an EARLIER frame of the same group (the only
+    in-call reference nlinv_batch accepts); sources are always in earlier
+    groups.  Without the option no frame gets one."""
+    grp, src, last = L.nlinv_stream_schedule(NF, D, WU, True)
+    for n in range(NF):
+        assert src[n] == O.source_frame(n, D, WU)
+        assert src[n] < 0 or grp[src[n]] < grp[n]
+        if n == 0 or src[n] == n - 1:
+            assert last[n] == -1
+        else:
+            assert last[n] == n - 1
+            assert grp[n - 1] < grp[n] or (grp[n - 1] == grp[n] and n - 1 < n)
+    _, _, last0 = L.nlinv_stream_schedule(NF, D, WU, False)
+    assert all(v == -1 for v in last0)
+
+
+def test_schedule_rejects_bad_arguments():
+    for args in ((5, 0, 0), (5, 1, -1), (-1, 1, 0)):
+        with pytest.raises(L.NlinvError):
+            L.nlinv_stream_schedule(*args)
+    for args in ((-1, 1, 0), (3, 0, 0), (3, 1, -2)):
+        with pytest.raises(L.NlinvError):
+            L.nlinv_stream_source(*args)

@@ -52,3 +52,43 @@ def test_static_rejects_sizes_beyond_its_array():
     with pytest.raises(L.NlinvError) as e:
         L.nlinv_apply_normal_static(N, J, 0, 220.0, 32.0, x, x, P, 0.1, o)
     assert e.value.code == L.NLINV_EINVAL
+
+
+def test_static_allocates_no_device_memory():
+    """After the first call on the device (its one-time set-up), further
+    calls leave the device's free memory unchanged: nothing is allocated."""
+    from paper_1701_08361_gb300 import nlinv as L
+    N, J = 64, 4
+    P, _, _ = radial_psf(N, 9, 5, 2)
+    g = O.Geometry(N=N, J=J)
+    x, d = random_xhat(g, 301), random_xhat(g, 302)
+    xd, dd, Pd = to_dev(x.flat()), to_dev(d.flat()), to_dev(P, torch.float32)
+    out = torch.empty_like(xd)
+    L.nlinv_apply_normal_static(N, J, 0, 220.0, 32.0, xd, dd, Pd, 0.5, out)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for alpha in (0.5, 0.25, 0.125):
+        L.nlinv_apply_normal_static(N, J, 0, 220.0, 32.0, xd, dd, Pd, alpha, out)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert rel(to_np(out), O.normal(x, d, P, 0.125, g).flat()) <= TOL
+
+
+def test_static_tables_follow_a_change_of_sizes():
+    """Calls alternating between grid sizes and weight constants: each call's
+    result matches the plan entry point (the cached tables are rewritten
+    whenever G, Gc, w_a or w_l change)."""
+    from paper_1701_08361_gb300 import nlinv as L
+    for N, J, Gc, w_a in [(20, 3, 0, 220.0), (64, 4, 32, 220.0), (20, 3, 0, 220.0), (20, 3, 0, 55.0)]:
+        P, _, _ = radial_psf(N, 9, 5, 0)
+        plan = make_plan(N, J, Gc, psf=P, w_a=w_a)
+        g = geometry(plan)
+        x, d = random_xhat(g, 400 + N), random_xhat(g, 401 + N)
+        xd, dd = to_dev(x.flat()), to_dev(d.flat())
+        want, got = torch.empty_like(xd), torch.empty_like(xd)
+        L.nlinv_apply_normal(plan, xd, dd, 0, 0.3, want)
+        L.nlinv_apply_normal_static(N, J, Gc, w_a, 32.0, xd, dd, to_dev(P, torch.float32), 0.3, got)
+        assert L.nlinv_sync(plan) == 0
+        torch.cuda.synchronize()
+        assert rel(to_np(got), to_np(want)) <= TOL, (N, J, Gc, w_a)
