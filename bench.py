@@ -282,6 +282,10 @@ def run_ours(args):
         raise RuntimeError(L.nlinv_strerror(rc))
 
     pk, pk_src = peaks()
+    path, cs = L.nlinv_plan_path(plan)
+    kernel_name = {1: "per-phase launches (k_row_cg, k_col_c, ...)",
+                   2: "k_frame (grid kernel, one launch per frame)",
+                   3: "k_frame_cl (cluster kernel, one launch per frame, %d CTAs per channel)" % cs}[path]
     fl = flops_per_frame(N, G, Gc, J, CFG["M"], CFG["CG"])
     by = bytes_per_frame(N, G, Gc, J, CFG["M"], CFG["CG"])
     mean_frame_s = statistics.mean(t_frames) / 1e3
@@ -296,22 +300,23 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": "real-time radial stream: N=160, G=320, J=10, 13 spokes x 5 turns, "
                                "7 Newton x 10 CG, moving phantom, sigma=1e-3",
-                   "frames_per_step": F, "exec_mode": ["persistent", "per-phase"][args.exec_mode],
+                   "frames_per_step": F,
+                   "exec_mode": ["automatic", "per-phase", "grid kernel", "cluster kernel"][args.exec_mode],
                    "l2": "inputs larger than L2 (%.0f MB of gridded data per step) and L2 flushed "
                          "between steps" % (Yall.numel() * 8 / 1e6),
                    "parallelism": "replicas" if world > 1 else "single"},
         "latency_ms": {"p50": round(statistics.median(lat), 4), "min": round(lat[0], 4)},
         "roofline": {"bound": "alu", "achieved": round(achieved, 3),
                      "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
-                     "frac": round(achieved / fp32_peak, 4), "traffic": profiled_traffic("k_frame_c2_stream"),
-                     "kernel": "k_frame (persistent, one launch per frame)",
+                     "frac": round(achieved / fp32_peak, 4), "traffic": profiled_traffic(["", "", "k_frame", "k_frame_cl"][path]),
+                     "kernel": kernel_name,
                      "peak_source": "FP32: %d SMs x 128 lanes x 2 flop x sm_max_mhz (%s)" % (sm_count(), pk_src)},
         "hbm": {"achieved_gbs": round(hbm, 1), "peak_gbs": pk["hbm_gbs"],
                 "frac": round(hbm / pk["hbm_gbs"], 4), "peak_source": pk_src},
         "e2e": {"value": round(frames / (e2e_ms / 1e3), 2), "unit": "frames/s",
                 "h2d_bytes_per_step": int(Yall.numel() * 8),
                 "d2h_bytes_per_step": int(imgs.numel() * 8)},
-        "gpu_launches": K * F * (1 if args.exec_mode == 0 else -1),
+        "gpu_launches": K * F,
         "clocks": clk,
     }
     if args.exec_mode == 1:
@@ -323,7 +328,7 @@ def run_ours(args):
         out["cpu_baseline"] = cpu_baseline(args.cpu_frames)
     if rank == 0 and args.plain_loop:
         out["plain_gpu_loop"] = plain_gpu_loop(raw, args)
-    if rank == 0 and args.unfused_frames > 0 and args.exec_mode == 0:
+    if rank == 0 and args.unfused_frames > 0 and args.exec_mode != 1:
         out["unfused_own_kernels"] = unfused_own_kernels(Yall, Ps, args)
     if rank == 0 and args.c3_groups > 0:
         out["batched_c3"] = batched_c3(args)
@@ -742,7 +747,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--frames-per-step", type=int, default=25)
-    ap.add_argument("--exec-mode", type=int, default=0, choices=[0, 1])
+    ap.add_argument("--exec-mode", type=int, default=0, choices=[0, 1, 2, 3])
     ap.add_argument("--cpu-frames", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-loop", type=int, default=1)

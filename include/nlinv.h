@@ -67,8 +67,19 @@ typedef struct {
   double damping;     /* x_ref = damping * x_prev (1.0 = Eq. 1 literally) */
   double w_a, w_l;    /* Sobolev weight constants (220, 32) */
   long long spin_limit; /* polls before a device-side wait gives up; 0 -> default */
-  int exec_mode;      /* 0: one persistent cooperative launch per frame;
-                         1: one launch per phase (unfused comparator) */
+  int exec_mode;      /* how nlinv_frame runs a frame:
+                         0: automatic -- the cluster kernel when the plan's
+                            channels fit it (3), else the grid kernel (2);
+                         1: one launch per phase (unfused comparator);
+                         2: one persistent cooperative launch, CTAs
+                            synchronised by grid barriers between phases;
+                         3: one persistent cooperative launch with one
+                            thread-block cluster per channel (per-channel
+                            passes exchange data in distributed shared
+                            memory; grid barriers only for the channel sum
+                            and the CG inner products); nlinv_plan returns
+                            NLINV_EUNSUPPORTED when the J clusters cannot be
+                            co-resident */
   int max_batch;      /* frames of this plan one nlinv_batch call may hold, 1..64;
                          0 -> 1 (the plan allocates one workspace per frame) */
 } nlinv_params_t;
@@ -88,6 +99,12 @@ int nlinv_plan_destroy(nlinv_plan_t plan);
 
 /* n_x, G and Gc of a plan (host values). */
 int nlinv_plan_sizes(nlinv_plan_t plan, long long* nx, int* G, int* Gc);
+
+/* How nlinv_frame runs this plan's frames: *exec_path = 1 (per-phase
+ * launches), 2 (grid kernel) or 3 (cluster kernel, see exec_mode), and
+ * *cluster_size = CTAs per channel cluster (0 unless exec_path is 3).
+ * Either pointer may be NULL. */
+int nlinv_plan_path(nlinv_plan_t plan, int* exec_path, int* cluster_size);
 
 /* Copy one turn's PSF (device float [G][G]) into the plan. */
 int nlinv_set_psf(nlinv_plan_t plan, int turn, const float* psf, nlinv_stream_t stream);

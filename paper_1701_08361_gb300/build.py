@@ -1,7 +1,15 @@
-"""Build the in-tree CUDA library libnlinv.so for sm_103a with nvcc."""
+"""Build the in-tree CUDA library libnlinv.so for sm_103a with nvcc.
+
+The host C ABI (csrc/nlinv.cu) is one translation unit; the kernels are
+compiled once per FFT grid size from csrc/grid.cu (the sizes listed by
+NLINV_GRIDS in csrc/common.h), all units in parallel, then linked into one
+shared library.
+"""
 from __future__ import annotations
 
+import concurrent.futures as cf
 import os
+import re
 import shutil
 import subprocess
 
@@ -10,6 +18,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libnlinv.so")
+OBJ = os.path.join(PKG, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -23,8 +32,11 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
-def sources():
-    return [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC)) if f.endswith(".cu")]
+def grid_sizes():
+    """(G1, G2) of every compiled grid size, as csrc/common.h lists them."""
+    txt = open(os.path.join(CSRC, "common.h")).read()
+    line = re.search(r"#define NLINV_GRIDS\(X\)(.*)", txt).group(1)
+    return [(int(a), int(b)) for a, b in re.findall(r"X\((\d+),\s*(\d+)\)", line)]
 
 
 def deps():
@@ -38,17 +50,38 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(d) <= t for d in deps())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every .cu under csrc/ into libnlinv.so (static cudart)."""
-    if not force and up_to_date():
-        return LIB
-    cmd = [nvcc(), *FLAGS, *ARCH, "-shared", "-I", INCLUDE, "-I", CSRC, "-o", LIB + ".tmp",
-           *sources()]
-    if verbose:
-        print(" ".join(cmd), flush=True)
-    subprocess.run(cmd, check=True)
-    os.replace(LIB + ".tmp", LIB)
-    return LIB
+def units(extra=(), sizes=None):
+    """(object path, nvcc compile command) of every translation unit."""
+    base = [nvcc(), *FLAGS, *ARCH, *extra, "-I", INCLUDE, "-I", CSRC, "-c"]
+    out = [(os.path.join(OBJ, "nlinv.o"), base + [os.path.join(CSRC, "nlinv.cu")])]
+    for g1, g2 in (sizes or grid_sizes()):
+        o = os.path.join(OBJ, f"grid_{g1}x{g2}.o")
+        out.append((o, base + [f"-DNLINV_G1={g1}", f"-DNLINV_G2={g2}", os.path.join(CSRC, "grid.cu")]))
+    return out
+
+
+def build(force: bool = False, verbose: bool = False, extra=(), sizes=None, lib: str = LIB) -> str:
+    """Compile every unit (in parallel) and link libnlinv.so (static cudart).
+    `sizes` restricts the grid sizes (quick builds; the others are then
+    unsupported), `extra` adds nvcc flags, `lib` names the output."""
+    if not force and lib == LIB and not extra and sizes is None and up_to_date():
+        return lib
+    os.makedirs(OBJ, exist_ok=True)
+    jobs = units(extra, sizes)
+
+    def run(job):
+        o, cmd = job
+        cmd = cmd + ["-o", o]
+        if verbose:
+            print(" ".join(cmd), flush=True)
+        subprocess.run(cmd, check=True)
+        return o
+
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 1))) as ex:
+        objs = list(ex.map(run, jobs))
+    subprocess.run([nvcc(), *ARCH, "-shared", "-o", lib + ".tmp", *objs], check=True)
+    os.replace(lib + ".tmp", lib)
+    return lib
 
 
 if __name__ == "__main__":

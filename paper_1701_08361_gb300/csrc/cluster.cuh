@@ -70,6 +70,8 @@ struct View {
   unsigned a_rb, a_cb, a_hb, a_kb;
 };
 
+// Built at the start of every phase (nothing of it stays live across the
+// persistent kernel's phases): the rank comes from an opaque read.
 template <class K>
 __device__ __forceinline__ View make_view(const Ctx& C, const Lay& L, float2* sm) {
   View v;
@@ -124,7 +126,8 @@ __device__ __forceinline__ void push_kb(const Lay& L, const View& v, int y, int 
 // of G), keep rows y < N, 1/G; pushed to HB of the row owners.
 // src: coil part [J][Gc][Gc] of a vector (global).
 template <class K>
-__device__ __forceinline__ void coil_y(const Ctx& C, const Lay& L, const View& v, const float2* src) {
+__device__ __forceinline__ void coil_y(const Ctx& C, const Lay& L, float2* sm, const float2* src) {
+  const View v = make_view<K>(C, L, sm);
   constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW;
   const int Gc = C.Gc, j = v.j;
   const int t = phase_tid();
@@ -172,7 +175,8 @@ __device__ __forceinline__ void coil_y(const Ctx& C, const Lay& L, const View& v
 // maps), u = rho c_j, forward FFT of the padded row, pushed to CB.
 // ROW_COILONLY: the coil maps only (global), for the final image.
 template <class K>
-__device__ __forceinline__ void row_b(const Ctx& C, const Lay& L, const View& v, int mode) {
+__device__ __forceinline__ void row_b(const Ctx& C, const Lay& L, float2* sm, int mode) {
+  const View v = make_view<K>(C, L, sm);
   constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW, RS = K::RS, N = K::NR;
   const int Gc = C.Gc, j = v.j;
   const int t = phase_tid();
@@ -250,7 +254,8 @@ __device__ __forceinline__ void row_b(const Ctx& C, const Lay& L, const View& v,
 // x pass of W^-1 of H r_k (HB), u = c_j r_rho + rho dc, forward row FFT,
 // pushed to CB.  rk: the residual (global; its rho part is read).
 template <class K>
-__device__ __forceinline__ void row_cg(const Ctx& C, const Lay& L, const View& v, const float2* rk) {
+__device__ __forceinline__ void row_cg(const Ctx& C, const Lay& L, float2* sm, const float2* rk) {
+  const View v = make_view<K>(C, L, sm);
   constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW, RS = K::RS, N = K::NR;
   const int Gc = C.Gc;
   const int t = phase_tid();
@@ -328,8 +333,9 @@ __device__ __forceinline__ void row_cg(const Ctx& C, const Lay& L, const View& v
 // COL_RHS : FFT_y, (Y - P X / G) / G, iFFT_y, keep N rows
 // The kept rows are pushed to RB of their row owners.
 template <class K>
-__device__ __forceinline__ void col_c(const Ctx& C, const Lay& L, const View& v, int mode, const float* P,
+__device__ __forceinline__ void col_c(const Ctx& C, const Lay& L, float2* sm, int mode, const float* P,
                                       const float2* Yin, Scal2 beta, bool first) {
+  const View v = make_view<K>(C, L, sm);
   constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW;
   const int j = v.j;
   const int t = phase_tid();
@@ -420,8 +426,9 @@ __device__ __forceinline__ void col_c(const Ctx& C, const Lay& L, const View& v,
 // also accumulates Re<p_rho, s_j> with p_rho = r_rho + beta p_old_rho formed
 // on the fly (pq: the caller's running term of Re<p, A p>).
 template <class K>
-__device__ __forceinline__ void row_d(const Ctx& C, const Lay& L, const View& v, const float2* pr_r,
+__device__ __forceinline__ void row_d(const Ctx& C, const Lay& L, float2* sm, const float2* pr_r,
                                       const float2* pr_old, Scal2 beta, bool first, float& pq) {
+  const View v = make_view<K>(C, L, sm);
   constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW, RS = K::RS, N = K::NR;
   const int Gc = C.Gc, j = v.j;
   const int t = phase_tid();
@@ -512,9 +519,10 @@ __device__ __forceinline__ void row_d(const Ctx& C, const Lay& L, const View& v,
 // E_RHS: r_0c = DF^H(...)_c - alpha (x_c - xr_s x_ref_c) (to out), rr +=
 //        |r_0c|^2, and H r_0 pushed to HB
 template <class K, int mode>
-__device__ __forceinline__ void col_e(const Ctx& C, const Lay& L, const View& v, float alpha, Scal2 beta,
+__device__ __forceinline__ void col_e(const Ctx& C, const Lay& L, float2* sm, float alpha, Scal2 beta,
                                       bool first, const float2* r_c, const float2* p_old, float2* p_new,
                                       float2* out, const float2* xr, float xr_s, float& acc) {
+  const View v = make_view<K>(C, L, sm);
   constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW, N = K::NR;
   const int Gc = C.Gc, j = v.j, NN = N * N;
   const int t = phase_tid();
@@ -616,8 +624,9 @@ __device__ __forceinline__ void col_e(const Ctx& C, const Lay& L, const View& v,
 // H r_{k+1} pushed to HB; on the last iteration x^_{n+1,c} = x^_{n,c} +
 // x_cg,c + a p_c instead.
 template <class K>
-__device__ __forceinline__ void upd_coil(const Ctx& C, const Lay& L, const View& v, Scal2 a, bool first, bool last,
+__device__ __forceinline__ void upd_coil(const Ctx& C, const Lay& L, float2* sm, Scal2 a, bool first, bool last,
                                          const float2* rk, float2* rk1, const float2* p, float& acc) {
+  const View v = make_view<K>(C, L, sm);
   constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW, N = K::NR;
   const int Gc = C.Gc, j = v.j, NN = N * N;
   const int t = phase_tid();

@@ -1,0 +1,173 @@
+// Declarations shared by the host C ABI (nlinv.cu) and the per-grid-size
+// kernel units (grid.cu, compiled once per FFT split G = G1 x G2): the plan,
+// the frame/batch launch arguments, error handling, and the table of
+// per-grid-size operations the host dispatches through.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "cluster.cuh"
+#include "nlinv.h"
+#include "phases.cuh"
+
+namespace nlinv {
+
+// ------------------------------------------------------------ errors
+// Record a failed CUDA call (thread-local message) and map it to a code.
+int cuda_fail(cudaError_t e, const char* what);
+
+#define CK(call)                                            \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return ::nlinv::cuda_fail(e_, #call); \
+  } while (0)
+
+#define CKL(what)                                           \
+  do {                                                      \
+    cudaError_t e_ = cudaGetLastError();                    \
+    if (e_ != cudaSuccess) return ::nlinv::cuda_fail(e_, what); \
+  } while (0)
+
+#define RC(x)                        \
+  do {                               \
+    int rc_ = (x);                   \
+    if (rc_ != NLINV_OK) return rc_; \
+  } while (0)
+
+constexpr int kMaxNewton = 32;
+constexpr int kMaxBatch = 64;
+
+// per-frame inputs and outputs
+struct FrameIO {
+  const float2* Y;
+  const float* P;
+  const float2* xprev;
+  float2* xout;
+  float2* rho_out;
+  float2* img_out;
+  const float2* xlast;    // regulariser of the last Newton step (x ref = damping * xlast), or null
+  const unsigned* wait;   // before the last Newton step: wait until *wait != 0, or null
+  unsigned* done;         // set to 1 once xout is written, or null
+};
+
+// barrier counter and completion flag of the frame group f of a launch, one
+// 128-byte line each so that groups do not contend
+constexpr int kBarStride = 32;   // unsigned words per frame group
+
+struct FrameArgs {
+  FrameIO io;
+  int M, K;
+  float damping;
+  float alpha[kMaxNewton];
+};
+
+struct BatchArgs {
+  int nf, M, K;
+  float damping;
+  float alpha[kMaxNewton];
+  size_t fstride;             // bytes between the frames' workspaces
+  FrameIO io[kMaxBatch];
+};
+
+// the workspace of frame f: every per-frame buffer moved by `off` bytes
+__host__ __device__ __forceinline__ Ctx frame_ctx(Ctx C, size_t off) {
+#define NLINV_ADV(T, p) C.p = (T*)((char*)C.p + off)
+  NLINV_ADV(float2, c);
+  NLINV_ADV(float2, h);
+  NLINV_ADV(float2, v);
+  NLINV_ADV(float2, s);
+  NLINV_ADV(float2, kb);
+  NLINV_ADV(float2, xn);
+  NLINV_ADV(float2, xref);
+  NLINV_ADV(float2, xcg);
+  NLINV_ADV(float2, rb[0]);
+  NLINV_ADV(float2, rb[1]);
+  NLINV_ADV(float2, q);
+  NLINV_ADV(float2, pb[0]);
+  NLINV_ADV(float2, pb[1]);
+  NLINV_ADV(float2, part);
+  NLINV_ADV(float2, Hr);
+  NLINV_ADV(float2, vold);
+#undef NLINV_ADV
+  return C;
+}
+
+inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+inline int plan_grid(int items, int min_items) {
+  int g = items > min_items ? items : min_items;
+  if (g < 1) g = 1;
+  return g > kMaxPart ? kMaxPart : g;
+}
+
+}  // namespace nlinv
+
+// ================================================================== plan
+// ================================================================== plan
+struct nlinv_plan_s {
+  nlinv_params_t prm;
+  int N, G, Gc, J, U;
+  long long nx;
+  int dev, nsm;
+  int max_batch = 1;
+  size_t fstride = 0;         // bytes between the per-frame workspaces
+  void* mem = nullptr;
+  void* prep = nullptr;
+  size_t prep_bytes = 0;
+  nlinv::Ctx C;               // frame 0's workspace
+  float* psf;
+  int coop_grid = 0;          // co-resident CTAs of k_frame
+  int batch_occ = 0;          // co-resident CTAs per SM of k_batch
+  int cl_cs = 0;              // CTAs per cluster of k_frame_cl (0: it does not fit)
+  nlinv::cl::Lay cl_lay;             // its shared-memory layout
+  cudaStream_t aux = nullptr; // stream of this plan's group inside nlinv_batch
+  cudaEvent_t ev_fork = nullptr, ev_done = nullptr;
+};
+
+namespace nlinv {
+
+// Operations of one FFT grid size, implemented by grid.cu for its Cfg.
+// Every call is asynchronous on `st` and returns NLINV_OK or an error code.
+struct GridOps {
+  int G;
+  // per plan: kernel attributes, co-residency of the persistent kernels and
+  // (exec_mode 0 or 3) the cluster kernel's configuration
+  int (*setup)(nlinv_plan_s* pl);
+  // for callers without a plan set-up: kernel attributes and the constant
+  // tables of this unit on the current device
+  int (*prepare)();
+  // coil maps c = W^-1 c^ of x into the plan's coil buffer
+  int (*coils)(const nlinv_plan_s* pl, cudaStream_t st, const float2* x);
+  // z = DF(x)[d], dx = DF(x)^H z, out = (DF^H P DF + alpha) d at x; with
+  // coils_ready the plan's coil buffer already holds W^-1 of x's coil part
+  int (*DF)(const nlinv_plan_s* pl, cudaStream_t st, const float2* x, const float2* d, float2* z,
+            bool coils_ready);
+  int (*DFH)(const nlinv_plan_s* pl, cudaStream_t st, const float2* x, const float2* z, float2* out,
+             bool coils_ready);
+  int (*normal)(const nlinv_plan_s* pl, cudaStream_t st, const float2* x, const float2* d, const float* P,
+                double alpha, float2* out, bool coils_ready);
+  // Y = U pad(img), img [J][N][N] in the plan's s buffer (gridding's last step)
+  int (*grid_fwd)(const nlinv_plan_s* pl, cudaStream_t st, float2* Y);
+  // one whole frame on the plan's execution path
+  int (*frame)(const nlinv_plan_s* pl, cudaStream_t st, const FrameArgs& F);
+  // frames of one plan in one cooperative launch of `grid` CTAs
+  int (*batch)(const nlinv_plan_s* pl, cudaStream_t st, const BatchArgs& B, int grid);
+#ifdef NLINV_TIMELINE
+  int (*timeline)(unsigned long long* host, int n);
+  int (*stages)(unsigned long long* ns, unsigned long long* cnt);
+#endif
+};
+
+// the compiled grid sizes G = G1 x G2 (one grid.cu unit each); a unit left
+// out of a build leaves its size unsupported (weak reference)
+#define NLINV_GRIDS(X) X(4, 4) X(4, 6) X(4, 10) X(8, 8) X(8, 16) X(16, 16) X(16, 20) X(16, 24) X(16, 32)
+#define NLINV_DECLARE_OPS(a, b) const GridOps* grid_ops_##a##_##b() __attribute__((weak));
+NLINV_GRIDS(NLINV_DECLARE_OPS)
+#undef NLINV_DECLARE_OPS
+
+// the operations of grid size G, or nullptr when G has no compiled schedule
+const GridOps* grid_ops(int G);
+
+}  // namespace nlinv

@@ -1,26 +1,27 @@
 // C-ABI implementation of the GB300 NLINV hot path (see include/nlinv.h).
 //
-// Kernels: the fused phases of phases.cuh, launched either one per phase or
-// all inside one persistent cooperative kernel per frame (grid barriers with
-// bounded waits between phases), plus the preprocessing kernels that turn a
-// trajectory into a PSF and raw samples into gridded data.
+// The host side: argument checks, plans, the batch and stream schedulers and
+// the reverse-mode driver.  The kernels of the hot path live in grid.cuh,
+// compiled once per FFT grid size (grid.cu) and reached through the GridOps
+// table of each size; the preprocessing kernels (PSF of a trajectory,
+// gridding by the adjoint NDFT) and the reverse mode's vector kernels are
+// here.
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
 
-#include "nlinv.h"
-#include "phases.cuh"
+#include "common.h"
 
 using namespace nlinv;
 
-namespace {
+namespace nlinv {
 
-// ------------------------------------------------------------ errors
 thread_local char g_cuda_err[256] = "";
 
 int cuda_fail(cudaError_t e, const char* what) {
@@ -28,290 +29,23 @@ int cuda_fail(cudaError_t e, const char* what) {
   return e == cudaErrorMemoryAllocation ? NLINV_ENOMEM : NLINV_ECUDA;
 }
 
-#define CK(call)                                   \
-  do {                                             \
-    cudaError_t e_ = (call);                       \
-    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
-  } while (0)
-
-#define CKL(what)                                  \
-  do {                                             \
-    cudaError_t e_ = cudaGetLastError();           \
-    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
-  } while (0)
-
-// ---------------------------------------------------- kernel wrappers
-// every CTA of a one-frame launch works on that frame
-__device__ __forceinline__ Ctx whole_grid(const Ctx& C0) {
-  Ctx C = C0;
-  C.bid = blockIdx.x;
-  C.nb = gridDim.x;
-  return C;
+const GridOps* grid_ops(int G) {
+#define NLINV_PICK_OPS(a, b) \
+  if (G == (a) * (b) && grid_ops_##a##_##b) return grid_ops_##a##_##b();
+  NLINV_GRIDS(NLINV_PICK_OPS)
+#undef NLINV_PICK_OPS
+  return nullptr;
 }
 
-template <class K>
-__global__ void __launch_bounds__(K::BS) k_coil_y(Ctx C0, const float2* src, float2* hout) {
-  const Ctx C = whole_grid(C0);
-  extern __shared__ float2 sm[];
-  phase_coil_y<K>(C, sm, src, hout);
-}
+}  // namespace nlinv
 
-template <class K>
-__global__ void __launch_bounds__(K::BS) k_row_cg(Ctx C0, int k, const float2* p_old, float2* p_new,
-                                                  float2* vout) {
-  const Ctx C = whole_grid(C0);
-  extern __shared__ float2 sm[];
-  __shared__ float2 sred[32];
-  phase_row_cg<K>(C, sm, sred, k, p_old, p_new, vout);
-}
+namespace {
 
-template <class K>
-__global__ void __launch_bounds__(K::BS) k_row_b(Ctx C0, int mode, const float2* hin, const float2* rho,
-                                                 const float2* drho, const float2* img, float2* vout) {
-  const Ctx C = whole_grid(C0);
-  extern __shared__ float2 sm[];
-  phase_row_b<K>(C, sm, mode, hin, rho, drho, img, vout);
-}
+bool supported_grid(int G) { return grid_ops(G) != nullptr; }
 
-template <class K>
-__global__ void __launch_bounds__(K::BS) k_col_c(Ctx C0, int mode, const float* P, const float2* Yin,
-                                                 float2* zout, float2* vio, int k) {
-  const Ctx C = whole_grid(C0);
-  extern __shared__ float2 sm[];
-  phase_col_c<K>(C, sm, mode, P, Yin, zout, vio, k);
-}
+bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
 
-template <class K>
-__global__ void __launch_bounds__(K::BS) k_row_d(Ctx C0, const float2* rho, const float2* win, float2* sout,
-                                                 float2* kbout) {
-  const Ctx C = whole_grid(C0);
-  extern __shared__ float2 sm[];
-  phase_row_d<K>(C, sm, rho, win, sout, kbout);
-}
-
-template <class K>
-__global__ void __launch_bounds__(K::BS) k_col_e(Ctx C0, int mode, float alpha, int k, const float2* kbin,
-                                                 const float2* sin, const float2* p_old, float2* p_new,
-                                                 float2* out, float2* hout, int slot) {
-  const Ctx C = whole_grid(C0);
-  extern __shared__ float2 sm[];
-  __shared__ float2 sred[32];
-  switch (mode) {
-    case E_CG: phase_col_e<K, E_CG>(C, sm, sred, alpha, k, kbin, sin, p_old, p_new, out, hout, slot); break;
-    case E_RHS: phase_col_e<K, E_RHS>(C, sm, sred, alpha, k, kbin, sin, p_old, p_new, out, hout, slot); break;
-    case E_DFH: phase_col_e<K, E_DFH>(C, sm, sred, alpha, k, kbin, sin, p_old, p_new, out, hout, slot); break;
-    default: phase_col_e<K, E_NORMAL>(C, sm, sred, alpha, k, kbin, sin, p_old, p_new, out, hout, slot);
-  }
-}
-
-template <class K>
-__global__ void __launch_bounds__(K::BS) k_upd(Ctx C0, int k, int last, const float2* p) {
-  const Ctx C = whole_grid(C0);
-  extern __shared__ float2 sm[];
-  __shared__ float2 sred[32];
-  phase_upd<K>(C, sm, sred, k, last != 0, p);
-}
-
-__global__ void k_init(Ctx C0, const float2* xprev, float damping) {
-  const Ctx C = whole_grid(C0);
-  phase_init(C, xprev, damping);
-}
-
-__global__ void k_final(Ctx C0, float2* xout, float2* rho_out, float2* img_out) {
-  const Ctx C = whole_grid(C0);
-  phase_final(C, xout, rho_out, img_out);
-}
-
-constexpr int kMaxNewton = 32;
-constexpr int kMaxBatch = 64;
-
-// per-frame inputs and outputs
-struct FrameIO {
-  const float2* Y;
-  const float* P;
-  const float2* xprev;
-  float2* xout;
-  float2* rho_out;
-  float2* img_out;
-  const float2* xlast;    // regulariser of the last Newton step (x ref = damping * xlast), or null
-  const unsigned* wait;   // before the last Newton step: wait until *wait != 0, or null
-  unsigned* done;         // set to 1 once xout is written, or null
-};
-
-// barrier counter and completion flag of the frame group f of a launch, one
-// 128-byte line each so that groups do not contend
-constexpr int kBarStride = 32;   // unsigned words per frame group
-
-struct FrameArgs {
-  FrameIO io;
-  int M, K;
-  float damping;
-  float alpha[kMaxNewton];
-};
-
-struct BatchArgs {
-  int nf, M, K;
-  float damping;
-  float alpha[kMaxNewton];
-  size_t fstride;             // bytes between the frames' workspaces
-  FrameIO io[kMaxBatch];
-};
-
-// the workspace of frame f: every per-frame buffer moved by `off` bytes
-__host__ __device__ __forceinline__ Ctx frame_ctx(Ctx C, size_t off) {
-#define NLINV_ADV(T, p) C.p = (T*)((char*)C.p + off)
-  NLINV_ADV(float2, c);
-  NLINV_ADV(float2, h);
-  NLINV_ADV(float2, v);
-  NLINV_ADV(float2, s);
-  NLINV_ADV(float2, kb);
-  NLINV_ADV(float2, xn);
-  NLINV_ADV(float2, xref);
-  NLINV_ADV(float2, xcg);
-  NLINV_ADV(float2, rb[0]);
-  NLINV_ADV(float2, rb[1]);
-  NLINV_ADV(float2, q);
-  NLINV_ADV(float2, pb[0]);
-  NLINV_ADV(float2, pb[1]);
-  NLINV_ADV(float2, part);
-  NLINV_ADV(float2, Hr);
-  NLINV_ADV(float2, vold);
-#undef NLINV_ADV
-  return C;
-}
-
-#ifdef NLINV_TIMELINE
-// profiling builds: per-CTA global timer at the start of every phase and
-// after every barrier of the first frame launch
-__device__ unsigned long long g_timeline[160][1024];
-__device__ __forceinline__ void tl_mark(int& i) {
-  if (threadIdx.x == 0 && blockIdx.x < 160 && i < 1024) {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    g_timeline[blockIdx.x][i] = t;
-  }
-  ++i;
-}
-#define NLINV_MARK() tl_mark(tl_i)
-#else
-#define NLINV_MARK()
-#endif
-
-// Every phase of every Newton step and CG iteration of one frame, separated
-// by bounded grid barriers (which all CTAs of the launch pass together).
-
-// The five phases of a Newton step's right-hand side (Eqs. (2)-(3): DF^H (Y -
-// P F^(x^_n)) - alpha_n (x^_n - x_ref), and H r_0).  They run once per Newton
-// step against ten CG iterations, so they live in their own function: kept
-// out of the persistent kernel's body, they no longer add to the register
-// pressure (and spills) of the CG loop, which measured 2 % faster per frame.
-template <class K>
-__device__ __noinline__ bool newton_rhs_phases(const Ctx& C, float2* sm, float2* sred, const FrameIO& io, float al,
-                                               bool lastreg, float damping, unsigned& epoch) {
-  const int NN = C.N * C.N;
-  phase_coil_y<K>(C, sm, C.xn + NN, C.h);
-  if (!grid_sync(C, epoch)) return false;
-  phase_row_b<K>(C, sm, ROW_COIL, C.h, C.xn, nullptr, nullptr, C.v);
-  if (!grid_sync(C, epoch)) return false;
-  phase_col_c<K>(C, sm, COL_RHS, io.P, io.Y, nullptr, C.v);
-  if (!grid_sync(C, epoch)) return false;
-  phase_row_d<K>(C, sm, C.xn, C.v, C.s, C.kb);
-  if (!grid_sync(C, epoch)) return false;
-  phase_col_e<K, E_RHS>(C, sm, sred, al, 0, C.kb, C.s, nullptr, nullptr, C.rb[0], C.Hr, SLOT_RR0,
-                        lastreg ? io.xlast : nullptr, lastreg ? damping : 1.f);
-  if (!grid_sync(C, epoch)) return false;
-  return true;
-}
-
-template <class K>
-__device__ __forceinline__ void frame_body(const Ctx& C, float2* sm, float2* sred, const FrameIO& io, int M,
-                                           int Kcg, float damping, const float* alpha) {
-  const int NN = C.N * C.N;
-  unsigned epoch = 0;
-#ifdef NLINV_TIMELINE
-  int tl_i = 0;
-#endif
-#define NLINV_SYNC()              \
-  NLINV_MARK();                   \
-  if (!grid_sync(C, epoch)) return; \
-  NLINV_MARK()
-  phase_init(C, io.xprev, damping);
-  NLINV_SYNC();
-  for (int n = 0; n < M; ++n) {
-    const float al = alpha[n];
-    const bool lastreg = (n == M - 1) && io.xlast != nullptr;
-    if (lastreg && io.wait) {   // Eq. (10): the last step waits for frame n - 1
-      if (threadIdx.x == 0) {
-        long long it = 0;
-        while (ld_acquire(io.wait) == 0u) {
-          if (*(volatile int*)C.err != 0) break;
-          if (++it > C.spin_limit) {
-            raise_err(C, DEV_ETIMEOUT);
-            break;
-          }
-          __nanosleep(64);
-        }
-      }
-      __syncthreads();
-      if (*(volatile int*)C.err != 0) return;
-    }
-    // Newton right-hand side: DF^H (Y - P F^(x^_n)) - alpha_n (x^_n - x_ref)
-    if (!newton_rhs_phases<K>(C, sm, sred, io, al, lastreg, damping, epoch)) return;
-    for (int k = 0; k < Kcg; ++k) {
-      float2* pk = C.pb[k & 1];
-      const float2* pm = C.pb[(k + 1) & 1];
-      phase_row_cg<K>(C, sm, sred, k, pm, pk, C.v);
-      NLINV_SYNC();
-      phase_col_cg<K>(C, sm, io.P, C.v, k);
-      NLINV_SYNC();
-      phase_row_d<K>(C, sm, C.xn, C.v, C.s, C.kb);
-      NLINV_SYNC();
-      phase_col_e<K, E_CG>(C, sm, sred, al, k, C.kb, C.s, pm, pk, C.q, nullptr, SLOT_PQ);
-      NLINV_SYNC();
-      phase_upd<K>(C, sm, sred, k, k == Kcg - 1, pk);
-      NLINV_SYNC();
-    }
-  }
-  phase_coil_y<K>(C, sm, C.xn + NN, C.h);
-  NLINV_SYNC();
-  phase_row_b<K>(C, sm, ROW_COILONLY, C.h, nullptr, nullptr, nullptr, nullptr);
-  NLINV_SYNC();
-  phase_final(C, io.xout, io.rho_out, io.img_out);
-  if (io.done) {   // publish x_out to a frame waiting on this one
-    NLINV_SYNC();
-    if (C.bid == 0 && threadIdx.x == 0) st_release(io.done, 1u);
-  }
-#undef NLINV_SYNC
-}
-
-// One whole NLINV frame in one cooperative launch.
-template <class K>
-__global__ void __launch_bounds__(K::BS, K::MINB) k_frame(Ctx C0, FrameArgs F) {
-  extern __shared__ float2 sm[];
-  __shared__ float2 sred[32];
-  const Ctx C = whole_grid(C0);
-  frame_body<K>(C, sm, sred, F.io, F.M, F.K, F.damping, F.alpha);
-}
-
-// Several frames of one size in one cooperative launch: the CTAs are split
-// into one contiguous group per frame; each group runs its frame on its own
-// workspace with its own barrier, so the groups progress independently (a
-// frame whose last Newton step waits for an earlier frame of the launch
-// cannot hold the others up: all groups are co-resident).
-template <class K>
-__global__ void __launch_bounds__(K::BS, K::MINB) k_batch(Ctx C0, BatchArgs B) {
-  extern __shared__ float2 sm[];
-  __shared__ float2 sred[32];
-  const int nf = B.nf;
-  const int f = (int)(((long long)blockIdx.x * nf) / gridDim.x);
-  const int lo = (int)(((long long)f * gridDim.x + nf - 1) / nf);
-  const int hi = (int)(((long long)(f + 1) * gridDim.x + nf - 1) / nf);
-  Ctx C = frame_ctx(C0, (size_t)f * B.fstride);
-  C.bid = blockIdx.x - lo;
-  C.nb = hi - lo;
-  C.bar = C0.bar + (size_t)f * kBarStride;   // this group's own barrier
-  frame_body<K>(C, sm, sred, B.io[f], B.M, B.K, B.damping, B.alpha);
-}
+int check_plan(const nlinv_plan_s* pl) { return pl ? NLINV_OK : NLINV_EINVAL; }
 
 // bounded wait on a device flag (used to test the timeout path)
 __global__ void k_wait_flag(const volatile int* flag, int expected, long long limit, int* err) {
@@ -406,179 +140,6 @@ __global__ void k_adj_ndft(int N, int S, const float2* __restrict__ yv, const fl
   if (x < N && y < N) img[((size_t)j * N + y) * N + x] = cscale(acc, scale);
 }
 
-// ----------------------------------------------------- size dispatch
-// NLINV_ONLY_G=<G> compiles one grid size only (quick profiling builds)
-#ifdef NLINV_ONLY_G
-#define NLINV_CASE(g, a, b)                          \
-  case g:                                            \
-    if constexpr (g == NLINV_ONLY_G) return f(Cfg<a, b>{}); \
-    else return NLINV_EUNSUPPORTED;
-#else
-#define NLINV_CASE(g, a, b) \
-  case g: return f(Cfg<a, b>{});
-#endif
-template <class F>
-int dispatch(int G, F&& f) {
-  switch (G) {
-    NLINV_CASE(16, 4, 4)
-    NLINV_CASE(24, 4, 6)
-    NLINV_CASE(40, 4, 10)
-    NLINV_CASE(64, 8, 8)
-    NLINV_CASE(128, 8, 16)
-    NLINV_CASE(256, 16, 16)
-    NLINV_CASE(320, 16, 20)
-    NLINV_CASE(384, 16, 24)
-    NLINV_CASE(512, 16, 32)
-    default: return NLINV_EUNSUPPORTED;
-  }
-}
-
-bool supported_grid(int G) {
-  return dispatch(G, [](auto) { return NLINV_OK; }) == NLINV_OK;
-}
-
-std::mutex g_mu;
-bool g_tw_ready[64] = {};
-
-int ensure_constants(int dev) {
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (dev < 0 || dev >= 64) return NLINV_EINVAL;
-  if (g_tw_ready[dev]) return NLINV_OK;
-  float2 h[TWL];
-  for (int e = 0; e < TWL; ++e) {
-    const double a = -2.0 * M_PI * (double)e / TWL;
-    h[e] = make_float2((float)std::cos(a), (float)std::sin(a));
-  }
-  CK(cudaMemcpyToSymbol(c_tw, h, sizeof(h)));
-  g_tw_ready[dev] = true;
-  return NLINV_OK;
-}
-
-bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
-
-}  // namespace
-
-// ================================================================== plan
-struct nlinv_plan_s {
-  nlinv_params_t prm;
-  int N, G, Gc, J, U;
-  long long nx;
-  int dev, nsm;
-  int max_batch = 1;
-  size_t fstride = 0;         // bytes between the per-frame workspaces
-  void* mem = nullptr;
-  void* prep = nullptr;
-  size_t prep_bytes = 0;
-  Ctx C;                      // frame 0's workspace
-  float* psf;
-  int coop_grid = 0;          // co-resident CTAs of k_frame
-  int batch_occ = 0;          // co-resident CTAs per SM of k_batch
-  cudaStream_t aux = nullptr; // stream of this plan's group inside nlinv_batch
-  cudaEvent_t ev_fork = nullptr, ev_done = nullptr;
-};
-
-namespace {
-
-size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
-
-int plan_grid(int items, int min_items) {
-  int g = items > min_items ? items : min_items;
-  if (g < 1) g = 1;
-  return g > kMaxPart ? kMaxPart : g;
-}
-
-template <class K>
-int set_smem_attrs() {
-  if (K::SMEM > 48 * 1024) {
-    CK(cudaFuncSetAttribute(k_coil_y<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
-    CK(cudaFuncSetAttribute(k_row_b<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
-    CK(cudaFuncSetAttribute(k_col_c<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
-    CK(cudaFuncSetAttribute(k_row_d<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
-    CK(cudaFuncSetAttribute(k_col_e<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
-    CK(cudaFuncSetAttribute(k_row_cg<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
-    CK(cudaFuncSetAttribute(k_upd<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
-    CK(cudaFuncSetAttribute(k_frame<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
-    CK(cudaFuncSetAttribute(k_batch<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
-  }
-  return NLINV_OK;
-}
-
-// launch helpers for the one-launch-per-phase path
-template <class K>
-struct Launch {
-  const nlinv_plan_s* pl;
-  cudaStream_t st;
-  int fixed = 0;   // if > 0: every launch uses this many CTAs (CG reductions need equal counts)
-  int pick(int g) const { return fixed > 0 ? fixed : g; }
-  int coil_y(const float2* src, float2* hout) const {
-    const Ctx& C = pl->C;
-    const int g = plan_grid(C.J * ((C.Gc + K::TW - 1) / K::TW), 1);
-    k_coil_y<K><<<pick(g), K::BS, K::SMEM, st>>>(C, src, hout);
-    CKL("k_coil_y");
-    return NLINV_OK;
-  }
-  int row_cg(int k, const float2* p_old, float2* p_new, float2* vout) const {
-    const Ctx& C = pl->C;
-    const int g = plan_grid(C.J * ((C.N + K::TW - 1) / K::TW), 1);
-    k_row_cg<K><<<pick(g), K::BS, K::SMEM, st>>>(C, k, p_old, p_new, vout);
-    CKL("k_row_cg");
-    return NLINV_OK;
-  }
-  int row_b(int mode, const float2* hin, const float2* rho, const float2* drho, const float2* img,
-            float2* vout) const {
-    const Ctx& C = pl->C;
-    const int g = plan_grid(C.J * ((C.N + K::TW - 1) / K::TW), 1);
-    k_row_b<K><<<pick(g), K::BS, K::SMEM, st>>>(C, mode, hin, rho, drho, img, vout);
-    CKL("k_row_b");
-    return NLINV_OK;
-  }
-  int col_c(int mode, const float* P, const float2* Yin, float2* zout, float2* vio, int k = 0) const {
-    const Ctx& C = pl->C;
-    const int g = plan_grid(C.J * ((C.G + K::TW - 1) / K::TW), 1);
-    k_col_c<K><<<pick(g), K::BS, K::SMEM, st>>>(C, mode, P, Yin, zout, vio, k);
-    CKL("k_col_c");
-    return NLINV_OK;
-  }
-  int row_d(const float2* rho, const float2* win, float2* sout, float2* kbout) const {
-    const Ctx& C = pl->C;
-    const int g = plan_grid(C.J * ((C.N + K::TW - 1) / K::TW), 1);
-    k_row_d<K><<<pick(g), K::BS, K::SMEM, st>>>(C, rho, win, sout, kbout);
-    CKL("k_row_d");
-    return NLINV_OK;
-  }
-  int col_e(int mode, float alpha, int k, const float2* kbin, const float2* sin, const float2* p_old,
-            float2* p_new, float2* out, float2* hout, int slot) const {
-    const Ctx& C = pl->C;
-    const int items = C.J * ((C.Gc + K::TW - 1) / K::TW);
-    const int g = plan_grid(items, (C.N * C.N + K::BS - 1) / K::BS);
-    k_col_e<K><<<pick(g), K::BS, K::SMEM, st>>>(C, mode, alpha, k, kbin, sin, p_old, p_new, out, hout, slot);
-    CKL("k_col_e");
-    return NLINV_OK;
-  }
-  int upd(int k, int last, const float2* p) const {
-    const Ctx& C = pl->C;
-    const int items = C.J * ((C.Gc + K::TW - 1) / K::TW);
-    const int g = plan_grid(items, (C.N * C.N + K::BS - 1) / K::BS);
-    k_upd<K><<<pick(g), K::BS, K::SMEM, st>>>(C, k, last, p);
-    CKL("k_upd");
-    return NLINV_OK;
-  }
-  // coil maps c_j = W^-1 c^_j of x^ into the plan's c buffer
-  int coils(const float2* xhat) const {
-    const Ctx& C = pl->C;
-    int rc = coil_y(xhat + (size_t)C.N * C.N, C.h);
-    if (rc) return rc;
-    return row_b(ROW_COILONLY, C.h, nullptr, nullptr, nullptr, nullptr);
-  }
-};
-
-#define RC(x)                 \
-  do {                        \
-    int rc_ = (x);            \
-    if (rc_ != NLINV_OK) return rc_; \
-  } while (0)
-
-int check_plan(const nlinv_plan_s* pl) { return pl ? NLINV_OK : NLINV_EINVAL; }
 
 }  // namespace
 
@@ -632,14 +193,14 @@ int nlinv_plan(nlinv_plan_t* out, const nlinv_params_t* p, const float* psf, nli
   if (p->n_turns < 1 || p->n_turns > 1024) return NLINV_EINVAL;
   if (!(p->alpha0 > 0.0) || !(p->q > 0.0) || p->q > 1.0 || !(p->damping >= 0.0)) return NLINV_EINVAL;
   if (!(p->w_a >= 0.0) || !(p->w_l >= 0.0)) return NLINV_EINVAL;
-  if (p->exec_mode != 0 && p->exec_mode != 1) return NLINV_EINVAL;
+  if (p->exec_mode < 0 || p->exec_mode > 3) return NLINV_EINVAL;
   if (p->max_batch < 0 || p->max_batch > kMaxBatch) return NLINV_EINVAL;
   if (psf && ((uintptr_t)psf & 3u)) return NLINV_EINVAL;
 
   cudaStream_t st = (cudaStream_t)stream;
   int dev = 0;
   CK(cudaGetDevice(&dev));
-  RC(ensure_constants(dev));
+  const GridOps* ops = grid_ops(G);
 
   nlinv_plan_s* pl = new nlinv_plan_s();
   pl->prm = *p;
@@ -761,22 +322,13 @@ int nlinv_plan(nlinv_plan_t* out, const nlinv_params_t* p, const float* psf, nli
   }
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(cuda_fail(e, "sync"));
 
-  rc = dispatch(G, [&](auto k) -> int {
-    using K = decltype(k);
-    RC(set_smem_attrs<K>());
-    int nbk = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nbk, k_frame<K>, K::BS, K::SMEM));
-    int g = nbk * pl->nsm;
-    if (g > kMaxPart) g = kMaxPart;
-    pl->coop_grid = g;
-    int nbb = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nbb, k_batch<K>, K::BS, K::SMEM));
-    pl->batch_occ = nbb;
-    CK(cudaStreamCreateWithFlags(&pl->aux, cudaStreamNonBlocking));
-    CK(cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming));
-    CK(cudaEventCreateWithFlags(&pl->ev_done, cudaEventDisableTiming));
-    return (g > 0 && nbb > 0) ? NLINV_OK : NLINV_ECUDA;
-  });
+  rc = ops->setup(pl);
+  if (rc == NLINV_OK) {
+    if ((e = cudaStreamCreateWithFlags(&pl->aux, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&pl->ev_done, cudaEventDisableTiming)) != cudaSuccess)
+      rc = cuda_fail(e, "plan streams");
+  }
   if (rc != NLINV_OK) return fail(rc);
   *out = pl;
   return NLINV_OK;
@@ -798,6 +350,15 @@ int nlinv_plan_sizes(nlinv_plan_t pl, long long* nx, int* G, int* Gc) {
   if (nx) *nx = pl->nx;
   if (G) *G = pl->G;
   if (Gc) *Gc = pl->Gc;
+  return NLINV_OK;
+}
+
+int nlinv_plan_path(nlinv_plan_t pl, int* exec_path, int* cluster_size) {
+  RC(check_plan(pl));
+  const int m = pl->prm.exec_mode;
+  const int path = m == 1 ? 1 : ((m == 0 || m == 3) && pl->cl_cs > 0 ? 3 : 2);
+  if (exec_path) *exec_path = path;
+  if (cluster_size) *cluster_size = path == 3 ? pl->cl_cs : 0;
   return NLINV_OK;
 }
 
@@ -856,44 +417,21 @@ int nlinv_grid(nlinv_plan_t pl, int S, const double* kxy, const void* y, void* Y
   k_adj_ndft<<<dim3((N + 15) / 16, (N + 15) / 16, J), dim3(16, 16), 0, st>>>(
       N, S, (const float2*)y, Ex, Ey, pl->C.s, (float)(1.0 / pl->G));
   CKL("k_adj_ndft");
-  return dispatch(pl->G, [&](auto k) -> int {
-    using K = decltype(k);
-    Launch<K> L{pl, st};
-    RC(L.row_b(ROW_IMG, nullptr, nullptr, nullptr, pl->C.s, pl->C.v));
-    return L.col_c(COL_FWD, nullptr, nullptr, (float2*)Y_out, pl->C.v);
-  });
+  return grid_ops(pl->G)->grid_fwd(pl, st, (float2*)Y_out);
 }
 
 int nlinv_apply_DF(nlinv_plan_t pl, const void* xhat, const void* dx, void* z, nlinv_stream_t stream) {
   RC(check_plan(pl));
   if (!xhat || !dx || !z || !aligned8(xhat) || !aligned8(dx) || !aligned8(z)) return NLINV_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
-  const float2* xh = (const float2*)xhat;
-  const float2* d = (const float2*)dx;
-  const size_t NN = (size_t)pl->N * pl->N;
-  return dispatch(pl->G, [&](auto k) -> int {
-    using K = decltype(k);
-    Launch<K> L{pl, st};
-    RC(L.coils(xh));
-    RC(L.coil_y(d + NN, pl->C.h));
-    RC(L.row_b(ROW_LIN, pl->C.h, xh, d, nullptr, pl->C.v));
-    return L.col_c(COL_FWD, nullptr, nullptr, (float2*)z, pl->C.v);
-  });
+  return grid_ops(pl->G)->DF(pl, st, (const float2*)xhat, (const float2*)dx, (float2*)z, false);
 }
 
 int nlinv_apply_DFH(nlinv_plan_t pl, const void* xhat, const void* z, void* dx_out, nlinv_stream_t stream) {
   RC(check_plan(pl));
   if (!xhat || !z || !dx_out || !aligned8(xhat) || !aligned8(z) || !aligned8(dx_out)) return NLINV_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
-  const float2* xh = (const float2*)xhat;
-  return dispatch(pl->G, [&](auto k) -> int {
-    using K = decltype(k);
-    Launch<K> L{pl, st};
-    RC(L.coils(xh));
-    RC(L.col_c(COL_INV, nullptr, (const float2*)z, nullptr, pl->C.v));
-    RC(L.row_d(xh, pl->C.v, pl->C.s, pl->C.kb));
-    return L.col_e(E_DFH, 0.f, 0, pl->C.kb, pl->C.s, nullptr, nullptr, (float2*)dx_out, nullptr, SLOT_PQ);
-  });
+  return grid_ops(pl->G)->DFH(pl, st, (const float2*)xhat, (const float2*)z, (float2*)dx_out, false);
 }
 
 int nlinv_apply_normal(nlinv_plan_t pl, const void* xhat, const void* dx, int turn, double alpha, void* out,
@@ -903,21 +441,8 @@ int nlinv_apply_normal(nlinv_plan_t pl, const void* xhat, const void* dx, int tu
   if (turn < 0 || turn >= pl->U || !(alpha >= 0.0)) return NLINV_EINVAL;
   if (out == xhat || out == dx) return NLINV_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
-  const float2* xh = (const float2*)xhat;
-  const float2* d = (const float2*)dx;
-  const size_t NN = (size_t)pl->N * pl->N;
   const float* P = pl->psf + (size_t)turn * pl->G * pl->G;
-  return dispatch(pl->G, [&](auto k) -> int {
-    using K = decltype(k);
-    Launch<K> L{pl, st};
-    RC(L.coils(xh));
-    RC(L.coil_y(d + NN, pl->C.h));
-    RC(L.row_b(ROW_LIN, pl->C.h, xh, d, nullptr, pl->C.v));
-    RC(L.col_c(COL_TOEP, P, nullptr, nullptr, pl->C.v));
-    RC(L.row_d(xh, pl->C.v, pl->C.s, pl->C.kb));
-    return L.col_e(E_NORMAL, (float)alpha, 0, pl->C.kb, pl->C.s, nullptr, (float2*)d, (float2*)out, nullptr,
-                   SLOT_PQ);
-  });
+  return grid_ops(pl->G)->normal(pl, st, (const float2*)xhat, (const float2*)dx, P, alpha, (float2*)out, false);
 }
 
 int nlinv_frame(nlinv_plan_t pl, const void* Y, int turn, const void* x_prev, void* x_out, void* rho_out,
@@ -941,43 +466,7 @@ int nlinv_frame(nlinv_plan_t pl, const void* Y, int turn, const void* x_prev, vo
   F.K = p.cg_iters;
   F.damping = (float)p.damping;
   for (int n = 0; n < F.M; ++n) F.alpha[n] = (float)(p.alpha0 * std::pow(p.q, n));
-  Ctx C = pl->C;
-  const int NN = pl->N * pl->N;
-  return dispatch(pl->G, [&](auto k) -> int {
-    using K = decltype(k);
-    if (p.exec_mode == 0) {
-      CK(cudaMemsetAsync(C.bar, 0, 2 * sizeof(unsigned), st));
-      void* args[] = {(void*)&C, (void*)&F};
-      CK(cudaLaunchCooperativeKernel((const void*)k_frame<K>, dim3(pl->coop_grid), dim3(K::BS), args,
-                                     (size_t)K::SMEM, st));
-      return NLINV_OK;
-    }
-    Launch<K> L{pl, st, pl->coop_grid};
-    const int ge = plan_grid((int)((C.nx + 255) / 256), 1);
-    k_init<<<ge, 256, 0, st>>>(C, F.io.xprev, F.damping);
-    CKL("k_init");
-    for (int n = 0; n < F.M; ++n) {
-      const float alpha = F.alpha[n];
-      RC(L.coil_y(C.xn + NN, C.h));
-      RC(L.row_b(ROW_COIL, C.h, C.xn, nullptr, nullptr, C.v));
-      RC(L.col_c(COL_RHS, F.io.P, F.io.Y, nullptr, C.v));
-      RC(L.row_d(C.xn, C.v, C.s, C.kb));
-      RC(L.col_e(E_RHS, alpha, 0, C.kb, C.s, nullptr, nullptr, C.rb[0], C.Hr, SLOT_RR0));
-      for (int kk = 0; kk < F.K; ++kk) {
-        float2* pk = C.pb[kk & 1];
-        const float2* pm = C.pb[(kk + 1) & 1];
-        RC(L.row_cg(kk, pm, pk, C.v));
-        RC(L.col_c(COL_CG, F.io.P, nullptr, nullptr, C.v, kk));
-        RC(L.row_d(C.xn, C.v, C.s, C.kb));
-        RC(L.col_e(E_CG, alpha, kk, C.kb, C.s, pm, pk, C.q, nullptr, SLOT_PQ));
-        RC(L.upd(kk, kk == F.K - 1, pk));
-      }
-    }
-    RC(L.coils(C.xn));
-    k_final<<<ge, 256, 0, st>>>(C, F.io.xout, F.io.rho_out, F.io.img_out);
-    CKL("k_final");
-    return NLINV_OK;
-  });
+  return grid_ops(pl->G)->frame(pl, st, F);
 }
 
 int nlinv_batch(const nlinv_frame_desc_t* frames, int nframes, nlinv_stream_t stream) {
@@ -1068,15 +557,7 @@ int nlinv_batch(const nlinv_frame_desc_t* frames, int nframes, nlinv_stream_t st
     if (grid < B.nf) return NLINV_EINVAL;
     cudaStream_t gs = fork ? pl->aux : st;
     if (fork) CK(cudaStreamWaitEvent(gs, plans[0]->ev_fork, 0));
-    Ctx C = pl->C;
-    const int rc = dispatch(pl->G, [&](auto k) -> int {
-      using K = decltype(k);
-      CK(cudaMemsetAsync(C.bar, 0, (size_t)B.nf * kBarStride * sizeof(unsigned), gs));
-      void* args[] = {(void*)&C, (void*)&B};
-      CK(cudaLaunchCooperativeKernel((const void*)k_batch<K>, dim3(grid), dim3(K::BS), args,
-                                     (size_t)K::SMEM, gs));
-      return NLINV_OK;
-    });
+    const int rc = grid_ops(pl->G)->batch(pl, gs, B, grid);
     if (rc != NLINV_OK) return rc;
     if (fork) {
       CK(cudaEventRecord(pl->ev_done, gs));
@@ -1221,7 +702,7 @@ int static_scratch(void** out, int G, int Gc, double w_a, double w_l, bool* fres
   int dev = 0;
   CK(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return NLINV_EINVAL;
-  RC(ensure_constants(dev));
+  RC(grid_ops(G)->prepare());
   std::lock_guard<std::mutex> lk(g_static_mu);
   if (!g_static_ptr[dev]) {
     void* p = nullptr;
@@ -1316,20 +797,7 @@ extern "C" int nlinv_apply_normal_static(int N, int J, int Gc, double w_a, doubl
     CKL("k_static_tables");
     static_tables_written(G, Gc, w_a, w_l);
   }
-  const float2* xh = (const float2*)xhat;
-  const float2* d = (const float2*)dx;
-  const size_t NN = (size_t)N * N;
-  return dispatch(G, [&](auto k) -> int {
-    using K = decltype(k);
-    RC(set_smem_attrs<K>());
-    Launch<K> L{&tmp, st};
-    RC(L.coils(xh));
-    RC(L.coil_y(d + NN, C.h));
-    RC(L.row_b(ROW_LIN, C.h, xh, d, nullptr, C.v));
-    RC(L.col_c(COL_TOEP, psf, nullptr, nullptr, C.v));
-    RC(L.row_d(xh, C.v, C.s, C.kb));
-    return L.col_e(E_NORMAL, (float)alpha, 0, C.kb, C.s, nullptr, (float2*)d, (float2*)out, nullptr, SLOT_PQ);
-  });
+  return grid_ops(G)->normal(&tmp, st, (const float2*)xhat, (const float2*)dx, psf, alpha, (float2*)out, false);
 }
 
 // ======================================================================
@@ -1484,17 +952,18 @@ struct GradOps {
   long long nx, nk;
   double* part;   // [kMaxDots][kDotBlocks]
   double* dres;   // device scalars [kMaxDots]
+  const GridOps* ops;
   // The plan's coil-map buffer holds W^-1 of lin's coil part when
   // coils_at == lin.  lin is the Newton step's checkpoint x^_n, which is not
   // written while it is the linearisation point; maps of any other point
   // (a buffer that may change between calls) are never reused.
   const float2* lin = nullptr;
   mutable const float2* coils_at = nullptr;
-  template <class Lc>
-  int coils(const Lc& L, const float2* w) const {
-    if (w != nullptr && w == lin && coils_at == lin) return NLINV_OK;
+  // whether the coil buffer already holds the maps of w; updates the record
+  bool coils_ready(const float2* w) const {
+    const bool ready = w != nullptr && w == lin && coils_at == lin;
     coils_at = (w == lin) ? lin : nullptr;
-    return L.coils(w);
+    return ready;
   }
 
   int grid(long long n) const {
@@ -1535,41 +1004,14 @@ struct GradOps {
     return NLINV_OK;
   }
   // z = DF(x)[d]
-  int DF(const float2* x, const float2* d, float2* z) const {
-    const size_t NN = (size_t)pl->N * pl->N;
-    return dispatch(pl->G, [&](auto k) -> int {
-      using K = decltype(k);
-      Launch<K> L{pl, st};
-      RC(coils(L, x));
-      RC(L.coil_y(d + NN, pl->C.h));
-      RC(L.row_b(ROW_LIN, pl->C.h, x, d, nullptr, pl->C.v));
-      return L.col_c(COL_FWD, nullptr, nullptr, z, pl->C.v);
-    });
-  }
+  int DF(const float2* x, const float2* d, float2* z) const { return ops->DF(pl, st, x, d, z, coils_ready(x)); }
   // out = DF(w)^H z
   int DFH(const float2* w, const float2* z, float2* out) const {
-    return dispatch(pl->G, [&](auto k) -> int {
-      using K = decltype(k);
-      Launch<K> L{pl, st};
-      RC(coils(L, w));
-      RC(L.col_c(COL_INV, nullptr, z, nullptr, pl->C.v));
-      RC(L.row_d(w, pl->C.v, pl->C.s, pl->C.kb));
-      return L.col_e(E_DFH, 0.f, 0, pl->C.kb, pl->C.s, nullptr, nullptr, out, nullptr, SLOT_PQ);
-    });
+    return ops->DFH(pl, st, w, z, out, coils_ready(w));
   }
   // out = (DF(x)^H P DF(x) + alpha) d
   int normal(const float2* x, const float2* d, double alpha, float2* out) const {
-    const size_t NN = (size_t)pl->N * pl->N;
-    return dispatch(pl->G, [&](auto k) -> int {
-      using K = decltype(k);
-      Launch<K> L{pl, st};
-      RC(coils(L, x));
-      RC(L.coil_y(d + NN, pl->C.h));
-      RC(L.row_b(ROW_LIN, pl->C.h, x, d, nullptr, pl->C.v));
-      RC(L.col_c(COL_TOEP, P, nullptr, nullptr, pl->C.v));
-      RC(L.row_d(x, pl->C.v, pl->C.s, pl->C.kb));
-      return L.col_e(E_NORMAL, (float)alpha, 0, pl->C.kb, pl->C.s, nullptr, (float2*)d, out, nullptr, SLOT_PQ);
-    });
+    return ops->normal(pl, st, x, d, P, alpha, out, coils_ready(x));
   }
   int psf(float2* z, float s) const {
     k_psf_scale<<<grid(nk), 256, 0, st>>>(pl->J, pl->G, z, P, s);
@@ -1705,7 +1147,7 @@ extern "C" int nlinv_frame_vjp(nlinv_plan_t pl, const void* Y, int turn, const v
   GradWS w;
   RC(grad_workspace(pl, w));
   GradOps O{pl, (cudaStream_t)stream, pl->psf + (size_t)turn * pl->G * pl->G, pl->nx,
-            (long long)pl->J * pl->G * pl->G, w.part, w.dres};
+            (long long)pl->J * pl->G * pl->G, w.part, w.dres, grid_ops(pl->G)};
   const long long nx = O.nx, nk = O.nk;
   const float2* Yd = (const float2*)Y;
   // x^_0 and x_ref
@@ -1836,14 +1278,13 @@ extern "C" int nlinv_frame_vjp(nlinv_plan_t pl, const void* Y, int turn, const v
 }
 
 #ifdef NLINV_TIMELINE
-extern "C" int nlinv_debug_timeline(unsigned long long* host, int n) {
-  if (n > 160 * 1024) n = 160 * 1024;
-  CK(cudaMemcpyFromSymbol(host, g_timeline, (size_t)n * sizeof(unsigned long long)));
-  return NLINV_OK;
+// profiling builds: the timeline and stage sums of grid size G's unit
+extern "C" int nlinv_debug_timeline(int G, unsigned long long* host, int n) {
+  const GridOps* o = grid_ops(G);
+  return o ? o->timeline(host, n) : NLINV_EUNSUPPORTED;
 }
-extern "C" int nlinv_debug_stages(unsigned long long* ns, unsigned long long* cnt) {
-  CK(cudaMemcpyFromSymbol(ns, nlinv::g_stage_ns, sizeof(unsigned long long) * 64));
-  CK(cudaMemcpyFromSymbol(cnt, nlinv::g_stage_n, sizeof(unsigned long long) * 64));
-  return NLINV_OK;
+extern "C" int nlinv_debug_stages(int G, unsigned long long* ns, unsigned long long* cnt) {
+  const GridOps* o = grid_ops(G);
+  return o ? o->stages(ns, cnt) : NLINV_EUNSUPPORTED;
 }
 #endif

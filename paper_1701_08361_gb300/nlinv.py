@@ -74,6 +74,7 @@ _SIGS = {
     "nlinv_plan_sizes": (_I, [_VP, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_I),
                               ctypes.POINTER(_I)]),
     "nlinv_set_psf": (_I, [_VP, _I, _VP, _VP]),
+    "nlinv_plan_path": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "nlinv_psf": (_I, [_VP, _I, _I, _VP, _VP, _VP]),
     "nlinv_grid": (_I, [_VP, _I, _VP, _VP, _VP, _VP]),
     "nlinv_apply_DF": (_I, [_VP, _VP, _VP, _VP, _VP]),
@@ -189,6 +190,13 @@ def nlinv_plan(params: nlinv_params_t, psf=None, stream=None) -> Plan:
 
 def nlinv_plan_destroy(plan: Plan):
     plan.close()
+
+
+def nlinv_plan_path(plan: Plan):
+    """(exec_path, cluster_size): 1 per-phase, 2 grid kernel, 3 cluster kernel."""
+    path, cs = ctypes.c_int(), ctypes.c_int()
+    _check(_lib().nlinv_plan_path(plan.handle, ctypes.byref(path), ctypes.byref(cs)), "nlinv_plan_path")
+    return path.value, cs.value
 
 
 def nlinv_set_psf(plan: Plan, turn: int, psf, stream=None):

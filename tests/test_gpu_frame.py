@@ -1,14 +1,15 @@
 """GPU parity of whole NLINV frames (IRGNM + CG, Eqs. (2)-(3)) against the
 FP64 oracle through the C ABI: final x^, rho and the coil-combined image
 within relative L2 1e-3 (FP32 arithmetic against FP64 through 7 x 10
-Newton/CG steps), in both execution modes."""
+Newton/CG steps), in every execution mode (per-phase launches, the grid
+kernel, the cluster kernel, and the automatic choice)."""
 import numpy as np
 import pytest
 import torch
 
 import oracle as O
 import synth as S
-from gpu_util import make_plan, rel, to_dev, to_np
+from gpu_util import make_plan, radial_psf, rel, to_dev, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -35,7 +36,7 @@ def run_frames(plan, frames, xprev=None):
     return out
 
 
-@pytest.mark.parametrize("exec_mode", [0, 1])
+@pytest.mark.parametrize("exec_mode", [0, 1, 2, 3])
 def test_cartesian_frame_C1(exec_mode):
     """64x64 image on the 128 grid, 4 coils, every 3rd line + 16 centre
     lines, sigma = 1e-3, 7 Newton x 10 CG, alpha0 = 1, q = 1/2."""
@@ -84,13 +85,15 @@ def test_frame_from_given_x_prev_and_modes_agree():
     prm = O.Params(newton_steps=4, cg_iters=6, alpha0=2.0, q=0.6, damping=0.8)
     ref = O.nlinv_frame(Y, P, xp, xp.scale(0.8), g, prm)
     outs = []
-    for mode in (0, 1):
+    for mode in (1, 2, 3):
         plan = make_plan(N, J, psf=P, newton_steps=4, cg_iters=6, alpha0=2.0, q=0.6,
                          damping=0.8, exec_mode=mode)
         (x, _, _), = run_frames(plan, [(Y, 0)], xprev=xp.flat())
         assert rel(x, ref.flat()) <= TOL
         outs.append(x)
+    # the same arithmetic up to the order of the inner products' partial sums
     assert rel(outs[0], outs[1]) <= 1e-5
+    assert rel(outs[2], outs[1]) <= 1e-5
 
 
 @pytest.mark.slow
@@ -139,7 +142,8 @@ def test_frame_C4_size_modes_agree():
     assert rel(xs[0], xs[1]) <= 1e-5
 
 
-@pytest.mark.parametrize("M,K,mode", [(1, 1, 0), (1, 0, 0), (2, 1, 1), (1, 3, 1), (3, 0, 1)])
+@pytest.mark.parametrize("M,K,mode", [(1, 1, 2), (1, 0, 2), (2, 1, 1), (1, 3, 1), (3, 0, 1),
+                                      (1, 1, 3), (1, 0, 3), (2, 2, 3)])
 def test_degenerate_iteration_counts(M, K, mode):
     """One Newton step, one CG iteration, or none (x^ stays the initial value):
     the drivers' edge cases against the oracle, ragged N=20 grid."""
@@ -153,3 +157,32 @@ def test_degenerate_iteration_counts(M, K, mode):
     if K == 0:
         np.testing.assert_array_equal(x, O.XVec.initial(g).flat().astype(np.complex64))
     assert rel(x, ref.flat()) <= TOL
+
+
+@pytest.mark.parametrize("N,J,Gc,cs", [(160, 10, 0, 0), (64, 4, 0, 0), (20, 3, 0, 0), (32, 4, 16, 0),
+                                       (160, 10, 0, 8), (128, 8, 0, 0)])
+def test_cluster_kernel_matches_oracle_and_grid_kernel(N, J, Gc, cs, monkeypatch):
+    """The cluster-resident frame kernel (one cluster per channel; ragged
+    partitions of rows, columns and coil columns for most sizes) against the
+    FP64 oracle and against the grid kernel, on a radial frame from the
+    initial value (3 Newton x 5 CG)."""
+    from paper_1701_08361_gb300 import nlinv as L
+    if cs:
+        monkeypatch.setenv("NLINV_CLUSTER_CS", str(cs))
+    K, U = 13, 5
+    P, kx, ky = radial_psf(N, K, U, 1)
+    g = O.Geometry(N=N, J=J, Gc=Gc or None)
+    coils = S.coil_maps(N, J, 7)
+    _, _, y, _, _ = S.radial_frame(N, J, K, U, 1, seed=7, coils=coils)
+    Y = O.grid_data(kx, ky, y, N, g.G)
+    prm = O.Params(newton_steps=3, cg_iters=5)
+    ref = O.nlinv_frame(Y, P, O.XVec.initial(g), O.XVec.initial(g), g, prm)
+    xs = []
+    for mode in (3, 2):
+        plan = make_plan(N, J, Gc, psf=P, newton_steps=3, cg_iters=5, exec_mode=mode)
+        (x, rho, img), = run_frames(plan, [(Y, 0)])
+        e = rel(x, ref.flat())
+        print(f"N={N} J={J} mode {mode}: rel L2 vs FP64 {e:.2e}")
+        assert e <= TOL
+        xs.append(x)
+    assert rel(xs[0], xs[1]) <= 1e-4
