@@ -110,9 +110,10 @@ int nlinv_plan_path(nlinv_plan_t plan, int* exec_path, int* cluster_size);
 int nlinv_set_psf(nlinv_plan_t plan, int turn, const float* psf, nlinv_stream_t stream);
 
 /* PSF of a trajectory (Sec. 2.2 footnote): P(f) = sum_d p(d) e^{-2 pi i f.d/G},
- * p(d) = G^-2 sum_s e^{2 pi i k_s.d} for d in [-(N-1), N-1]^2, evaluated as
- * G^-2 sum_s Dir(kx_s - fx/G) Dir(ky_s - fy/G) with the Dirichlet kernel
- * Dir(t) = sin((2N-1) pi t) / sin(pi t).
+ * p(d) = (2N)^-2 sum_s e^{2 pi i k_s.d} for d in [-(N-1), N-1]^2, evaluated as
+ * (2N)^-2 sum_s Dir(kx_s - fx/G) Dir(ky_s - fy/G) with the Dirichlet kernel
+ * Dir(t) = sin((2N-1) pi t) / sin(pi t).  (A sample is (2N)^-1 sum_r x_r
+ * e^{-2 pi i k.r}: its scale is fixed by the image size N.)
  * kxy: device double [S][2] (kx, ky) in cycles/pixel.  The result goes into
  * the plan's slot `turn` and, if P_out != NULL, to device float [G][G]. */
 int nlinv_psf(nlinv_plan_t plan, int turn, int S, const double* kxy, float* P_out,
@@ -120,7 +121,7 @@ int nlinv_psf(nlinv_plan_t plan, int turn, int S, const double* kxy, float* P_ou
 
 /* Gridding by the exact adjoint NDFT (the preprocessing stage of Sec. 3.1
  * in its brute-force form): Y_j = U pad(A^H y_j) with
- * (A^H y)(r) = G^-1 sum_s y_s e^{+2 pi i k_s.r}.
+ * (A^H y)(r) = (2N)^-1 sum_s y_s e^{+2 pi i k_s.r}.
  * kxy: device double [S][2]; y: device complex64 [J][S];
  * Y_out: device complex64 [J][G][G].  Uses the plan's workspace. */
 int nlinv_grid(nlinv_plan_t plan, int S, const double* kxy, const void* y, void* Y_out,

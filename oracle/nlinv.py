@@ -20,8 +20,12 @@ Equation numbers follow their order of appearance in the paper:
 
 Conventions (readings of the paper where it is silent; each is listed with
 its reason in the design notes):
-  * grid G = 2N (gamma = 1 in Eq. (8)); image rho on N x N, the FOV sits at
-    rows/cols [0, N) of the G grid (pad writes top-left, crop reads top-left);
+  * grid G = 2 gamma N of Eq. (8) (G = 2N, gamma = 1, unless chosen); image
+    rho on N x N, the FOV sits at rows/cols [0, N) of the G grid (pad writes
+    top-left, crop reads top-left);
+  * a sample at k (cycles/pixel) is (2N)^-1 sum_r x_r exp(-2 pi i k.r): the
+    scale is fixed by the image size, not by the reconstruction grid, so the
+    same raw samples can be reconstructed on any G;
   * unitary 2-D DFT U (norm="ortho"), unshifted frequency order;
   * D^-1(f) = (1 + a |2f/G|^2)^(-l/2) with a = 220, l = 32 -- identical to the
     figure's 880 |k|^2 with k = f/G -- applied on the coil grid;
@@ -59,18 +63,21 @@ def workers() -> int:
 
 @dataclass(frozen=True)
 class Geometry:
-    """Sizes of one reconstruction: image side N, grid G = 2N, J channels,
-    coil grid Gc (Sec. 3.2: Gc = floor(G/4); Gc = G disables the crop), and
-    the Sobolev weight constants (Fig. 7)."""
+    """Sizes of one reconstruction: image side N, J channels, coil grid Gc
+    (Sec. 3.2: Gc = floor(G/4); Gc = G disables the crop), the Sobolev weight
+    constants (Fig. 7) and the grid G = 2 gamma N of Eq. (8) (`grid`; None
+    means gamma = 1, G = 2N).  G >= 2N - 1 keeps the PSF convolution of the
+    FOV free of wrap-around."""
     N: int
     J: int
     Gc: int | None = None
     w_a: float = 220.0
     w_l: float = 32.0
+    grid: int | None = None
 
     @property
     def G(self) -> int:
-        return 2 * self.N
+        return 2 * self.N if self.grid is None else self.grid
 
     @property
     def gc(self) -> int:
@@ -353,23 +360,25 @@ def nlinv_stream(frames, geom: Geometry, prm: Params = Params(),
 # ---------------------------------------------------------------------------
 
 def ndft_adjoint(kx: np.ndarray, ky: np.ndarray, y: np.ndarray, N: int, G: int) -> np.ndarray:
-    """A^H y: (A^H y)(r) = G^-1 sum_s y_s exp(+2 pi i k_s . r) on the N x N FOV,
-    y [..., S] -> [..., N, N]."""
+    """A^H y: (A^H y)(r) = (2N)^-1 sum_s y_s exp(+2 pi i k_s . r) on the N x N
+    FOV, y [..., S] -> [..., N, N] (the sample scale is fixed by N; G only
+    names the reconstruction grid)."""
     r = np.arange(N, dtype=np.float64)
     ex = np.exp(2j * np.pi * np.outer(kx, r))        # [S, x]
     ey = np.exp(2j * np.pi * np.outer(ky, r))        # [S, y]
-    return np.einsum("...s,sy,sx->...yx", y, ey, ex, optimize=True) / G
+    return np.einsum("...s,sy,sx->...yx", y, ey, ex, optimize=True) / (2 * N)
 
 
 def psf_kernel(kx: np.ndarray, ky: np.ndarray, N: int, G: int) -> np.ndarray:
     """PSF P on the G grid for the Toeplitz form of A^H A:
-    p(d) = G^-2 sum_s exp(2 pi i k_s . d) for d in [-(N-1), N-1]^2, embedded
-    circularly on the G grid (p = 0 at offset +-N), P = G U p.  Real because
-    p is Hermitian; returned as float64 [G, G]."""
+    p(d) = (2N)^-2 sum_s exp(2 pi i k_s . d) for d in [-(N-1), N-1]^2, embedded
+    circularly on the G grid (G >= 2N - 1: no offset wraps onto another),
+    P = G U p.  Real because p is Hermitian; returned as [G, G]."""
+    assert G >= 2 * N - 1
     d = np.arange(-(N - 1), N, dtype=np.float64)
     ex = np.exp(2j * np.pi * np.outer(kx, d))        # [S, dx]
     ey = np.exp(2j * np.pi * np.outer(ky, d))        # [S, dy]
-    p = (ey.T @ ex) / (G * G)                          # [dy, dx]
+    p = (ey.T @ ex) / (4.0 * N * N)                    # [dy, dx]
     emb = np.zeros((G, G), np.complex128)
     idx = d.astype(int) % G
     emb[idx[:, None], idx[None, :]] = p

@@ -397,7 +397,7 @@ int nlinv_psf(nlinv_plan_t pl, int turn, int S, const double* kxy, float* P_out,
   CKL("k_dirichlet");
   float* P = pl->psf + (size_t)turn * G * G;
   k_psf_gemm<<<dim3((G + 15) / 16, (G + 15) / 16), dim3(16, 16), 0, st>>>(G, S, Dx, Dy, P,
-                                                                         1.0 / ((double)G * G));
+                                                                         1.0 / (4.0 * pl->N * pl->N));
   CKL("k_psf_gemm");
   if (P_out) CK(cudaMemcpyAsync(P_out, P, (size_t)G * G * sizeof(float), cudaMemcpyDeviceToDevice, st));
   return NLINV_OK;
@@ -415,7 +415,7 @@ int nlinv_grid(nlinv_plan_t pl, int S, const double* kxy, const void* y, void* Y
   k_ndft_tables<<<(S * N + 255) / 256, 256, 0, st>>>(N, S, kxy, Ex, Ey);
   CKL("k_ndft_tables");
   k_adj_ndft<<<dim3((N + 15) / 16, (N + 15) / 16, J), dim3(16, 16), 0, st>>>(
-      N, S, (const float2*)y, Ex, Ey, pl->C.s, (float)(1.0 / pl->G));
+      N, S, (const float2*)y, Ex, Ey, pl->C.s, (float)(0.5 / pl->N));
   CKL("k_adj_ndft");
   return grid_ops(pl->G)->grid_fwd(pl, st, (float2*)Y_out);
 }

@@ -160,7 +160,7 @@ def test_degenerate_iteration_counts(M, K, mode):
 
 
 @pytest.mark.parametrize("N,J,Gc,cs", [(160, 10, 0, 0), (64, 4, 0, 0), (20, 3, 0, 0), (32, 4, 16, 0),
-                                       (160, 10, 0, 8), (128, 8, 0, 0)])
+                                       (128, 8, 0, 8), (128, 8, 0, 0), (64, 4, 0, 6)])
 def test_cluster_kernel_matches_oracle_and_grid_kernel(N, J, Gc, cs, monkeypatch):
     """The cluster-resident frame kernel (one cluster per channel; ragged
     partitions of rows, columns and coil columns for most sizes) against the

@@ -16,8 +16,10 @@ def rand_x(g, seed, scale=1.0):
                   S.random_complex((g.J, g.gc, g.gc), seed + 1, scale))
 
 
+# the twofold grid, and grids G = 2 gamma N of Eq. (8) with odd G and odd Gc
 GEOMS = [O.Geometry(N=8, J=2), O.Geometry(N=8, J=3, Gc=16), O.Geometry(N=12, J=2),
-         O.Geometry(N=10, J=4, Gc=8)]
+         O.Geometry(N=10, J=4, Gc=8), O.Geometry(N=8, J=2, grid=20), O.Geometry(N=6, J=2, grid=15),
+         O.Geometry(N=8, J=3, grid=24, Gc=8)]
 
 
 @pytest.mark.parametrize("g", GEOMS)
@@ -98,12 +100,14 @@ def test_four_ffts_per_channel_per_iteration(monkeypatch):
     assert per_ch * g.J * int(vals["cg_iterations"]) == int(vals["ffts_per_image"])
 
 
-def test_crop_of_coil_grid_is_exact_in_fp64():
+@pytest.mark.parametrize("N,G", [(16, 32), (12, 36), (10, 30), (8, 22)])
+def test_crop_of_coil_grid_is_exact_in_fp64(N, G):
     """Sec. 3.2 crop: the discarded band carries D^-1 <= (1 + 220/16)^-16, so
     the normal operator on the cropped grid equals the uncropped one
-    restricted to the kept band (rel 1e-12)."""
-    gf = O.Geometry(N=16, J=2, Gc=32)
-    gcr = O.Geometry(N=16, J=2)
+    restricted to the kept band (rel 1e-12); on the twofold grid and on
+    grids G = 2 gamma N (Eq. (8)) where Gc = floor(G/4) may be odd."""
+    gf = O.Geometry(N=N, J=2, Gc=G, grid=G)
+    gcr = O.Geometry(N=N, J=2, grid=G)
     x = rand_x(gcr, 21)
     d = rand_x(gcr, 23)
     xf = O.XVec(x.rho, O.crop_coef(O.pad_coef(x.chat, gf.G), gf.gc))

@@ -8,13 +8,13 @@ import oracle as O
 import synth as S
 
 
-def ndft_matrix(kx, ky, N, G):
-    """Dense A: row s, column (y, x): G^-1 exp(-2 pi i (kx x + ky y)), built by loops."""
+def ndft_matrix(kx, ky, N):
+    """Dense A: row s, column (y, x): (2N)^-1 exp(-2 pi i (kx x + ky y)), built by loops."""
     A = np.zeros((len(kx), N * N), complex)
     for s in range(len(kx)):
         for y in range(N):
             for x in range(N):
-                A[s, y * N + x] = np.exp(-2j * np.pi * (kx[s] * x + ky[s] * y)) / G
+                A[s, y * N + x] = np.exp(-2j * np.pi * (kx[s] * x + ky[s] * y)) / (2 * N)
     return A
 
 
@@ -28,11 +28,12 @@ def trajectories(N):
     yield S.radial_trajectory(N, 3, 5, 2)
 
 
-@pytest.mark.parametrize("N", [4, 6, 8])
-def test_psf_toeplitz_equals_AHA(N):
-    G = 2 * N
+@pytest.mark.parametrize("N,G", [(4, 8), (6, 12), (8, 16), (4, 7), (5, 13), (6, 18), (8, 27)])
+def test_psf_toeplitz_equals_AHA(N, G):
+    """On the twofold grid and on every grid G = 2 gamma N >= 2N - 1 of
+    Eq. (8) (odd sizes included): the same A^H A."""
     for kx, ky in trajectories(N):
-        A = ndft_matrix(kx, ky, N, G)
+        A = ndft_matrix(kx, ky, N)
         P = O.psf_kernel(kx, ky, N, G)
         assert np.max(np.abs(P.imag)) <= 1e-12 * np.max(np.abs(P.real))
         for seed in range(3):
@@ -46,11 +47,10 @@ def test_psf_toeplitz_equals_AHA(N):
             assert abs(q.real - np.linalg.norm(A @ x.reshape(-1)) ** 2) < 1e-12 * q.real
 
 
-@pytest.mark.parametrize("N", [4, 8])
-def test_grid_data_is_adjoint_ndft(N):
-    G = 2 * N
+@pytest.mark.parametrize("N,G", [(4, 8), (8, 16), (6, 15), (8, 24)])
+def test_grid_data_is_adjoint_ndft(N, G):
     kx, ky = S.radial_trajectory(N, 5, 3, 1)
-    A = ndft_matrix(kx, ky, N, G)
+    A = ndft_matrix(kx, ky, N)
     y = S.random_complex((2, len(kx)), 4)
     Y = O.grid_data(kx, ky, y, N, G)
     for j in range(2):
