@@ -15,12 +15,13 @@
  *
  * Conventions (all entry points):
  *   - complex data are complex64, interleaved (re, im) float pairs, row-major;
- *   - N = image side, G = 2N grid side, J channels, Gc coil grid side (even);
+ *   - N = image side, G grid side (2N, or 2 gamma N of Eq. 8), J channels,
+ *     Gc coil grid side (odd or even);
  *   - unitary 2-D DFT U, unshifted frequency order; the field of view is
  *     rows/cols [0, N) of the G grid;
  *   - the unknown x^ is ONE contiguous vector of n_x = N*N + J*Gc*Gc complex
  *     values: rho [N][N] followed by c^ [J][Gc][Gc], the c^ grid holding
- *     frequency f at index f mod Gc;
+ *     frequency f at index f mod Gc (f in [-floor(Gc/2), (Gc-1)/2]);
  *   - D_W^-1(f) = (1 + w_a |2f/G|^2)^(-w_l/2) (Fig. 7's (1+880|k|^2)^16 with
  *     k = f/G for w_a = 220, w_l = 32);
  *   - the PSF P [U][G][G] is real, unshifted; sampling enters only through
@@ -57,9 +58,9 @@ typedef struct nlinv_plan_s* nlinv_plan_t;
 typedef void* nlinv_stream_t; /* cudaStream_t */
 
 typedef struct {
-  int N;              /* image side; grid G = 2N (gamma = 1 in Eq. 8) */
+  int N;              /* image side (the field of view is N x N) */
   int J;              /* receive channels */
-  int Gc;             /* coil grid side, even, <= G; 0 -> floor(G/4) (Sec. 3.2) */
+  int Gc;             /* coil grid side, <= G; 0 -> floor(G/4) (Sec. 3.2) */
   int newton_steps;   /* M, 1..32 (Sec. 2.2: 6 to 10) */
   int cg_iters;       /* fixed CG iterations per Newton step, 0..4096 */
   int n_turns;        /* U: PSFs held by the plan (Sec. 2.1, Fig. 3) */
@@ -82,6 +83,9 @@ typedef struct {
                             co-resident */
   int max_batch;      /* frames of this plan one nlinv_batch call may hold, 1..64;
                          0 -> 1 (the plan allocates one workspace per frame) */
+  int G;              /* grid side: 0 -> 2N (gamma = 1); else a grid G = 2 gamma N
+                         of Eq. 8 (G >= 2N) among the compiled (G, N) pairs
+                         (NLINV_EUNSUPPORTED otherwise) */
 } nlinv_params_t;
 
 /* Fill `p` with the defaults for an N x N image and J channels:

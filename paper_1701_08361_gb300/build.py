@@ -33,10 +33,10 @@ def nvcc() -> str:
 
 
 def grid_sizes():
-    """(G1, G2) of every compiled grid size, as csrc/common.h lists them."""
+    """(G1, G2, N) of every compiled grid, as NLINV_GRIDS in csrc/common.h lists them."""
     txt = open(os.path.join(CSRC, "common.h")).read()
-    line = re.search(r"#define NLINV_GRIDS\(X\)(.*)", txt).group(1)
-    return [(int(a), int(b)) for a, b in re.findall(r"X\((\d+),\s*(\d+)\)", line)]
+    body = re.search(r"#define NLINV_GRIDS\(X\)((?:.*\\\n)*.*)", txt).group(1)
+    return [(int(a), int(b), int(n)) for a, b, n in re.findall(r"X\((\d+),\s*(\d+),\s*(\d+)\)", body)]
 
 
 def deps():
@@ -54,9 +54,10 @@ def units(extra=(), sizes=None):
     """(object path, nvcc compile command) of every translation unit."""
     base = [nvcc(), *FLAGS, *ARCH, *extra, "-I", INCLUDE, "-I", CSRC, "-c"]
     out = [(os.path.join(OBJ, "nlinv.o"), base + [os.path.join(CSRC, "nlinv.cu")])]
-    for g1, g2 in (sizes or grid_sizes()):
-        o = os.path.join(OBJ, f"grid_{g1}x{g2}.o")
-        out.append((o, base + [f"-DNLINV_G1={g1}", f"-DNLINV_G2={g2}", os.path.join(CSRC, "grid.cu")]))
+    for g1, g2, n in (sizes or grid_sizes()):
+        o = os.path.join(OBJ, f"grid_{g1}x{g2}_{n}.o")
+        out.append((o, base + [f"-DNLINV_G1={g1}", f"-DNLINV_G2={g2}", f"-DNLINV_NR={n}",
+                               os.path.join(CSRC, "grid.cu")]))
     return out
 
 

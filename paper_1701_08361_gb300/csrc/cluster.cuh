@@ -163,7 +163,8 @@ __device__ __forceinline__ void coil_y(const Ctx& C, const Lay& L, float2* sm, c
         for (int n1 = 0; n1 < G1; ++n1) b[n1] = v.xb[(k2 * G1 + n1) * TW + cc];
         dft<G1, true>(b);
 #pragma unroll
-        for (int k1 = 0; k1 < G1 / 2; ++k1) push_hb(L, v, Gc, k2 + G2 * k1, fx, cscale(b[k1], C.inv_G));
+        for (int k1 = 0; k1 < K::B2; ++k1)
+          if (in2<K>(k1, k2)) push_hb(L, v, Gc, k2 + G2 * k1, fx, cscale(b[k1], C.inv_G));
       }
     }
     __syncthreads();
@@ -212,7 +213,7 @@ __device__ __forceinline__ void row_b(const Ctx& C, const Lay& L, float2* sm, in
 #pragma unroll
       for (int k1 = 0; k1 < G1; ++k1) {
         u[k1] = czero();
-        if (k1 < G1 / 2) {
+        if (in2<K>(k1, k2)) {
           const int x = k2 + G2 * k1;
           C.c[((size_t)j * N + y) * N + x] = b[k1];
           if (mode == ROW_COIL) {
@@ -263,11 +264,11 @@ __device__ __forceinline__ void row_cg(const Ctx& C, const Lay& L, float2* sm, c
     const int rr = t / G2, k2 = t % G2;
     const bool ok = rr < TW && r0 + rr < v.ny;
     const int yl = r0 + rr, y = v.y0 + yl;
-    float2 rv[G1 / 2], rh[G1 / 2];   // stage-2 operands requested before stage 1
+    float2 rv[K::B2], rh[K::B2];   // stage-2 operands requested before stage 1
 #pragma unroll
-    for (int k1 = 0; k1 < G1 / 2; ++k1) {
+    for (int k1 = 0; k1 < K::B2; ++k1) {
       rv[k1] = rh[k1] = czero();
-      if (ok) {
+      if (ok && in2<K>(k1, k2)) {
         const int ir = y * N + k2 + G2 * k1;
         rv[k1] = ldcg(rk + ir);
         rh[k1] = ldcg(C.xn + ir);
@@ -300,7 +301,9 @@ __device__ __forceinline__ void row_cg(const Ctx& C, const Lay& L, float2* sm, c
       dft<G1, true>(b);
 #pragma unroll
       for (int k1 = 0; k1 < G1; ++k1)
-        u[k1] = (k1 < G1 / 2) ? cadd(cmul(v.cj[yl * N + k2 + G2 * k1], rv[k1]), cmul(rh[k1], b[k1])) : czero();
+        u[k1] = (k1 < K::B2 && in2<K>(k1, k2))
+                    ? cadd(cmul(v.cj[yl * N + k2 + G2 * k1], rv[k1 < K::B2 ? k1 : 0]), cmul(rh[k1 < K::B2 ? k1 : 0], b[k1]))
+                    : czero();
       dft<G1, false>(u);
 #pragma unroll
       for (int kb = 1; kb < G1; ++kb) u[kb] = cmul(u[kb], twg<false>(C.tw, k2 * kb));
@@ -361,7 +364,7 @@ __device__ __forceinline__ void col_c(const Ctx& C, const Lay& L, float2* sm, in
 #pragma unroll
         for (int n2 = 0; n2 < G2; ++n2) {
           a[n2] = czero();
-          if (n2 < G2 / 2) {
+          if (in1<K>(n2, n1)) {
             const int y = n1 + G1 * n2;
             a[n2] = v.cb[y * L.C + xl];
             if (cg) {
@@ -412,7 +415,8 @@ __device__ __forceinline__ void col_c(const Ctx& C, const Lay& L, float2* sm, in
         for (int a2 = 0; a2 < G2; ++a2) d[a2] = v.xb[(m1 * G2 + a2) * TW + cc];
         dft<G2, true>(d);
 #pragma unroll
-        for (int m2 = 0; m2 < G2 / 2; ++m2) push_rb<K>(L, v, m1 + G1 * m2, x, d[m2]);
+        for (int m2 = 0; m2 < K::B1; ++m2)
+          if (in1<K>(m2, m1)) push_rb<K>(L, v, m1 + G1 * m2, x, d[m2]);
       }
     }
     __syncthreads();
@@ -436,11 +440,11 @@ __device__ __forceinline__ void row_d(const Ctx& C, const Lay& L, float2* sm, co
     const int rr = t / G2, k2 = t % G2;
     const bool ok = rr < TW && r0 + rr < v.ny;
     const int yl = r0 + rr, y = v.y0 + yl;
-    float2 rh[G1 / 2], pp[G1 / 2];
+    float2 rh[K::B2], pp[K::B2];
 #pragma unroll
-    for (int k1 = 0; k1 < G1 / 2; ++k1) {
+    for (int k1 = 0; k1 < K::B2; ++k1) {
       rh[k1] = pp[k1] = czero();
-      if (ok) {
+      if (ok && in2<K>(k1, k2)) {
         const int ir = y * N + k2 + G2 * k1;
         rh[k1] = ldcg(C.xn + ir);
         if (pr_r) {
@@ -476,12 +480,13 @@ __device__ __forceinline__ void row_d(const Ctx& C, const Lay& L, float2* sm, co
 #pragma unroll
       for (int k1 = 0; k1 < G1; ++k1) {
         g[k1] = czero();
-        if (k1 < G1 / 2) {
+        if (k1 < K::B2 && in2<K>(k1, k2)) {
+          const int kk = k1 < K::B2 ? k1 : 0;
           const int x = k2 + G2 * k1;
           const float2 sv = cconjmul(v.cj[yl * N + x], b[k1]);
           C.s[((size_t)j * N + y) * N + x] = sv;
-          if (pr_r) pq = fmaf(pp[k1].x, sv.x, fmaf(pp[k1].y, sv.y, pq));
-          g[k1] = cconjmul(rh[k1], b[k1]);
+          if (pr_r) pq = fmaf(pp[kk].x, sv.x, fmaf(pp[kk].y, sv.y, pq));
+          g[k1] = cconjmul(rh[kk], b[k1]);
         }
       }
       dft<G1, false>(g);
@@ -534,7 +539,7 @@ __device__ __forceinline__ void col_e(const Ctx& C, const Lay& L, float2* sm, fl
     float2 a[G2];
 #pragma unroll
     for (int n2 = 0; n2 < G2; ++n2)
-      a[n2] = (n1 < G1 && colok && n2 < G2 / 2) ? v.kb[(n1 + G1 * n2) * L.Cc + fl] : czero();
+      a[n2] = (n1 < G1 && colok && in1<K>(n2, n1)) ? v.kb[(n1 + G1 * n2) * L.Cc + fl] : czero();
     const int k2 = t / TW;
     const bool ok = k2 < G2 && colok;
     float2 o1[G1], o2[G1];
@@ -612,7 +617,8 @@ __device__ __forceinline__ void col_e(const Ctx& C, const Lay& L, float2* sm, fl
         for (int a2 = 0; a2 < G2; ++a2) d[a2] = v.xb[(m1 * G2 + a2) * TW + cc];
         dft<G2, true>(d);
 #pragma unroll
-        for (int m2 = 0; m2 < G2 / 2; ++m2) push_hb(L, v, Gc, m1 + G1 * m2, fx, cscale(d[m2], C.inv_G));
+        for (int m2 = 0; m2 < K::B1; ++m2)
+          if (in1<K>(m2, m1)) push_hb(L, v, Gc, m1 + G1 * m2, fx, cscale(d[m2], C.inv_G));
       }
     }
     __syncthreads();
@@ -675,7 +681,8 @@ __device__ __forceinline__ void upd_coil(const Ctx& C, const Lay& L, float2* sm,
       for (int q1 = 0; q1 < G1; ++q1) b[q1] = v.xb[(k2 * G1 + q1) * TW + cc];
       dft<G1, true>(b);
 #pragma unroll
-      for (int k1 = 0; k1 < G1 / 2; ++k1) push_hb(L, v, Gc, k2 + G2 * k1, fx, cscale(b[k1], C.inv_G));
+      for (int k1 = 0; k1 < K::B2; ++k1)
+        if (in2<K>(k1, k2)) push_hb(L, v, Gc, k2 + G2 * k1, fx, cscale(b[k1], C.inv_G));
     }
     __syncthreads();
   }

@@ -131,7 +131,7 @@ namespace nlinv {
 // Operations of one FFT grid size, implemented by grid.cu for its Cfg.
 // Every call is asynchronous on `st` and returns NLINV_OK or an error code.
 struct GridOps {
-  int G;
+  int G, N;
   // per plan: kernel attributes, co-residency of the persistent kernels and
   // (exec_mode 0 or 3) the cluster kernel's configuration
   int (*setup)(nlinv_plan_s* pl);
@@ -160,14 +160,20 @@ struct GridOps {
 #endif
 };
 
-// the compiled grid sizes G = G1 x G2 (one grid.cu unit each); a unit left
-// out of a build leaves its size unsupported (weak reference)
-#define NLINV_GRIDS(X) X(4, 4) X(4, 6) X(4, 10) X(8, 8) X(8, 16) X(16, 16) X(16, 20) X(16, 24) X(16, 32)
-#define NLINV_DECLARE_OPS(a, b) const GridOps* grid_ops_##a##_##b() __attribute__((weak));
+// The compiled grids X(G1, G2, N): G = G1 x G2 with an N x N field of view
+// (one grid.cu unit each).  G = 2N for the twofold grids; the others are
+// grids G = 2 gamma N of Eq. (8) with gamma > 1 (radix 3, 5 and 7 splits).
+// A unit left out of a build leaves its grid unsupported (weak reference).
+#define NLINV_GRIDS(X)                                                                          \
+  X(4, 4, 8) X(4, 6, 12) X(4, 10, 20) X(8, 8, 32) X(8, 16, 64) X(16, 16, 128) X(16, 20, 160)   \
+  X(16, 24, 192) X(16, 32, 256) X(4, 14, 20) X(6, 9, 20) X(8, 9, 24) X(16, 28, 160)            \
+  X(16, 30, 160) X(18, 27, 160) X(16, 32, 160) X(20, 28, 160) X(16, 24, 128)
+#define NLINV_DECLARE_OPS(a, b, n) const GridOps* grid_ops_##a##_##b##_##n() __attribute__((weak));
 NLINV_GRIDS(NLINV_DECLARE_OPS)
 #undef NLINV_DECLARE_OPS
 
-// the operations of grid size G, or nullptr when G has no compiled schedule
-const GridOps* grid_ops(int G);
+// the operations of grid G with an N x N field of view, or nullptr when that
+// pair has no compiled schedule
+const GridOps* grid_ops(int G, int N);
 
 }  // namespace nlinv

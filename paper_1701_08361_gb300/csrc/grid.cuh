@@ -538,9 +538,14 @@ int ensure_constants() {
   if (dev < 0 || dev >= 64) return NLINV_EINVAL;
   if (g_tw_ready[dev]) return NLINV_OK;
   float2 h[TWL];
-  for (int e = 0; e < TWL; ++e) {
-    const double a = -2.0 * M_PI * (double)e / TWL;
-    h[e] = make_float2((float)std::cos(a), (float)std::sin(a));
+  int off = 0;
+  for (int i = 0; i < kNumTwLens; ++i) {   // block L: exp(-2 pi i e / L), e < L
+    const int L = kTwLens[i];
+    for (int e = 0; e < L; ++e) {
+      const double a = -2.0 * M_PI * (double)e / L;
+      h[off + e] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+    off += L;
   }
   CK(cudaMemcpyToSymbol(c_tw, h, sizeof(h)));
   g_tw_ready[dev] = true;
@@ -671,7 +676,7 @@ struct Ops {
 
 template <class K>
 const GridOps* make_ops() {
-  static const GridOps ops = {K::G, &Ops<K>::setup, &Ops<K>::prepare, &Ops<K>::coils, &Ops<K>::DF,
+  static const GridOps ops = {K::G, K::NR, &Ops<K>::setup, &Ops<K>::prepare, &Ops<K>::coils, &Ops<K>::DF,
                               &Ops<K>::DFH, &Ops<K>::normal, &Ops<K>::grid_fwd, &Ops<K>::frame, &Ops<K>::batch
 #ifdef NLINV_TIMELINE
                               , &read_timeline, &read_stages

@@ -29,9 +29,9 @@ int cuda_fail(cudaError_t e, const char* what) {
   return e == cudaErrorMemoryAllocation ? NLINV_ENOMEM : NLINV_ECUDA;
 }
 
-const GridOps* grid_ops(int G) {
-#define NLINV_PICK_OPS(a, b) \
-  if (G == (a) * (b) && grid_ops_##a##_##b) return grid_ops_##a##_##b();
+const GridOps* grid_ops(int G, int N) {
+#define NLINV_PICK_OPS(a, b, n) \
+  if (G == (a) * (b) && N == (n) && grid_ops_##a##_##b##_##n) return grid_ops_##a##_##b##_##n();
   NLINV_GRIDS(NLINV_PICK_OPS)
 #undef NLINV_PICK_OPS
   return nullptr;
@@ -41,7 +41,7 @@ const GridOps* grid_ops(int G) {
 
 namespace {
 
-bool supported_grid(int G) { return grid_ops(G) != nullptr; }
+bool supported_grid(int G, int N) { return grid_ops(G, N) != nullptr; }
 
 bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
 
@@ -177,17 +177,19 @@ int nlinv_default_params(nlinv_params_t* p, int N, int J) {
   p->spin_limit = 0;
   p->exec_mode = 0;
   p->max_batch = 1;
+  p->G = 0;
   return NLINV_OK;
 }
 
 int nlinv_plan(nlinv_plan_t* out, const nlinv_params_t* p, const float* psf, nlinv_stream_t stream) {
   if (!out || !p) return NLINV_EINVAL;
   *out = nullptr;
-  const int N = p->N, G = 2 * p->N, J = p->J;
+  const int N = p->N, G = p->G ? p->G : 2 * p->N, J = p->J;
   const int Gc = p->Gc ? p->Gc : G / 4;
   if (N <= 0 || J <= 0 || J > 4096) return NLINV_EINVAL;
-  if (!supported_grid(G)) return NLINV_EUNSUPPORTED;
-  if (Gc < 2 || Gc > G || (Gc & 1)) return NLINV_EINVAL;
+  if (G < 2 * N) return NLINV_EINVAL;
+  if (!supported_grid(G, N)) return NLINV_EUNSUPPORTED;
+  if (Gc < 2 || Gc > G) return NLINV_EINVAL;
   if (p->newton_steps < 1 || p->newton_steps > kMaxNewton) return NLINV_EINVAL;
   if (p->cg_iters < 0 || p->cg_iters > 4096) return NLINV_EINVAL;
   if (p->n_turns < 1 || p->n_turns > 1024) return NLINV_EINVAL;
@@ -200,7 +202,7 @@ int nlinv_plan(nlinv_plan_t* out, const nlinv_params_t* p, const float* psf, nli
   cudaStream_t st = (cudaStream_t)stream;
   int dev = 0;
   CK(cudaGetDevice(&dev));
-  const GridOps* ops = grid_ops(G);
+  const GridOps* ops = grid_ops(G, N);
 
   nlinv_plan_s* pl = new nlinv_plan_s();
   pl->prm = *p;
@@ -417,21 +419,21 @@ int nlinv_grid(nlinv_plan_t pl, int S, const double* kxy, const void* y, void* Y
   k_adj_ndft<<<dim3((N + 15) / 16, (N + 15) / 16, J), dim3(16, 16), 0, st>>>(
       N, S, (const float2*)y, Ex, Ey, pl->C.s, (float)(0.5 / pl->N));
   CKL("k_adj_ndft");
-  return grid_ops(pl->G)->grid_fwd(pl, st, (float2*)Y_out);
+  return grid_ops(pl->G, pl->N)->grid_fwd(pl, st, (float2*)Y_out);
 }
 
 int nlinv_apply_DF(nlinv_plan_t pl, const void* xhat, const void* dx, void* z, nlinv_stream_t stream) {
   RC(check_plan(pl));
   if (!xhat || !dx || !z || !aligned8(xhat) || !aligned8(dx) || !aligned8(z)) return NLINV_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
-  return grid_ops(pl->G)->DF(pl, st, (const float2*)xhat, (const float2*)dx, (float2*)z, false);
+  return grid_ops(pl->G, pl->N)->DF(pl, st, (const float2*)xhat, (const float2*)dx, (float2*)z, false);
 }
 
 int nlinv_apply_DFH(nlinv_plan_t pl, const void* xhat, const void* z, void* dx_out, nlinv_stream_t stream) {
   RC(check_plan(pl));
   if (!xhat || !z || !dx_out || !aligned8(xhat) || !aligned8(z) || !aligned8(dx_out)) return NLINV_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
-  return grid_ops(pl->G)->DFH(pl, st, (const float2*)xhat, (const float2*)z, (float2*)dx_out, false);
+  return grid_ops(pl->G, pl->N)->DFH(pl, st, (const float2*)xhat, (const float2*)z, (float2*)dx_out, false);
 }
 
 int nlinv_apply_normal(nlinv_plan_t pl, const void* xhat, const void* dx, int turn, double alpha, void* out,
@@ -442,7 +444,7 @@ int nlinv_apply_normal(nlinv_plan_t pl, const void* xhat, const void* dx, int tu
   if (out == xhat || out == dx) return NLINV_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   const float* P = pl->psf + (size_t)turn * pl->G * pl->G;
-  return grid_ops(pl->G)->normal(pl, st, (const float2*)xhat, (const float2*)dx, P, alpha, (float2*)out, false);
+  return grid_ops(pl->G, pl->N)->normal(pl, st, (const float2*)xhat, (const float2*)dx, P, alpha, (float2*)out, false);
 }
 
 int nlinv_frame(nlinv_plan_t pl, const void* Y, int turn, const void* x_prev, void* x_out, void* rho_out,
@@ -466,7 +468,7 @@ int nlinv_frame(nlinv_plan_t pl, const void* Y, int turn, const void* x_prev, vo
   F.K = p.cg_iters;
   F.damping = (float)p.damping;
   for (int n = 0; n < F.M; ++n) F.alpha[n] = (float)(p.alpha0 * std::pow(p.q, n));
-  return grid_ops(pl->G)->frame(pl, st, F);
+  return grid_ops(pl->G, pl->N)->frame(pl, st, F);
 }
 
 int nlinv_batch(const nlinv_frame_desc_t* frames, int nframes, nlinv_stream_t stream) {
@@ -557,7 +559,7 @@ int nlinv_batch(const nlinv_frame_desc_t* frames, int nframes, nlinv_stream_t st
     if (grid < B.nf) return NLINV_EINVAL;
     cudaStream_t gs = fork ? pl->aux : st;
     if (fork) CK(cudaStreamWaitEvent(gs, plans[0]->ev_fork, 0));
-    const int rc = grid_ops(pl->G)->batch(pl, gs, B, grid);
+    const int rc = grid_ops(pl->G, pl->N)->batch(pl, gs, B, grid);
     if (rc != NLINV_OK) return rc;
     if (fork) {
       CK(cudaEventRecord(pl->ev_done, gs));
@@ -702,7 +704,7 @@ int static_scratch(void** out, int G, int Gc, double w_a, double w_l, bool* fres
   int dev = 0;
   CK(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return NLINV_EINVAL;
-  RC(grid_ops(G)->prepare());
+  RC(grid_ops(G, G / 2)->prepare());
   std::lock_guard<std::mutex> lk(g_static_mu);
   if (!g_static_ptr[dev]) {
     void* p = nullptr;
@@ -733,9 +735,9 @@ extern "C" int nlinv_apply_normal_static(int N, int J, int Gc, double w_a, doubl
                                          nlinv_stream_t stream) {
   const int G = 2 * N;
   if (N <= 0 || J <= 0 || J > 4096) return NLINV_EINVAL;
-  if (!supported_grid(G)) return NLINV_EUNSUPPORTED;
+  if (!supported_grid(G, N)) return NLINV_EUNSUPPORTED;
   if (Gc == 0) Gc = G / 4;
-  if (Gc < 2 || Gc > G || (Gc & 1)) return NLINV_EINVAL;
+  if (Gc < 2 || Gc > G) return NLINV_EINVAL;
   if (!(alpha >= 0.0) || !(w_a >= 0.0) || !(w_l >= 0.0)) return NLINV_EINVAL;
   if (!xhat || !dx || !psf || !out || !aligned8(xhat) || !aligned8(dx) || !aligned8(out) ||
       ((uintptr_t)psf & 3u))
@@ -797,7 +799,7 @@ extern "C" int nlinv_apply_normal_static(int N, int J, int Gc, double w_a, doubl
     CKL("k_static_tables");
     static_tables_written(G, Gc, w_a, w_l);
   }
-  return grid_ops(G)->normal(&tmp, st, (const float2*)xhat, (const float2*)dx, psf, alpha, (float2*)out, false);
+  return grid_ops(G, N)->normal(&tmp, st, (const float2*)xhat, (const float2*)dx, psf, alpha, (float2*)out, false);
 }
 
 // ======================================================================
@@ -1147,7 +1149,7 @@ extern "C" int nlinv_frame_vjp(nlinv_plan_t pl, const void* Y, int turn, const v
   GradWS w;
   RC(grad_workspace(pl, w));
   GradOps O{pl, (cudaStream_t)stream, pl->psf + (size_t)turn * pl->G * pl->G, pl->nx,
-            (long long)pl->J * pl->G * pl->G, w.part, w.dres, grid_ops(pl->G)};
+            (long long)pl->J * pl->G * pl->G, w.part, w.dres, grid_ops(pl->G, pl->N)};
   const long long nx = O.nx, nk = O.nk;
   const float2* Yd = (const float2*)Y;
   // x^_0 and x_ref
@@ -1279,12 +1281,12 @@ extern "C" int nlinv_frame_vjp(nlinv_plan_t pl, const void* Y, int turn, const v
 
 #ifdef NLINV_TIMELINE
 // profiling builds: the timeline and stage sums of grid size G's unit
-extern "C" int nlinv_debug_timeline(int G, unsigned long long* host, int n) {
-  const GridOps* o = grid_ops(G);
+extern "C" int nlinv_debug_timeline(int G, int N, unsigned long long* host, int n) {
+  const GridOps* o = grid_ops(G, N);
   return o ? o->timeline(host, n) : NLINV_EUNSUPPORTED;
 }
-extern "C" int nlinv_debug_stages(int G, unsigned long long* ns, unsigned long long* cnt) {
-  const GridOps* o = grid_ops(G);
+extern "C" int nlinv_debug_stages(int G, int N, unsigned long long* ns, unsigned long long* cnt) {
+  const GridOps* o = grid_ops(G, N);
   return o ? o->stages(ns, cnt) : NLINV_EUNSUPPORTED;
 }
 #endif

@@ -122,14 +122,21 @@ struct Ctx {
   int bid, nb;          // this CTA's index within the CTAs working on this frame, and their count
 };
 
-template <int G1_, int G2_> struct Cfg {
+// One compiled grid: G = G1 x G2 (the two register DFT lengths) and the
+// image side NR (the field of view, rows/cols [0, NR) of the G grid; G = 2 NR
+// unless a grid G = 2 gamma N of Eq. (8) is chosen).
+template <int G1_, int G2_, int NR_ = G1_ * G2_ / 2> struct Cfg {
   static constexpr int G1 = G1_, G2 = G2_;
   static constexpr int G = G1 * G2;
   static constexpr int MX = G1 > G2 ? G1 : G2;
   static constexpr int TW = NLINV_TW;       // columns per tile / rows per group
-  static constexpr int BS = TW * MX;        // threads per CTA
+  static constexpr int BS = (TW * MX + 31) / 32 * 32;   // threads per CTA (whole warps)
   static constexpr int RS = G + MX;         // smem stride of one row (float2)
-  static constexpr int NR = G / 2;          // image rows N (G = 2N)
+  static constexpr int NR = NR_;            // image rows N
+  // FOV pruning: an index a + G2 b (a < G2, b unrolled) lies in [0, NR) for
+  // every a when b < B2F, for some a when b < B2; likewise a + G1 b with B1F, B1
+  static constexpr int B2F = NR / G2, B2 = (NR + G2 - 1) / G2;
+  static constexpr int B1F = NR / G1, B1 = (NR + G1 - 1) / G1;
   static constexpr int SMEM_X = TW * RS * 8;  // exchange buffer bytes
   // CTAs per SM the persistent kernel is compiled for (caps registers)
 #ifdef NLINV_MINB
@@ -146,11 +153,20 @@ template <int G1_, int G2_> struct Cfg {
   static constexpr int NBUF = 1;
   static constexpr int SMEM = SMEM_X + NBUF * CT;  // dynamic smem bytes
   static_assert(SMEM <= SMEM_LIM, "staging buffer does not fit");
-  static_assert(TW % 4 == 0 && (G % 4) == 0, "16-byte staging chunks");
-  static_assert(G1 % 2 == 0 && G2 % 2 == 0, "G1, G2 must be even");
+  static_assert(TW % 4 == 0 && (G % 2) == 0, "16-byte staging chunks (even rows of float2)");
+  static_assert(2 * NR <= G, "the field of view is at most half the grid");
   // the block reductions use full-warp shuffles over blockDim / 32 warps
   static_assert(BS % 32 == 0, "threads per CTA must be a whole number of warps");
 };
+
+// a + G2 b < NR (b compile-time after unrolling: only the one ragged b tests a)
+template <class K> __device__ __forceinline__ bool in2(int b, int a) {
+  return b < K::B2F || (b < K::B2 && a + K::G2 * b < K::NR);
+}
+// a + G1 b < NR
+template <class K> __device__ __forceinline__ bool in1(int b, int a) {
+  return b < K::B1F || (b < K::B1 && a + K::G1 * b < K::NR);
+}
 
 __device__ __forceinline__ float2 ldcg(const float2* p) { return __ldcg(p); }
 
@@ -174,11 +190,12 @@ __device__ __forceinline__ float2 axpy2(float2 x, Scal2 s, float2 y) {
   return make_float2(fmaf(s.hi, x.x, fmaf(s.lo, x.x, y.x)), fmaf(s.hi, x.y, fmaf(s.lo, x.y, y.y)));
 }
 
-// index of grid position pos in the G_c coil band, -1 outside (Gc even)
+// index of grid position pos in the G_c coil band, -1 outside: the band
+// holds the (Gc + 1) / 2 frequencies 0, 1, ... and the Gc / 2 frequencies
+// -1, -2, ... (unshifted order; Gc odd or even)
 __device__ __forceinline__ int coef_index(int pos, int G, int Gc) {
-  const int h = Gc >> 1;
-  if (pos < h) return pos;
-  if (pos >= G - h) return pos - G + Gc;
+  if (pos < ((Gc + 1) >> 1)) return pos;
+  if (pos >= G - (Gc >> 1)) return pos - G + Gc;
   return -1;
 }
 
@@ -329,9 +346,9 @@ __device__ NLINV_PHASE void phase_coil_y(const Ctx& C, float2* sm, const float2*
         for (int n1 = 0; n1 < G1; ++n1) b[n1] = sm[(k2 * G1 + n1) * TW + cc];
         dft<G1, true>(b);
 #pragma unroll
-        for (int k1 = 0; k1 < G1 / 2; ++k1) {
+        for (int k1 = 0; k1 < K::B2; ++k1) {
           const int y = k2 + G2 * k1;
-          hout[((size_t)j * N + y) * Gc + fx] = cscale(b[k1], C.inv_G);
+          if (in2<K>(k1, k2)) hout[((size_t)j * N + y) * Gc + fx] = cscale(b[k1], C.inv_G);
         }
       }
     }
@@ -411,7 +428,7 @@ __device__ NLINV_PHASE void phase_row_b(const Ctx& C, float2* sm, int mode, cons
 #pragma unroll
       for (int k1 = 0; k1 < G1; ++k1) {
         u[k1] = czero();
-        if (k1 < G1 / 2) {
+        if (in2<K>(k1, k2)) {
           const int x = k2 + G2 * k1;
           const size_t ic = ((size_t)j * N + y) * N + x;
           const int ir = y * N + x;
@@ -485,11 +502,11 @@ __device__ NLINV_PHASE void phase_row_cg(const Ctx& C, float2* sm, float2* sred,
     // stage-2 operands (r_rho, c_j, rho rows) are requested with stage 1's
     const int rr = t / G2, k2 = t % G2, y = y0 + rr;
     const bool ok = rr < TW && y < N;
-    float2 rv[G1 / 2], cv[G1 / 2], rh[G1 / 2];
+    float2 rv[K::B2], cv[K::B2], rh[K::B2];
 #pragma unroll
-    for (int k1 = 0; k1 < G1 / 2; ++k1) {
+    for (int k1 = 0; k1 < K::B2; ++k1) {
       rv[k1] = cv[k1] = rh[k1] = czero();
-      if (ok) {
+      if (ok && in2<K>(k1, k2)) {
         const int ir = y * N + k2 + G2 * k1;
         rv[k1] = ldcg(rk + ir);
         cv[k1] = ldcg(C.c + (size_t)j * N * N + ir);
@@ -526,7 +543,9 @@ __device__ NLINV_PHASE void phase_row_cg(const Ctx& C, float2* sm, float2* sred,
       dft<G1, true>(b);
 #pragma unroll
       for (int k1 = 0; k1 < G1; ++k1)
-        u[k1] = (k1 < G1 / 2) ? cadd(cmul(cv[k1], rv[k1]), cmul(rh[k1], b[k1])) : czero();
+        u[k1] = (k1 < K::B2 && in2<K>(k1, k2))
+                    ? cadd(cmul(cv[k1 < K::B2 ? k1 : 0], rv[k1 < K::B2 ? k1 : 0]), cmul(rh[k1 < K::B2 ? k1 : 0], b[k1]))
+                    : czero();
       dft<G1, false>(u);
 #pragma unroll
       for (int kb = 1; kb < G1; ++kb) u[kb] = cmul(u[kb], twg<false>(C.tw, k2 * kb));
@@ -668,7 +687,7 @@ __device__ NLINV_PHASE void phase_col_cg(const Ctx& C, float2* sm, const float* 
 #pragma unroll
         for (int n2 = 0; n2 < G2; ++n2) {
           a[n2] = czero();
-          if (n2 < G2 / 2) {
+          if (in1<K>(n2, n1)) {
             const int y = n1 + G1 * n2;
             a[n2] = sv[y * TW + c];
             if (k > 0) a[n2] = axpy2(so[y * TW + c], beta, a[n2]);
@@ -715,7 +734,8 @@ __device__ NLINV_PHASE void phase_col_cg(const Ctx& C, float2* sm, const float* 
         for (int a2 = 0; a2 < G2; ++a2) d[a2] = sm[(m1 * G2 + a2) * TW + c];
         dft<G2, true>(d);
 #pragma unroll
-        for (int m2 = 0; m2 < G2 / 2; ++m2) vio[((size_t)j * NR + m1 + G1 * m2) * G + x0 + c] = d[m2];
+        for (int m2 = 0; m2 < K::B1; ++m2)
+          if (in1<K>(m2, m1)) vio[((size_t)j * NR + m1 + G1 * m2) * G + x0 + c] = d[m2];
       }
     }
     __syncthreads();
@@ -764,11 +784,12 @@ __device__ NLINV_PHASE void phase_col_c(const Ctx& C, float2* sm, int mode, cons
     if (mode != COL_INV) {  // stage 1: thread (n1, c): forward DFT over n2 (y = n1 + G1 n2 < N)
       const int n1 = t / TW;
       const bool ld = n1 < G1 && colok;
-      float2 a[G2], ao[G2 / 2];
+      float2 a[G2], ao[K::B1];
 #pragma unroll
       for (int n2 = 0; n2 < G2; ++n2) {
-        a[n2] = (ld && n2 < G2 / 2) ? ldcg(vio + ((size_t)j * N + n1 + G1 * n2) * G + x) : czero();
-        if (n2 < G2 / 2) ao[n2] = (ld && cg && k > 0) ? ldcg(C.vold + ((size_t)j * N + n1 + G1 * n2) * G + x) : czero();
+        const bool in = ld && in1<K>(n2, n1);
+        a[n2] = in ? ldcg(vio + ((size_t)j * N + n1 + G1 * n2) * G + x) : czero();
+        if (n2 < K::B1) ao[n2 < K::B1 ? n2 : 0] = (in && cg && k > 0) ? ldcg(C.vold + ((size_t)j * N + n1 + G1 * n2) * G + x) : czero();
       }
       if (need_beta) {   // CTA-uniform: first item of this CTA
         beta = cta_beta(C, k);
@@ -776,7 +797,8 @@ __device__ NLINV_PHASE void phase_col_c(const Ctx& C, float2* sm, int mode, cons
       }
       if (ld && cg) {
 #pragma unroll
-        for (int n2 = 0; n2 < G2 / 2; ++n2) {
+        for (int n2 = 0; n2 < K::B1; ++n2) {
+          if (!in1<K>(n2, n1)) continue;
           if (k > 0) a[n2] = axpy2(ao[n2], beta, a[n2]);
           C.vold[((size_t)j * N + n1 + G1 * n2) * G + x] = a[n2];
         }
@@ -843,7 +865,8 @@ __device__ NLINV_PHASE void phase_col_c(const Ctx& C, float2* sm, int mode, cons
         for (int a2 = 0; a2 < G2; ++a2) d[a2] = sm[(m1 * G2 + a2) * TW + (t % TW)];
         dft<G2, true>(d);
 #pragma unroll
-        for (int m2 = 0; m2 < G2 / 2; ++m2) vio[((size_t)j * N + m1 + G1 * m2) * G + x] = d[m2];
+        for (int m2 = 0; m2 < K::B1; ++m2)
+          if (in1<K>(m2, m1)) vio[((size_t)j * N + m1 + G1 * m2) * G + x] = d[m2];
       }
     }
     __syncthreads();
@@ -866,11 +889,11 @@ __device__ NLINV_PHASE void phase_row_d(const Ctx& C, float2* sm, const float2* 
     // stage-2 operands (c_j and rho rows) requested before stage 1 waits
     const int rr = t / G2, k2 = t % G2, y = y0 + rr;
     const bool ok = rr < TW && y < N;
-    float2 cv[G1 / 2], rh[G1 / 2];
+    float2 cv[K::B2], rh[K::B2];
 #pragma unroll
-    for (int k1 = 0; k1 < G1 / 2; ++k1) {
+    for (int k1 = 0; k1 < K::B2; ++k1) {
       cv[k1] = rh[k1] = czero();
-      if (ok) {
+      if (ok && in2<K>(k1, k2)) {
         const int ir = y * N + k2 + G2 * k1;
         cv[k1] = ldcg(C.c + (size_t)j * N * N + ir);
         rh[k1] = ldcg(rho + ir);
@@ -903,9 +926,10 @@ __device__ NLINV_PHASE void phase_row_d(const Ctx& C, float2* sm, const float2* 
 #pragma unroll
       for (int k1 = 0; k1 < G1; ++k1) {
         g[k1] = czero();
-        if (k1 < G1 / 2) {
-          sout[((size_t)j * N + y) * N + k2 + G2 * k1] = cconjmul(cv[k1], b[k1]);
-          g[k1] = cconjmul(rh[k1], b[k1]);
+        if (k1 < K::B2 && in2<K>(k1, k2)) {
+          const int kk = k1 < K::B2 ? k1 : 0;
+          sout[((size_t)j * N + y) * N + k2 + G2 * k1] = cconjmul(cv[kk], b[k1]);
+          g[k1] = cconjmul(rh[kk], b[k1]);
         }
       }
       dft<G1, false>(g);
@@ -971,8 +995,8 @@ __device__ NLINV_PHASE void phase_col_e(const Ctx& C, float2* sm, float2* sred, 
     float2 a[G2];
 #pragma unroll
     for (int n2 = 0; n2 < G2; ++n2)
-      a[n2] = (n1 < G1 && colok && n2 < G2 / 2) ? ldcg(kbin + ((size_t)j * N + n1 + G1 * n2) * Gc + fx)
-                                                 : czero();
+      a[n2] = (n1 < G1 && colok && in1<K>(n2, n1)) ? ldcg(kbin + ((size_t)j * N + n1 + G1 * n2) * Gc + fx)
+                                                    : czero();
     const int k2 = t / TW, cc = t % TW;
     const bool ok = k2 < G2 && colok;
     float2 o1[G1], o2[G1];
@@ -1058,8 +1082,8 @@ __device__ NLINV_PHASE void phase_col_e(const Ctx& C, float2* sm, float2* sred, 
           for (int a2 = 0; a2 < G2; ++a2) d[a2] = sm[(m1 * G2 + a2) * TW + (t % TW)];
           dft<G2, true>(d);
 #pragma unroll
-          for (int m2 = 0; m2 < G2 / 2; ++m2)
-            hout[((size_t)j * N + m1 + G1 * m2) * Gc + fx] = cscale(d[m2], C.inv_G);
+          for (int m2 = 0; m2 < K::B1; ++m2)
+            if (in1<K>(m2, m1)) hout[((size_t)j * N + m1 + G1 * m2) * Gc + fx] = cscale(d[m2], C.inv_G);
         }
       }
     }
@@ -1182,8 +1206,8 @@ __device__ NLINV_PHASE void phase_upd(const Ctx& C, float2* sm, float2* sred, in
       for (int q1 = 0; q1 < G1; ++q1) b[q1] = sm[(k2 * G1 + q1) * TW + cc];
       dft<G1, true>(b);
 #pragma unroll
-      for (int k1 = 0; k1 < G1 / 2; ++k1)
-        C.Hr[((size_t)j * N + k2 + G2 * k1) * Gc + fx] = cscale(b[k1], C.inv_G);
+      for (int k1 = 0; k1 < K::B2; ++k1)
+        if (in2<K>(k1, k2)) C.Hr[((size_t)j * N + k2 + G2 * k1) * Gc + fx] = cscale(b[k1], C.inv_G);
     }
     __syncthreads();
   }

@@ -41,7 +41,7 @@ class nlinv_params_t(ctypes.Structure):
         ("alpha0", ctypes.c_double), ("q", ctypes.c_double), ("damping", ctypes.c_double),
         ("w_a", ctypes.c_double), ("w_l", ctypes.c_double),
         ("spin_limit", ctypes.c_longlong), ("exec_mode", ctypes.c_int),
-        ("max_batch", ctypes.c_int),
+        ("max_batch", ctypes.c_int), ("G", ctypes.c_int),
     ]
 
 
@@ -181,7 +181,7 @@ class Plan:
 
 def nlinv_plan(params: nlinv_params_t, psf=None, stream=None) -> Plan:
     h = _VP()
-    G = 2 * params.N
+    G = params.G or 2 * params.N
     ptr = _ptr(psf, torch.float32, params.n_turns * G * G, "psf") if psf is not None else None
     _check(_lib().nlinv_plan(ctypes.byref(h), ctypes.byref(params), ptr, _stream(stream)),
            "nlinv_plan")

@@ -36,7 +36,7 @@ def make_plan(N, J, Gc=0, turns=1, psf=None, **kw):
 
 
 def geometry(plan):
-    return O.Geometry(N=plan.N, J=plan.J, Gc=plan.Gc)
+    return O.Geometry(N=plan.N, J=plan.J, Gc=plan.Gc, grid=plan.G)
 
 
 def random_xhat(g, seed, coil_scale=None):
@@ -47,6 +47,6 @@ def random_xhat(g, seed, coil_scale=None):
                   S.random_complex((g.J, g.gc, g.gc), seed + 1, cs))
 
 
-def radial_psf(N, K, U, turn):
+def radial_psf(N, K, U, turn, G=None):
     kx, ky = S.radial_trajectory(N, K, U, turn)
-    return O.psf_kernel(kx, ky, N, 2 * N).real, kx, ky
+    return O.psf_kernel(kx, ky, N, G or 2 * N).real, kx, ky
