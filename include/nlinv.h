@@ -85,8 +85,18 @@ typedef struct {
                          0 -> 1 (the plan allocates one workspace per frame) */
   int G;              /* grid side: 0 -> 2N (gamma = 1); else a grid G = 2 gamma N
                          of Eq. 8 (G >= 2N) among the compiled (G, N) pairs
-                         (NLINV_EUNSUPPORTED otherwise) */
+                         (nlinv_grid_list; NLINV_EUNSUPPORTED otherwise) */
+  int cluster_cs;     /* CTAs per channel cluster of the cluster kernel: 0 ->
+                         the largest size whose J clusters are co-resident;
+                         else exactly this size (exec_mode 3 then returns
+                         NLINV_EUNSUPPORTED when it does not fit, exec_mode 0
+                         falls back to the grid kernel) */
 } nlinv_params_t;
+
+/* The compiled grids: (G_out[i], N_out[i]) for i < the returned count (at
+ * most cap entries are written; either array may be NULL to count only).
+ * Host-only. */
+int nlinv_grid_list(int* G_out, int* N_out, int cap);
 
 /* Fill `p` with the defaults for an N x N image and J channels:
  * Gc = G/4, 7 Newton steps x 10 CG, alpha0 = 1, q = 1/2, damping 1,

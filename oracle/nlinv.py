@@ -390,3 +390,63 @@ def grid_data(kx: np.ndarray, ky: np.ndarray, y: np.ndarray, N: int, G: int) -> 
     """Gridded data on the G grid with crop U^H Y_j = A^H y_j exactly:
     Y_j = U pad(A^H y_j)."""
     return fft2u(pad_img(ndft_adjoint(kx, ky, y, N, G), G))
+
+
+# ---------------------------------------------------------------------------
+# gridding by convolution (preprocessing stage, Sec. 3.1): the non-uniform
+# adjoint A^H y evaluated with a Kaiser-Bessel kernel on the G grid
+# ---------------------------------------------------------------------------
+
+def kb_beta(W: int, sigma: float = 2.0) -> float:
+    """Kaiser-Bessel shape for a kernel of W grid points on a grid
+    oversampled by sigma (the common choice of the gridding literature:
+    beta = pi sqrt((W/sigma)^2 (sigma - 1/2)^2 - 0.8))."""
+    return float(np.pi * np.sqrt((W / sigma) ** 2 * (sigma - 0.5) ** 2 - 0.8))
+
+
+def kb_kernel(u: np.ndarray, W: int, beta: float) -> np.ndarray:
+    """phi(u) = I0(beta sqrt(1 - (2u/W)^2)) for |u| <= W/2 (u in grid points),
+    else 0."""
+    u = np.asarray(u, dtype=np.float64)
+    a = 1.0 - (2.0 * u / W) ** 2
+    return np.where(a >= 0.0, np.i0(beta * np.sqrt(np.clip(a, 0.0, None))), 0.0)
+
+
+def kb_ft(t: np.ndarray, W: int, beta: float) -> np.ndarray:
+    """Continuous Fourier transform of kb_kernel, int phi(u) e^{2 pi i u t} du =
+    W sinh(s)/s with s = sqrt(beta^2 - (pi W t)^2) (t in cycles per grid
+    point, |pi W t| < beta)."""
+    s = np.sqrt(beta ** 2 - (np.pi * W * np.asarray(t, dtype=np.float64)) ** 2)
+    return W * np.sinh(s) / s
+
+
+def grid_data_kb(kx: np.ndarray, ky: np.ndarray, y: np.ndarray, N: int, G: int, W: int = 6) -> np.ndarray:
+    """Gridded data Y_j = U pad(A^H y_j) with A^H y by convolution gridding.
+    The field of view [0, N)^2 has its centre at c = N/2; relative to it the
+    image spans at most N/2 <= G/4 in each direction, where the periodic
+    copies of the kernel's transform are negligible.
+    (1) Each sample y_s is spread onto the W x W grid points f nearest to
+        its position p_s = G k_s (periodic on the G grid) with the weight
+        phi(u) exp(-2 pi i u.c / G), u = f - p_s (the kernel modulated by the
+        centre, so that the transform below is centred on c);
+    (2) z(r) = sum_f Z_f e^{2 pi i f.r/G} = G crop_N U^H Z, which equals
+        sum_s y_s e^{2 pi i k_s.r} Phi((rx - cx)/G) Phi((ry - cy)/G) up to the
+        kernel's aliases, Phi = kb_ft the continuous transform of phi;
+    (3) A^H y = z / ((2N) Phi Phi) (deapodisation);
+    (4) Y = U pad(A^H y).
+    The error against the exact adjoint NDFT falls with the kernel width W."""
+    beta = kb_beta(W, G / N)
+    J = y.shape[0]
+    c = N / 2.0
+    Z = np.zeros((J, G, G), np.complex128)
+    for s in range(len(kx)):
+        px, py = G * kx[s], G * ky[s]
+        fx = np.floor(px - W / 2.0).astype(int) + 1 + np.arange(W)   # the W points with |f - p| < W/2
+        fy = np.floor(py - W / 2.0).astype(int) + 1 + np.arange(W)
+        wx = kb_kernel(fx - px, W, beta) * np.exp(-2j * np.pi * (fx - px) * c / G)
+        wy = kb_kernel(fy - py, W, beta) * np.exp(-2j * np.pi * (fy - py) * c / G)
+        Z[:, (fy % G)[:, None], (fx % G)[None, :]] += y[:, s, None, None] * (wy[:, None] * wx[None, :])[None]
+    z = G * crop_img(ifft2u(Z), N)
+    dap = kb_ft((np.arange(N, dtype=np.float64) - c) / G, W, beta)
+    img = z / (2 * N * dap[:, None] * dap[None, :])[None]
+    return fft2u(pad_img(img, G))

@@ -420,13 +420,12 @@ cudaLaunchConfig_t cluster_config(const nlinv_plan_s* pl, int CS, int bs, int sm
 }
 
 // The largest cluster size (CTAs per channel) whose layout fits the shared
-// memory of one CTA and whose J clusters are co-resident, or none (cl_cs = 0).
-// NLINV_CLUSTER_CS in the environment restricts the choice to that size.
+// memory of one CTA and whose J clusters are co-resident, or none (cl_cs = 0);
+// the plan's cluster_cs, when set, is the only size tried.
 template <class K>
 int pick_cluster(nlinv_plan_s* pl) {
   static const int cand[] = {16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2, 1};
-  int only = 0;
-  if (const char* e = std::getenv("NLINV_CLUSTER_CS")) only = std::atoi(e);
+  const int only = pl->prm.cluster_cs;
   int optin = 0;
   CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pl->dev));
   // one attribute value for every plan of this grid size: the largest

@@ -160,6 +160,19 @@ const char* nlinv_strerror(int code) {
 
 const char* nlinv_last_cuda_error(void) { return g_cuda_err; }
 
+int nlinv_grid_list(int* G_out, int* N_out, int cap) {
+  int n = 0;
+#define NLINV_LIST_GRID(a, b, nr)                   \
+  if (grid_ops_##a##_##b##_##nr) {                  \
+    if (n < cap && G_out) G_out[n] = (a) * (b);     \
+    if (n < cap && N_out) N_out[n] = (nr);          \
+    ++n;                                            \
+  }
+  NLINV_GRIDS(NLINV_LIST_GRID)
+#undef NLINV_LIST_GRID
+  return n;
+}
+
 int nlinv_default_params(nlinv_params_t* p, int N, int J) {
   if (!p || N <= 0 || J <= 0) return NLINV_EINVAL;
   std::memset(p, 0, sizeof(*p));
@@ -178,6 +191,7 @@ int nlinv_default_params(nlinv_params_t* p, int N, int J) {
   p->exec_mode = 0;
   p->max_batch = 1;
   p->G = 0;
+  p->cluster_cs = 0;
   return NLINV_OK;
 }
 
@@ -197,6 +211,7 @@ int nlinv_plan(nlinv_plan_t* out, const nlinv_params_t* p, const float* psf, nli
   if (!(p->w_a >= 0.0) || !(p->w_l >= 0.0)) return NLINV_EINVAL;
   if (p->exec_mode < 0 || p->exec_mode > 3) return NLINV_EINVAL;
   if (p->max_batch < 0 || p->max_batch > kMaxBatch) return NLINV_EINVAL;
+  if (p->cluster_cs < 0 || p->cluster_cs > 16) return NLINV_EINVAL;
   if (psf && ((uintptr_t)psf & 3u)) return NLINV_EINVAL;
 
   cudaStream_t st = (cudaStream_t)stream;

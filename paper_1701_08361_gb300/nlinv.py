@@ -41,7 +41,7 @@ class nlinv_params_t(ctypes.Structure):
         ("alpha0", ctypes.c_double), ("q", ctypes.c_double), ("damping", ctypes.c_double),
         ("w_a", ctypes.c_double), ("w_l", ctypes.c_double),
         ("spin_limit", ctypes.c_longlong), ("exec_mode", ctypes.c_int),
-        ("max_batch", ctypes.c_int), ("G", ctypes.c_int),
+        ("max_batch", ctypes.c_int), ("G", ctypes.c_int), ("cluster_cs", ctypes.c_int),
     ]
 
 
@@ -69,6 +69,7 @@ _I = ctypes.c_int
 
 _SIGS = {
     "nlinv_default_params": (_I, [ctypes.POINTER(nlinv_params_t), _I, _I]),
+    "nlinv_grid_list": (_I, [_VP, _VP, _I]),
     "nlinv_plan": (_I, [ctypes.POINTER(_VP), ctypes.POINTER(nlinv_params_t), _VP, _VP]),
     "nlinv_plan_destroy": (_I, [_VP]),
     "nlinv_plan_sizes": (_I, [_VP, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_I),
@@ -147,6 +148,14 @@ def _ptr(t, dtype=torch.complex64, numel=None, name="tensor"):
 
 def nlinv_strerror(code: int) -> str:
     return _lib().nlinv_strerror(code).decode()
+
+
+def nlinv_grid_list():
+    """The compiled grids as a list of (G, N) pairs."""
+    n = _lib().nlinv_grid_list(None, None, 0)
+    G, N = (ctypes.c_int * n)(), (ctypes.c_int * n)()
+    _lib().nlinv_grid_list(G, N, n)
+    return list(zip(list(G), list(N)))
 
 
 def nlinv_default_params(N: int, J: int) -> nlinv_params_t:

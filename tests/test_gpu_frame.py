@@ -161,14 +161,12 @@ def test_degenerate_iteration_counts(M, K, mode):
 
 @pytest.mark.parametrize("N,J,Gc,cs", [(160, 10, 0, 0), (64, 4, 0, 0), (20, 3, 0, 0), (32, 4, 16, 0),
                                        (128, 8, 0, 8), (128, 8, 0, 0), (64, 4, 0, 6)])
-def test_cluster_kernel_matches_oracle_and_grid_kernel(N, J, Gc, cs, monkeypatch):
+def test_cluster_kernel_matches_oracle_and_grid_kernel(N, J, Gc, cs):
     """The cluster-resident frame kernel (one cluster per channel; ragged
     partitions of rows, columns and coil columns for most sizes) against the
     FP64 oracle and against the grid kernel, on a radial frame from the
     initial value (3 Newton x 5 CG)."""
     from paper_1701_08361_gb300 import nlinv as L
-    if cs:
-        monkeypatch.setenv("NLINV_CLUSTER_CS", str(cs))
     K, U = 13, 5
     P, kx, ky = radial_psf(N, K, U, 1)
     g = O.Geometry(N=N, J=J, Gc=Gc or None)
@@ -179,7 +177,10 @@ def test_cluster_kernel_matches_oracle_and_grid_kernel(N, J, Gc, cs, monkeypatch
     ref = O.nlinv_frame(Y, P, O.XVec.initial(g), O.XVec.initial(g), g, prm)
     xs = []
     for mode in (3, 2):
-        plan = make_plan(N, J, Gc, psf=P, newton_steps=3, cg_iters=5, exec_mode=mode)
+        plan = make_plan(N, J, Gc, psf=P, newton_steps=3, cg_iters=5, exec_mode=mode,
+                         cluster_cs=cs if mode == 3 else 0)
+        if mode == 3:
+            assert L.nlinv_plan_path(plan)[0] == 3 and (cs == 0 or L.nlinv_plan_path(plan)[1] == cs)
         (x, rho, img), = run_frames(plan, [(Y, 0)])
         e = rel(x, ref.flat())
         print(f"N={N} J={J} mode {mode}: rel L2 vs FP64 {e:.2e}")
