@@ -69,8 +69,10 @@ typedef struct {
   double w_a, w_l;    /* Sobolev weight constants (220, 32) */
   long long spin_limit; /* polls before a device-side wait gives up; 0 -> default */
   int exec_mode;      /* how nlinv_frame runs a frame:
-                         0: automatic -- the cluster kernel when the plan's
-                            channels fit it (3), else the grid kernel (2);
+                         0: default -- the grid kernel (2), which measured
+                            faster than the cluster kernel (3) on the
+                            configurations' sizes; the tuner (tune.py)
+                            records which is faster per size;
                          1: one launch per phase (unfused comparator);
                          2: one persistent cooperative launch, CTAs
                             synchronised by grid barriers between phases;
@@ -86,11 +88,10 @@ typedef struct {
   int G;              /* grid side: 0 -> 2N (gamma = 1); else a grid G = 2 gamma N
                          of Eq. 8 (G >= 2N) among the compiled (G, N) pairs
                          (nlinv_grid_list; NLINV_EUNSUPPORTED otherwise) */
-  int cluster_cs;     /* CTAs per channel cluster of the cluster kernel: 0 ->
-                         the largest size whose J clusters are co-resident;
-                         else exactly this size (exec_mode 3 then returns
-                         NLINV_EUNSUPPORTED when it does not fit, exec_mode 0
-                         falls back to the grid kernel) */
+  int cluster_cs;     /* CTAs per channel cluster of the cluster kernel
+                         (exec_mode 3): 0 -> the largest size whose J
+                         clusters are co-resident; else exactly this size
+                         (NLINV_EUNSUPPORTED when it does not fit) */
 } nlinv_params_t;
 
 /* The compiled grids: (G_out[i], N_out[i]) for i < the returned count (at
@@ -140,6 +141,22 @@ int nlinv_psf(nlinv_plan_t plan, int turn, int S, const double* kxy, float* P_ou
  * Y_out: device complex64 [J][G][G].  Uses the plan's workspace. */
 int nlinv_grid(nlinv_plan_t plan, int S, const double* kxy, const void* y, void* Y_out,
                nlinv_stream_t stream);
+
+/* Gridding by convolution (the preprocessing stage of Sec. 3.1 as a
+ * non-uniform FFT): the same Y_j = U pad(A^H y_j) as nlinv_grid, with A^H y
+ * evaluated by spreading each sample onto the W x W grid points nearest to
+ * G k_s with a Kaiser-Bessel kernel phi(u) = I0(beta sqrt(1 - (2u/W)^2)),
+ * beta = pi sqrt((W/sigma)^2 (sigma - 1/2)^2 - 0.8), sigma = G/N, modulated by
+ * the centre N/2 of the field of view; an inverse FFT of the grid; division by
+ * the kernel's continuous transform (deapodisation) on the field of view.
+ * The relative error against nlinv_grid falls geometrically with W (about
+ * 7e-6 at W = 6 and 6e-8 at W = 8 for sigma = 2, in exact arithmetic).
+ * kxy: device double [S][2]; y: device complex64 [J][S]; W: 2..16;
+ * Y_out: device complex64 [J][G][G].  Uses the plan's workspace (J G^2
+ * complex values for the spread grid); float atomics make the summation
+ * order, and so the last bits, vary between runs. */
+int nlinv_grid_nufft(nlinv_plan_t plan, int S, const double* kxy, const void* y, int W, void* Y_out,
+                     nlinv_stream_t stream);
 
 /* DF at x^_n applied to dx (Eq. 5 before the PSF):
  *   z_j = U pad_N(c_j drho + rho W^-1 dc^_j),  c_j = W^-1 c^_j of x^_n.

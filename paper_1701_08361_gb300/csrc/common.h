@@ -150,6 +150,10 @@ struct GridOps {
                 double alpha, float2* out, bool coils_ready);
   // Y = U pad(img), img [J][N][N] in the plan's s buffer (gridding's last step)
   int (*grid_fwd)(const nlinv_plan_s* pl, cudaStream_t st, float2* Y);
+  // convolution gridding after the spreading: Y = U pad(scale dap dap crop U^H Z),
+  // Z [J][G][G] the spread grid, dap [N] the per-axis deapodisation
+  int (*grid_kb)(const nlinv_plan_s* pl, cudaStream_t st, const float2* Z, const float* dap, float scale,
+                 float2* Y);
   // one whole frame on the plan's execution path
   int (*frame)(const nlinv_plan_s* pl, cudaStream_t st, const FrameArgs& F);
   // frames of one plan in one cooperative launch of `grid` CTAs

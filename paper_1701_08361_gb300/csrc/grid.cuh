@@ -52,6 +52,13 @@ __global__ void __launch_bounds__(K::BS) k_row_b(Ctx C0, int mode, const float2*
 }
 
 template <class K>
+__global__ void __launch_bounds__(K::BS) k_row_deapod(Ctx C0, const float* dap, float scale, float2* v) {
+  const Ctx C = whole_grid(C0);
+  extern __shared__ float2 sm[];
+  phase_row_deapod<K>(C, sm, dap, scale, v);
+}
+
+template <class K>
 __global__ void __launch_bounds__(K::BS) k_col_c(Ctx C0, int mode, const float* P, const float2* Yin,
                                                  float2* zout, float2* vio, int k) {
   const Ctx C = whole_grid(C0);
@@ -388,6 +395,7 @@ int set_smem_attrs() {
   if (K::SMEM > 48 * 1024) {
     CK(cudaFuncSetAttribute(k_coil_y<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(k_row_b<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
+    CK(cudaFuncSetAttribute(k_row_deapod<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(k_col_c<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(k_row_d<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(k_col_e<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
@@ -484,6 +492,13 @@ struct Launch {
     CKL("k_row_b");
     return NLINV_OK;
   }
+  int row_deapod(const float* dap, float scale, float2* v) const {
+    const Ctx& C = pl->C;
+    const int g = plan_grid(C.J * ((C.N + K::TW - 1) / K::TW), 1);
+    k_row_deapod<K><<<pick(g), K::BS, K::SMEM, st>>>(C, dap, scale, v);
+    CKL("k_row_deapod");
+    return NLINV_OK;
+  }
   int col_c(int mode, const float* P, const float2* Yin, float2* zout, float2* vio, int k = 0) const {
     const Ctx& C = pl->C;
     const int g = plan_grid(C.J * ((C.G + K::TW - 1) / K::TW), 1);
@@ -569,9 +584,10 @@ struct Ops {
     int nbb = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nbb, k_batch<K>, K::BS, K::SMEM));
     pl->batch_occ = nbb;
-    const int m = pl->prm.exec_mode;
-    if (m == 0 || m == 3) RC(pick_cluster<K>(pl));
-    if (m == 3 && pl->cl_cs == 0) return NLINV_EUNSUPPORTED;
+    if (pl->prm.exec_mode == 3) {
+      RC(pick_cluster<K>(pl));
+      if (pl->cl_cs == 0) return NLINV_EUNSUPPORTED;
+    }
     return (g > 0 && nbb > 0) ? NLINV_OK : NLINV_ECUDA;
   }
 
@@ -617,11 +633,19 @@ struct Ops {
     return L.col_c(COL_FWD, nullptr, nullptr, Y, pl->C.v);
   }
 
+  static int grid_kb(const nlinv_plan_s* pl, cudaStream_t st, const float2* Z, const float* dap, float scale,
+                     float2* Y) {
+    Launch<K> L{pl, st};
+    RC(L.col_c(COL_INV, nullptr, Z, nullptr, pl->C.v));
+    RC(L.row_deapod(dap, scale, pl->C.v));
+    return L.col_c(COL_FWD, nullptr, nullptr, Y, pl->C.v);
+  }
+
   static int frame(const nlinv_plan_s* pl, cudaStream_t st, const FrameArgs& F) {
     const int mode = pl->prm.exec_mode;
     Ctx C = pl->C;
     const int NN = pl->N * pl->N;
-    if ((mode == 0 || mode == 3) && pl->cl_cs > 0) {
+    if (mode == 3 && pl->cl_cs > 0) {
       CK(cudaMemsetAsync(C.bar, 0, 2 * sizeof(unsigned), st));
       cudaLaunchAttribute at[2];
       cudaLaunchConfig_t cfg = cluster_config(pl, pl->cl_cs, K::BS, pl->cl_lay.smem_bytes, at, st);
@@ -676,7 +700,7 @@ struct Ops {
 template <class K>
 const GridOps* make_ops() {
   static const GridOps ops = {K::G, K::NR, &Ops<K>::setup, &Ops<K>::prepare, &Ops<K>::coils, &Ops<K>::DF,
-                              &Ops<K>::DFH, &Ops<K>::normal, &Ops<K>::grid_fwd, &Ops<K>::frame, &Ops<K>::batch
+                              &Ops<K>::DFH, &Ops<K>::normal, &Ops<K>::grid_fwd, &Ops<K>::grid_kb, &Ops<K>::frame, &Ops<K>::batch
 #ifdef NLINV_TIMELINE
                               , &read_timeline, &read_stages
 #endif

@@ -41,6 +41,70 @@ const GridOps* grid_ops(int G, int N) {
 
 namespace {
 
+// ------------------------------------------- convolution gridding (NUFFT)
+// Kaiser-Bessel gridding of the preprocessing stage (Sec. 3.1): kernel
+// phi(u) = I0(beta sqrt(1 - (2u/W)^2)) on W grid points, modulated by the
+// centre c = N/2 of the field of view; continuous transform
+// Phi(t) = W sinh(s)/s, s = sqrt(beta^2 - (pi W t)^2).
+constexpr int kMaxKbWidth = 16;
+
+double kb_beta(int W, double sigma) {
+  return M_PI * std::sqrt((W / sigma) * (W / sigma) * (sigma - 0.5) * (sigma - 0.5) - 0.8);
+}
+
+// per sample and axis: the first grid point f0 of the W nearest to p = G k
+// and the W complex weights phi(f - p) exp(-2 pi i (f - p) c / G) (FP64)
+__global__ void k_kb_weights(int S, int G, int W, double beta, double c, const double* __restrict__ kxy, float2* w,
+                             int* f0) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S) return;
+#pragma unroll 1
+  for (int ax = 0; ax < 2; ++ax) {
+    const double p = G * kxy[2 * s + ax];
+    const int f = (int)floor(p - 0.5 * W) + 1;
+    f0[2 * s + ax] = f;
+    for (int i = 0; i < W; ++i) {
+      const double u = f + i - p;
+      const double a = 1.0 - (2.0 * u / W) * (2.0 * u / W);
+      const double ph = a >= 0.0 ? cyl_bessel_i0(beta * sqrt(a)) : 0.0;
+      double sn, cs;
+      sincospi(-2.0 * u * c / G, &sn, &cs);
+      w[((size_t)s * 2 + ax) * W + i] = make_float2((float)(ph * cs), (float)(ph * sn));
+    }
+  }
+}
+
+// dap[i] = 1 / Phi((i - N/2) / G)  (FP64)
+__global__ void k_kb_deapod(int N, int G, int W, double beta, float* dap) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double t = (i - 0.5 * N) / G;
+  const double sarg = sqrt(beta * beta - (M_PI * W * t) * (M_PI * W * t));
+  dap[i] = (float)(sarg / (W * sinh(sarg)));
+}
+
+// Z[j][fy][fx] += y[j][s] wy wx over the W x W points of sample s (periodic);
+// one thread per (sample, channel), float2 atomics in global memory
+__global__ void k_kb_spread(int S, int J, int G, int W, const float2* __restrict__ y, const float2* __restrict__ w,
+                            const int* __restrict__ f0, float2* Z) {
+  const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= (long long)S * J) return;
+  const int s = (int)(id % S), j = (int)(id / S);
+  const float2 yv = y[(size_t)j * S + s];
+  const float2* wx = w + (size_t)s * 2 * W;
+  const float2* wy = wx + W;
+  const int fx0 = f0[2 * s], fy0 = f0[2 * s + 1];
+  float2* Zj = Z + (size_t)j * G * G;
+  for (int a = 0; a < W; ++a) {
+    const int fy = ((fy0 + a) % G + G) % G;
+    const float2 ya = cmul(yv, wy[a]);
+    for (int b = 0; b < W; ++b) {
+      const int fx = ((fx0 + b) % G + G) % G;
+      atomicAdd(Zj + (size_t)fy * G + fx, cmul(ya, wx[b]));
+    }
+  }
+}
+
 bool supported_grid(int G, int N) { return grid_ops(G, N) != nullptr; }
 
 bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
@@ -373,7 +437,7 @@ int nlinv_plan_sizes(nlinv_plan_t pl, long long* nx, int* G, int* Gc) {
 int nlinv_plan_path(nlinv_plan_t pl, int* exec_path, int* cluster_size) {
   RC(check_plan(pl));
   const int m = pl->prm.exec_mode;
-  const int path = m == 1 ? 1 : ((m == 0 || m == 3) && pl->cl_cs > 0 ? 3 : 2);
+  const int path = m == 1 ? 1 : (m == 3 && pl->cl_cs > 0 ? 3 : 2);
   if (exec_path) *exec_path = path;
   if (cluster_size) *cluster_size = path == 3 ? pl->cl_cs : 0;
   return NLINV_OK;
@@ -435,6 +499,35 @@ int nlinv_grid(nlinv_plan_t pl, int S, const double* kxy, const void* y, void* Y
       N, S, (const float2*)y, Ex, Ey, pl->C.s, (float)(0.5 / pl->N));
   CKL("k_adj_ndft");
   return grid_ops(pl->G, pl->N)->grid_fwd(pl, st, (float2*)Y_out);
+}
+
+int nlinv_grid_nufft(nlinv_plan_t pl, int S, const double* kxy, const void* y, int W, void* Y_out,
+                     nlinv_stream_t stream) {
+  RC(check_plan(pl));
+  if (S <= 0 || !kxy || !y || !Y_out || ((uintptr_t)kxy & 7u) || !aligned8(y) || !aligned8(Y_out))
+    return NLINV_EINVAL;
+  if (W < 2 || W > kMaxKbWidth) return NLINV_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int N = pl->N, G = pl->G, J = pl->J;
+  const size_t zb = align_up((size_t)J * G * G * sizeof(float2));
+  const size_t wb = align_up((size_t)S * 2 * W * sizeof(float2));
+  const size_t bb = align_up((size_t)S * 2 * sizeof(int));
+  RC(ensure_prep(pl, zb + wb + bb + align_up((size_t)N * sizeof(float))));
+  char* base = (char*)pl->prep;
+  float2* Z = (float2*)base;
+  float2* w = (float2*)(base + zb);
+  int* f0 = (int*)(base + zb + wb);
+  float* dap = (float*)(base + zb + wb + bb);
+  const double beta = kb_beta(W, (double)G / N);
+  CK(cudaMemsetAsync(Z, 0, (size_t)J * G * G * sizeof(float2), st));
+  k_kb_weights<<<(S + 127) / 128, 128, 0, st>>>(S, G, W, beta, 0.5 * N, kxy, w, f0);
+  CKL("k_kb_weights");
+  k_kb_deapod<<<(N + 127) / 128, 128, 0, st>>>(N, G, W, beta, dap);
+  CKL("k_kb_deapod");
+  const long long nt = (long long)S * J;
+  k_kb_spread<<<(int)((nt + 255) / 256), 256, 0, st>>>(S, J, G, W, (const float2*)y, w, f0, Z);
+  CKL("k_kb_spread");
+  return grid_ops(pl->G, pl->N)->grid_kb(pl, st, Z, dap, (float)((double)G / (2.0 * N)), (float2*)Y_out);
 }
 
 int nlinv_apply_DF(nlinv_plan_t pl, const void* xhat, const void* dx, void* z, nlinv_stream_t stream) {

@@ -38,9 +38,6 @@
 #pragma once
 #include "fft.cuh"
 
-#ifndef NLINV_TW
-#define NLINV_TW 16
-#endif
 // phases are inlined into the persistent kernel unless NLINV_NOINLINE_PHASES
 // is defined (separate functions get their own register allocation but cost
 // more than they save here)
@@ -122,6 +119,21 @@ struct Ctx {
   int bid, nb;          // this CTA's index within the CTAs working on this frame, and their count
 };
 
+// Tile width (columns of a column item, rows of a row item): the widest
+// multiple of 4 (at most 16) whose CTA of TW x max(G1, G2) threads stays
+// within 256 threads, i.e. 8 warps, 2 per scheduler, so that a thread may
+// hold up to 255 registers: the register DFTs of a CTA with 10 or more warps
+// are capped at 168 registers and spill (measured on the 320 grid: 12
+// columns and 256 threads 3.44 ms per frame, 16 columns and 320 threads
+// 3.84 ms).  NLINV_TW overrides it (experiments).
+constexpr int default_tw(int mx) {
+#ifdef NLINV_TW
+  return NLINV_TW + 0 * mx;
+#else
+  return (256 / mx) / 4 * 4 > 16 ? 16 : ((256 / mx) / 4 * 4 < 4 ? 4 : (256 / mx) / 4 * 4);
+#endif
+}
+
 // One compiled grid: G = G1 x G2 (the two register DFT lengths) and the
 // image side NR (the field of view, rows/cols [0, NR) of the G grid; G = 2 NR
 // unless a grid G = 2 gamma N of Eq. (8) is chosen).
@@ -129,7 +141,7 @@ template <int G1_, int G2_, int NR_ = G1_ * G2_ / 2> struct Cfg {
   static constexpr int G1 = G1_, G2 = G2_;
   static constexpr int G = G1 * G2;
   static constexpr int MX = G1 > G2 ? G1 : G2;
-  static constexpr int TW = NLINV_TW;       // columns per tile / rows per group
+  static constexpr int TW = default_tw(MX);   // columns per tile / rows per group
   static constexpr int BS = (TW * MX + 31) / 32 * 32;   // threads per CTA (whole warps)
   static constexpr int RS = G + MX;         // smem stride of one row (float2)
   static constexpr int NR = NR_;            // image rows N
@@ -142,7 +154,7 @@ template <int G1_, int G2_, int NR_ = G1_ * G2_ / 2> struct Cfg {
 #ifdef NLINV_MINB
   static constexpr int MINB = NLINV_MINB;
 #else
-  static constexpr int MINB = BS <= 256 ? 2 : 1;
+  static constexpr int MINB = BS <= 128 ? 2 : 1;
 #endif
   // staged operands of one column item of the CG column pass: T(r_k) and
   // T(p_{k-1}) tiles [N][TW] (and the PSF tile [G][TW] if staged).  One staging buffer:
@@ -468,6 +480,78 @@ __device__ NLINV_PHASE void phase_row_b(const Ctx& C, float2* sm, int mode, cons
         for (int a2 = 0; a2 < G2; ++a2) d[a2] = sm[r3 * RS + kb * (G2 + 1) + a2];
         dft<G2, false>(d);
         float2* dst = vout + ((size_t)j * N + y3) * G;
+#pragma unroll
+        for (int ka = 0; ka < G2; ++ka) dst[kb + G1 * ka] = d[ka];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------ row pass of the convolution gridding (Sec. 3.1)
+// The spread grid after the column pass COL_INV holds, per row y < N, the
+// inverse transform along y; here: inverse DFT along x (keep x < N), times
+// scale * dap[x] * dap[y] (the deapodisation), forward DFT of the zero-padded
+// row, all G outputs back into the same row of v.
+template <class K>
+__device__ NLINV_PHASE void phase_row_deapod(const Ctx& C, float2* sm, const float* dap, float scale, float2* v) {
+  constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW, RS = K::RS;
+  const int N = C.N, J = C.J;
+  const int t = phase_tid();
+  const int groups = (N + TW - 1) / TW;
+  const int items = J * groups;
+  for (int it = C.bid; it < items; it += C.nb) {
+    const int j = it / groups;
+    const int y0 = (it - j * groups) * TW;
+    {  // stage 1: thread (row, n1): inverse DFT over n2 of the whole row
+      const int r1 = t / G1, n1 = t % G1, y1 = y0 + r1;
+      if (r1 < TW && y1 < N) {
+        float2 a[G2];
+        const float2* src = v + ((size_t)j * N + y1) * G;
+#pragma unroll
+        for (int n2 = 0; n2 < G2; ++n2) a[n2] = ldcg(src + n1 + G1 * n2);
+        dft<G2, true>(a);
+#pragma unroll
+        for (int q2 = 0; q2 < G2; ++q2) {
+          float2 x = a[q2];
+          if (q2) x = cmul(x, twg<true>(C.tw, n1 * q2));
+          sm[r1 * RS + q2 * (G1 + 1) + n1] = x;
+        }
+      }
+    }
+    __syncthreads();
+    // stage 2: thread (row, k2): inverse DFT over n1 -> x = k2 + G2 k1 (< N),
+    // deapodisation, forward DFT over k1 of the padded row
+    const int rr = t / G2, k2 = t % G2, y = y0 + rr;
+    const bool ok = rr < TW && y < N;
+    float2 u[G1];
+    if (ok) {
+      float2 b[G1];
+#pragma unroll
+      for (int q1 = 0; q1 < G1; ++q1) b[q1] = sm[rr * RS + k2 * (G1 + 1) + q1];
+      dft<G1, true>(b);
+      const float wy = scale * __ldg(dap + y);
+#pragma unroll
+      for (int k1 = 0; k1 < G1; ++k1)
+        u[k1] = in2<K>(k1, k2) ? cscale(b[k1], wy * __ldg(dap + k2 + G2 * k1)) : czero();
+      dft<G1, false>(u);
+#pragma unroll
+      for (int kb = 1; kb < G1; ++kb) u[kb] = cmul(u[kb], twg<false>(C.tw, k2 * kb));
+    }
+    __syncthreads();
+    if (ok) {
+#pragma unroll
+      for (int kb = 0; kb < G1; ++kb) sm[rr * RS + kb * (G2 + 1) + k2] = u[kb];
+    }
+    __syncthreads();
+    {  // stage 3: thread (row, kb): forward DFT over k2 -> kb + G1 ka
+      const int r3 = t / G1, kb = t % G1, y3 = y0 + r3;
+      if (r3 < TW && y3 < N) {
+        float2 d[G2];
+#pragma unroll
+        for (int a2 = 0; a2 < G2; ++a2) d[a2] = sm[r3 * RS + kb * (G2 + 1) + a2];
+        dft<G2, false>(d);
+        float2* dst = v + ((size_t)j * N + y3) * G;
 #pragma unroll
         for (int ka = 0; ka < G2; ++ka) dst[kb + G1 * ka] = d[ka];
       }

@@ -78,6 +78,7 @@ _SIGS = {
     "nlinv_plan_path": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "nlinv_psf": (_I, [_VP, _I, _I, _VP, _VP, _VP]),
     "nlinv_grid": (_I, [_VP, _I, _VP, _VP, _VP, _VP]),
+    "nlinv_grid_nufft": (_I, [_VP, _I, _VP, _VP, _I, _VP, _VP]),
     "nlinv_apply_DF": (_I, [_VP, _VP, _VP, _VP, _VP]),
     "nlinv_apply_DFH": (_I, [_VP, _VP, _VP, _VP, _VP]),
     "nlinv_apply_normal": (_I, [_VP, _VP, _VP, _I, ctypes.c_double, _VP, _VP]),
@@ -226,6 +227,14 @@ def nlinv_grid(plan: Plan, kxy, y, Y_out, stream=None):
                              _ptr(y, numel=plan.J * S, name="y"),
                              _ptr(Y_out, numel=plan.J * plan.G * plan.G, name="Y_out"),
                              _stream(stream)), "nlinv_grid")
+
+
+def nlinv_grid_nufft(plan: Plan, kxy, y, W: int, Y_out, stream=None):
+    S = kxy.shape[0]
+    _check(_lib().nlinv_grid_nufft(plan.handle, S, _ptr(kxy, torch.float64, 2 * S, "kxy"),
+                                   _ptr(y, numel=plan.J * S, name="y"), int(W),
+                                   _ptr(Y_out, numel=plan.J * plan.G * plan.G, name="Y_out"),
+                                   _stream(stream)), "nlinv_grid_nufft")
 
 
 def nlinv_apply_DF(plan: Plan, xhat, dx, z, stream=None):

@@ -24,7 +24,7 @@ def test_batch_of_independent_frames_matches_oracle_and_single_launches():
     g = O.Geometry(N=N, J=J)
     frames = cart_frames(N, J, B, seed=11)
     P = frames[0][1]
-    plan = make_plan(N, J, psf=P, max_batch=8)
+    plan = make_plan(N, J, psf=P, max_batch=8, exec_mode=2)   # single frames on the batch kernel's arithmetic
     # each frame starts from its own x_prev (frame 0 from the initial value)
     xps = [None] + [O.XVec(S.random_complex((N, N), 40 + f, 0.3) + 1.0,
                            S.random_complex((J, g.gc, g.gc), 50 + f, 20.0)) for f in range(1, B)]

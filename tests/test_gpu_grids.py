@@ -96,3 +96,57 @@ def test_grid_choices_outside_the_compiled_set_are_refused():
         with pytest.raises(L.NlinvError) as e:
             make_plan(N, 2, G=G)
         assert e.value.code == code
+
+
+@pytest.mark.parametrize("N,J,G,W", [(20, 3, 40, 6), (32, 2, 64, 8), (20, 2, 54, 6), (160, 4, 320, 6),
+                                     (160, 3, 486, 7)])
+def test_convolution_gridding_matches_oracle(N, J, G, W):
+    """nlinv_grid_nufft against the oracle's Kaiser-Bessel gridding (the same
+    algorithm, 1e-5) and against the exact adjoint NDFT within the kernel
+    bound (2e-5 at W >= 6)."""
+    from paper_1701_08361_gb300 import nlinv as L
+    kx, ky = S.radial_trajectory(N, 11, 5, 2)
+    y = S.random_complex((J, len(kx)), 91)
+    plan = make_plan(N, J, G=G)
+    kxy = torch.tensor(np.stack([kx, ky], 1), dtype=torch.float64, device="cuda")
+    Yd = torch.empty(J * G * G, dtype=torch.complex64, device="cuda")
+    L.nlinv_grid_nufft(plan, kxy, to_dev(y), W, Yd)
+    assert L.nlinv_sync(plan) == 0
+    got = to_np(Yd)
+    e_kb = rel(got, O.grid_data_kb(kx, ky, y, N, G, W))
+    e_ex = rel(got, O.grid_data(kx, ky, y, N, G))
+    print(f"N={N} G={G} W={W}: vs oracle KB gridding {e_kb:.2e}, vs exact NDFT {e_ex:.2e}")
+    assert e_kb <= TOL and e_ex <= 2e-5
+
+
+def test_autotuner_record_and_pick():
+    """The tuner times every candidate (compiled grids in the gamma range x
+    execution paths), keeps the fastest, and a plan made from its record
+    reconstructs the frame like the oracle on the picked grid."""
+    import json
+    import os
+    import tempfile
+    from paper_1701_08361_gb300 import nlinv as L
+    from paper_1701_08361_gb300 import tune as T
+    N, J, M, K = 20, 3, 2, 3
+    with tempfile.TemporaryDirectory() as d:
+        db = os.path.join(d, "db.json")
+        rec = T.tune(N, J, M, K, gamma=(1.0, 1.5), db=db, frames=3)
+        grids = {c["G"] for c in rec["candidates"]}
+        assert grids == {G for G, n in L.nlinv_grid_list() if n == N and G <= 60}
+        assert rec["ms_per_frame"] == min(c["ms_per_frame"] for c in rec["candidates"])
+        assert {2, 3} & {c["exec_mode"] for c in rec["candidates"]}
+        assert json.load(open(db))[T.gpu_name()]
+        p = T.tuned_params(N, J, M, K, gamma=(1.0, 1.5), db=db)
+        assert (p.G, p.exec_mode, p.cluster_cs) == (rec["pick"]["G"], rec["pick"]["exec_mode"],
+                                                     rec["pick"]["cluster_cs"])
+    G = p.G
+    g = O.Geometry(N=N, J=J, grid=G)
+    kx, ky, y, _, _ = S.radial_frame(N, J, 13, 5, 0, seed=3)
+    Y, P = O.grid_data(kx, ky, y, N, G), O.psf_kernel(kx, ky, N, G).real
+    ref = O.nlinv_frame(Y, P, O.XVec.initial(g), O.XVec.initial(g), g, O.Params(newton_steps=M, cg_iters=K))
+    plan = L.nlinv_plan(p, to_dev(P, torch.float32))
+    x = torch.empty(plan.nx, dtype=torch.complex64, device="cuda")
+    L.nlinv_frame(plan, to_dev(Y), 0, None, x)
+    assert L.nlinv_sync(plan) == 0
+    assert rel(to_np(x), ref.flat()) <= 1e-3
