@@ -33,10 +33,11 @@ def nvcc() -> str:
 
 
 def grid_sizes():
-    """(G1, G2, N) of every compiled grid, as NLINV_GRIDS in csrc/common.h lists them."""
+    """(G1, G2, N, TW, MINB) of every compiled grid, as NLINV_GRIDS in csrc/common.h lists them."""
     txt = open(os.path.join(CSRC, "common.h")).read()
     body = re.search(r"#define NLINV_GRIDS\(X\)((?:.*\\\n)*.*)", txt).group(1)
-    return [(int(a), int(b), int(n)) for a, b, n in re.findall(r"X\((\d+),\s*(\d+),\s*(\d+)\)", body)]
+    return [tuple(int(v) for v in m)
+            for m in re.findall(r"X\((\d+),\s*(\d+),\s*(\d+),\s*(\d+),\s*(\d+)\)", body)]
 
 
 def deps():
@@ -54,10 +55,10 @@ def units(extra=(), sizes=None):
     """(object path, nvcc compile command) of every translation unit."""
     base = [nvcc(), *FLAGS, *ARCH, *extra, "-I", INCLUDE, "-I", CSRC, "-c"]
     out = [(os.path.join(OBJ, "nlinv.o"), base + [os.path.join(CSRC, "nlinv.cu")])]
-    for g1, g2, n in (sizes or grid_sizes()):
+    for g1, g2, n, tw, mb in (sizes or grid_sizes()):
         o = os.path.join(OBJ, f"grid_{g1}x{g2}_{n}.o")
-        out.append((o, base + [f"-DNLINV_G1={g1}", f"-DNLINV_G2={g2}", f"-DNLINV_NR={n}",
-                               os.path.join(CSRC, "grid.cu")]))
+        out.append((o, base + [f"-DNLINV_G1={g1}", f"-DNLINV_G2={g2}", f"-DNLINV_NR={n}", f"-DNLINV_TWU={tw}",
+                               f"-DNLINV_MINBU={mb}", os.path.join(CSRC, "grid.cu")]))
     return out
 
 

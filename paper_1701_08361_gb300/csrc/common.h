@@ -164,15 +164,18 @@ struct GridOps {
 #endif
 };
 
-// The compiled grids X(G1, G2, N): G = G1 x G2 with an N x N field of view
-// (one grid.cu unit each).  G = 2N for the twofold grids; the others are
-// grids G = 2 gamma N of Eq. (8) with gamma > 1 (radix 3, 5 and 7 splits).
-// A unit left out of a build leaves its grid unsupported (weak reference).
-#define NLINV_GRIDS(X)                                                                          \
-  X(4, 4, 8) X(4, 6, 12) X(4, 10, 20) X(8, 8, 32) X(8, 16, 64) X(16, 16, 128) X(16, 20, 160)   \
-  X(16, 24, 192) X(16, 32, 256) X(4, 14, 20) X(6, 9, 20) X(8, 9, 24) X(16, 28, 160)            \
-  X(16, 30, 160) X(18, 27, 160) X(16, 32, 160) X(20, 28, 160) X(16, 24, 128)
-#define NLINV_DECLARE_OPS(a, b, n) const GridOps* grid_ops_##a##_##b##_##n() __attribute__((weak));
+// The compiled grids X(G1, G2, N, TW, MINB): G = G1 x G2 with an N x N field
+// of view, tile width TW and MINB CTAs per SM (Cfg in phases.cuh); one
+// grid.cu unit each.  G = 2N for the twofold grids; the others are grids
+// G = 2 gamma N of Eq. (8) with gamma > 1 (radix 3, 5 and 7 splits).  A unit
+// left out of a build leaves its grid unsupported (weak reference).
+#define NLINV_GRIDS(X)                                                                               \
+  X(4, 4, 8, 16, 2) X(4, 6, 12, 16, 2) X(4, 10, 20, 16, 2) X(8, 8, 32, 16, 2) X(8, 16, 64, 16, 2)   \
+  X(16, 16, 128, 16, 2) X(16, 20, 160, 12, 1) X(16, 24, 192, 16, 1) X(16, 32, 256, 16, 1)          \
+  X(4, 14, 20, 16, 2) X(6, 9, 20, 16, 2) X(8, 9, 24, 16, 2) X(16, 28, 160, 16, 1)                  \
+  X(16, 30, 160, 16, 1) X(18, 27, 160, 16, 1) X(16, 32, 160, 16, 1) X(20, 28, 160, 16, 1)          \
+  X(16, 24, 128, 16, 1)
+#define NLINV_DECLARE_OPS(a, b, n, tw, mb) const GridOps* grid_ops_##a##_##b##_##n() __attribute__((weak));
 NLINV_GRIDS(NLINV_DECLARE_OPS)
 #undef NLINV_DECLARE_OPS
 

@@ -30,7 +30,7 @@ int cuda_fail(cudaError_t e, const char* what) {
 }
 
 const GridOps* grid_ops(int G, int N) {
-#define NLINV_PICK_OPS(a, b, n) \
+#define NLINV_PICK_OPS(a, b, n, tw, mb) \
   if (G == (a) * (b) && N == (n) && grid_ops_##a##_##b##_##n) return grid_ops_##a##_##b##_##n();
   NLINV_GRIDS(NLINV_PICK_OPS)
 #undef NLINV_PICK_OPS
@@ -226,7 +226,7 @@ const char* nlinv_last_cuda_error(void) { return g_cuda_err; }
 
 int nlinv_grid_list(int* G_out, int* N_out, int cap) {
   int n = 0;
-#define NLINV_LIST_GRID(a, b, nr)                   \
+#define NLINV_LIST_GRID(a, b, nr, tw, mb)           \
   if (grid_ops_##a##_##b##_##nr) {                  \
     if (n < cap && G_out) G_out[n] = (a) * (b);     \
     if (n < cap && N_out) N_out[n] = (nr);          \

@@ -119,29 +119,23 @@ struct Ctx {
   int bid, nb;          // this CTA's index within the CTAs working on this frame, and their count
 };
 
-// Tile width (columns of a column item, rows of a row item): the widest
-// multiple of 4 (at most 16) whose CTA of TW x max(G1, G2) threads stays
-// within 256 threads, i.e. 8 warps, 2 per scheduler, so that a thread may
-// hold up to 255 registers: the register DFTs of a CTA with 10 or more warps
-// are capped at 168 registers and spill (measured on the 320 grid: 12
-// columns and 256 threads 3.44 ms per frame, 16 columns and 320 threads
-// 3.84 ms).  NLINV_TW overrides it (experiments).
-constexpr int default_tw(int mx) {
-#ifdef NLINV_TW
-  return NLINV_TW + 0 * mx;
-#else
-  return (256 / mx) / 4 * 4 > 16 ? 16 : ((256 / mx) / 4 * 4 < 4 ? 4 : (256 / mx) / 4 * 4);
-#endif
-}
-
-// One compiled grid: G = G1 x G2 (the two register DFT lengths) and the
-// image side NR (the field of view, rows/cols [0, NR) of the G grid; G = 2 NR
-// unless a grid G = 2 gamma N of Eq. (8) is chosen).
-template <int G1_, int G2_, int NR_ = G1_ * G2_ / 2> struct Cfg {
+// One compiled grid: G = G1 x G2 (the two register DFT lengths), the image
+// side NR (the field of view, rows/cols [0, NR) of the G grid; G = 2 NR unless
+// a grid G = 2 gamma N of Eq. (8) is chosen), the tile width TW (columns of a
+// column item, rows of a row item) and the CTAs per SM MINB the persistent
+// kernels are compiled for.  A CTA of TW x max(G1, G2) threads with 10 or
+// more warps is capped at 168 registers a thread and its register DFTs
+// spill; at 8 warps (2 per scheduler) a thread may hold 255.  On the 320
+// grid 12-wide tiles (256 threads) measured 3.44 ms per frame against 3.84
+// ms for 16-wide tiles (320 threads); the batched and the 512 grid sizes
+// measured faster with 16-wide tiles.
+template <int G1_, int G2_, int NR_ = G1_ * G2_ / 2, int TW_ = 16,
+          int MINB_ = ((TW_ * (G1_ > G2_ ? G1_ : G2_) + 31) / 32 * 32 <= 256 ? 2 : 1)>
+struct Cfg {
   static constexpr int G1 = G1_, G2 = G2_;
   static constexpr int G = G1 * G2;
   static constexpr int MX = G1 > G2 ? G1 : G2;
-  static constexpr int TW = default_tw(MX);   // columns per tile / rows per group
+  static constexpr int TW = TW_;            // columns per tile / rows per group
   static constexpr int BS = (TW * MX + 31) / 32 * 32;   // threads per CTA (whole warps)
   static constexpr int RS = G + MX;         // smem stride of one row (float2)
   static constexpr int NR = NR_;            // image rows N
@@ -151,11 +145,7 @@ template <int G1_, int G2_, int NR_ = G1_ * G2_ / 2> struct Cfg {
   static constexpr int B1F = NR / G1, B1 = (NR + G1 - 1) / G1;
   static constexpr int SMEM_X = TW * RS * 8;  // exchange buffer bytes
   // CTAs per SM the persistent kernel is compiled for (caps registers)
-#ifdef NLINV_MINB
-  static constexpr int MINB = NLINV_MINB;
-#else
-  static constexpr int MINB = BS <= 128 ? 2 : 1;
-#endif
+  static constexpr int MINB = MINB_;
   // staged operands of one column item of the CG column pass: T(r_k) and
   // T(p_{k-1}) tiles [N][TW] (and the PSF tile [G][TW] if staged).  One staging buffer:
   // a second one (a full item ahead) measured slower, as the larger shared
