@@ -82,7 +82,14 @@ typedef struct {
                             memory; grid barriers only for the channel sum
                             and the CG inner products); nlinv_plan returns
                             NLINV_EUNSUPPORTED when the J clusters cannot be
-                            co-resident */
+                            co-resident;
+                         4: the launches of 1 captured once into a CUDA graph
+                            with programmatic dependent launches between the
+                            phases, replayed per frame through plan-owned
+                            staging buffers (captured on the first frame and
+                            again after nlinv_set_alpha0; the capture is on a
+                            plan-owned stream, so the first frame must not be
+                            issued while the calling thread captures) */
   int max_batch;      /* frames of this plan one nlinv_batch call may hold, 1..64;
                          0 -> 1 (the plan allocates one workspace per frame) */
   int G;              /* grid side: 0 -> 2N (gamma = 1); else a grid G = 2 gamma N
@@ -116,7 +123,8 @@ int nlinv_plan_destroy(nlinv_plan_t plan);
 int nlinv_plan_sizes(nlinv_plan_t plan, long long* nx, int* G, int* Gc);
 
 /* How nlinv_frame runs this plan's frames: *exec_path = 1 (per-phase
- * launches), 2 (grid kernel) or 3 (cluster kernel, see exec_mode), and
+ * launches), 2 (grid kernel), 3 (cluster kernel) or 4 (per-phase launches in
+ * a CUDA graph), see exec_mode, and
  * *cluster_size = CTAs per channel cluster (0 unless exec_path is 3).
  * Either pointer may be NULL. */
 int nlinv_plan_path(nlinv_plan_t plan, int* exec_path, int* cluster_size);

@@ -122,6 +122,13 @@ struct nlinv_plan_s {
   int batch_occ = 0;          // co-resident CTAs per SM of k_batch
   int cl_cs = 0;              // CTAs per cluster of k_frame_cl (0: it does not fit)
   nlinv::cl::Lay cl_lay;             // its shared-memory layout
+  // exec_mode 4: the captured per-phase frame and its staging buffers
+  cudaGraphExec_t gexec = nullptr;
+  double galpha0 = 0.0;       // alpha_0 the graph was captured with
+  cudaStream_t gcap = nullptr;
+  void* gmem = nullptr;
+  float2 *gy = nullptr, *gxp = nullptr, *gx = nullptr, *grho = nullptr, *gimg = nullptr;
+  float* gp = nullptr;
   cudaStream_t aux = nullptr; // stream of this plan's group inside nlinv_batch
   cudaEvent_t ev_fork = nullptr, ev_done = nullptr;
 };

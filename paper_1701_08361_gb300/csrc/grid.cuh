@@ -27,9 +27,19 @@ __device__ __forceinline__ Ctx whole_grid(const Ctx& C0) {
   return C;
 }
 
+// Entry of a one-phase kernel: let the next kernel of the stream be launched
+// (programmatic dependent launch: its CTAs take SMs as ours leave), then wait
+// until the previous kernel has finished and its stores are visible.  Both
+// are no-ops for a kernel launched without programmatic dependencies.
+__device__ __forceinline__ Ctx phase_entry(const Ctx& C0) {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  return whole_grid(C0);
+}
+
 template <class K>
 __global__ void __launch_bounds__(K::BS) k_coil_y(Ctx C0, const float2* src, float2* hout) {
-  const Ctx C = whole_grid(C0);
+  const Ctx C = phase_entry(C0);
   extern __shared__ float2 sm[];
   phase_coil_y<K>(C, sm, src, hout);
 }
@@ -37,7 +47,7 @@ __global__ void __launch_bounds__(K::BS) k_coil_y(Ctx C0, const float2* src, flo
 template <class K>
 __global__ void __launch_bounds__(K::BS) k_row_cg(Ctx C0, int k, const float2* p_old, float2* p_new,
                                                   float2* vout) {
-  const Ctx C = whole_grid(C0);
+  const Ctx C = phase_entry(C0);
   extern __shared__ float2 sm[];
   __shared__ float2 sred[32];
   phase_row_cg<K>(C, sm, sred, k, p_old, p_new, vout);
@@ -46,14 +56,14 @@ __global__ void __launch_bounds__(K::BS) k_row_cg(Ctx C0, int k, const float2* p
 template <class K>
 __global__ void __launch_bounds__(K::BS) k_row_b(Ctx C0, int mode, const float2* hin, const float2* rho,
                                                  const float2* drho, const float2* img, float2* vout) {
-  const Ctx C = whole_grid(C0);
+  const Ctx C = phase_entry(C0);
   extern __shared__ float2 sm[];
   phase_row_b<K>(C, sm, mode, hin, rho, drho, img, vout);
 }
 
 template <class K>
 __global__ void __launch_bounds__(K::BS) k_row_deapod(Ctx C0, const float* dap, float scale, float2* v) {
-  const Ctx C = whole_grid(C0);
+  const Ctx C = phase_entry(C0);
   extern __shared__ float2 sm[];
   phase_row_deapod<K>(C, sm, dap, scale, v);
 }
@@ -61,7 +71,7 @@ __global__ void __launch_bounds__(K::BS) k_row_deapod(Ctx C0, const float* dap, 
 template <class K>
 __global__ void __launch_bounds__(K::BS) k_col_c(Ctx C0, int mode, const float* P, const float2* Yin,
                                                  float2* zout, float2* vio, int k) {
-  const Ctx C = whole_grid(C0);
+  const Ctx C = phase_entry(C0);
   extern __shared__ float2 sm[];
   phase_col_c<K>(C, sm, mode, P, Yin, zout, vio, k);
 }
@@ -69,7 +79,7 @@ __global__ void __launch_bounds__(K::BS) k_col_c(Ctx C0, int mode, const float* 
 template <class K>
 __global__ void __launch_bounds__(K::BS) k_row_d(Ctx C0, const float2* rho, const float2* win, float2* sout,
                                                  float2* kbout) {
-  const Ctx C = whole_grid(C0);
+  const Ctx C = phase_entry(C0);
   extern __shared__ float2 sm[];
   phase_row_d<K>(C, sm, rho, win, sout, kbout);
 }
@@ -78,7 +88,7 @@ template <class K>
 __global__ void __launch_bounds__(K::BS) k_col_e(Ctx C0, int mode, float alpha, int k, const float2* kbin,
                                                  const float2* sin, const float2* p_old, float2* p_new,
                                                  float2* out, float2* hout, int slot) {
-  const Ctx C = whole_grid(C0);
+  const Ctx C = phase_entry(C0);
   extern __shared__ float2 sm[];
   __shared__ float2 sred[32];
   switch (mode) {
@@ -91,19 +101,25 @@ __global__ void __launch_bounds__(K::BS) k_col_e(Ctx C0, int mode, float alpha, 
 
 template <class K>
 __global__ void __launch_bounds__(K::BS) k_upd(Ctx C0, int k, int last, const float2* p) {
-  const Ctx C = whole_grid(C0);
+  const Ctx C = phase_entry(C0);
   extern __shared__ float2 sm[];
   __shared__ float2 sred[32];
   phase_upd<K>(C, sm, sred, k, last != 0, p);
 }
 
+// x = (rho = 1, c^ = 0): the first frame's initial value (Sec. 3.3)
+__global__ void k_initial_value(int nx, int NN, float2* x) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nx; i += gridDim.x * blockDim.x)
+    x[i] = make_float2(i < NN ? 1.f : 0.f, 0.f);
+}
+
 __global__ void k_init(Ctx C0, const float2* xprev, float damping) {
-  const Ctx C = whole_grid(C0);
+  const Ctx C = phase_entry(C0);
   phase_init(C, xprev, damping);
 }
 
 __global__ void k_final(Ctx C0, float2* xout, float2* rho_out, float2* img_out) {
-  const Ctx C = whole_grid(C0);
+  const Ctx C = phase_entry(C0);
   phase_final(C, xout, rho_out, img_out);
 }
 
@@ -469,66 +485,72 @@ struct Launch {
   const nlinv_plan_s* pl;
   cudaStream_t st;
   int fixed = 0;   // if > 0: every launch uses this many CTAs (CG reductions need equal counts)
+  bool pdl = false;   // launch with programmatic dependent launch (see phase_entry)
   int pick(int g) const { return fixed > 0 ? fixed : g; }
+  template <class... KArgs, class... Args>
+  int go(void (*kern)(KArgs...), int grid, int block, size_t smem, const char* what, Args... args) const {
+    if (!pdl) {
+      kern<<<grid, block, smem, st>>>(args...);
+      CKL(what);
+      return NLINV_OK;
+    }
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    CK(cudaLaunchKernelEx(&cfg, kern, args...));
+    return NLINV_OK;
+  }
   int coil_y(const float2* src, float2* hout) const {
     const Ctx& C = pl->C;
     const int g = plan_grid(C.J * ((C.Gc + K::TW - 1) / K::TW), 1);
-    k_coil_y<K><<<pick(g), K::BS, K::SMEM, st>>>(C, src, hout);
-    CKL("k_coil_y");
-    return NLINV_OK;
+    return go(&k_coil_y<K>, pick(g), K::BS, (size_t)K::SMEM, "k_coil_y", C, src, hout);
   }
   int row_cg(int k, const float2* p_old, float2* p_new, float2* vout) const {
     const Ctx& C = pl->C;
     const int g = plan_grid(C.J * ((C.N + K::TW - 1) / K::TW), 1);
-    k_row_cg<K><<<pick(g), K::BS, K::SMEM, st>>>(C, k, p_old, p_new, vout);
-    CKL("k_row_cg");
-    return NLINV_OK;
+    return go(&k_row_cg<K>, pick(g), K::BS, (size_t)K::SMEM, "k_row_cg", C, k, p_old, p_new, vout);
   }
   int row_b(int mode, const float2* hin, const float2* rho, const float2* drho, const float2* img,
             float2* vout) const {
     const Ctx& C = pl->C;
     const int g = plan_grid(C.J * ((C.N + K::TW - 1) / K::TW), 1);
-    k_row_b<K><<<pick(g), K::BS, K::SMEM, st>>>(C, mode, hin, rho, drho, img, vout);
-    CKL("k_row_b");
-    return NLINV_OK;
+    return go(&k_row_b<K>, pick(g), K::BS, (size_t)K::SMEM, "k_row_b", C, mode, hin, rho, drho, img, vout);
   }
   int row_deapod(const float* dap, float scale, float2* v) const {
     const Ctx& C = pl->C;
     const int g = plan_grid(C.J * ((C.N + K::TW - 1) / K::TW), 1);
-    k_row_deapod<K><<<pick(g), K::BS, K::SMEM, st>>>(C, dap, scale, v);
-    CKL("k_row_deapod");
-    return NLINV_OK;
+    return go(&k_row_deapod<K>, pick(g), K::BS, (size_t)K::SMEM, "k_row_deapod", C, dap, scale, v);
   }
   int col_c(int mode, const float* P, const float2* Yin, float2* zout, float2* vio, int k = 0) const {
     const Ctx& C = pl->C;
     const int g = plan_grid(C.J * ((C.G + K::TW - 1) / K::TW), 1);
-    k_col_c<K><<<pick(g), K::BS, K::SMEM, st>>>(C, mode, P, Yin, zout, vio, k);
-    CKL("k_col_c");
-    return NLINV_OK;
+    return go(&k_col_c<K>, pick(g), K::BS, (size_t)K::SMEM, "k_col_c", C, mode, P, Yin, zout, vio, k);
   }
   int row_d(const float2* rho, const float2* win, float2* sout, float2* kbout) const {
     const Ctx& C = pl->C;
     const int g = plan_grid(C.J * ((C.N + K::TW - 1) / K::TW), 1);
-    k_row_d<K><<<pick(g), K::BS, K::SMEM, st>>>(C, rho, win, sout, kbout);
-    CKL("k_row_d");
-    return NLINV_OK;
+    return go(&k_row_d<K>, pick(g), K::BS, (size_t)K::SMEM, "k_row_d", C, rho, win, sout, kbout);
   }
   int col_e(int mode, float alpha, int k, const float2* kbin, const float2* sin, const float2* p_old,
             float2* p_new, float2* out, float2* hout, int slot) const {
     const Ctx& C = pl->C;
     const int items = C.J * ((C.Gc + K::TW - 1) / K::TW);
     const int g = plan_grid(items, (C.N * C.N + K::BS - 1) / K::BS);
-    k_col_e<K><<<pick(g), K::BS, K::SMEM, st>>>(C, mode, alpha, k, kbin, sin, p_old, p_new, out, hout, slot);
-    CKL("k_col_e");
-    return NLINV_OK;
+    return go(&k_col_e<K>, pick(g), K::BS, (size_t)K::SMEM, "k_col_e", C, mode, alpha, k, kbin, sin, p_old, p_new, out, hout, slot);
   }
   int upd(int k, int last, const float2* p) const {
     const Ctx& C = pl->C;
     const int items = C.J * ((C.Gc + K::TW - 1) / K::TW);
     const int g = plan_grid(items, (C.N * C.N + K::BS - 1) / K::BS);
-    k_upd<K><<<pick(g), K::BS, K::SMEM, st>>>(C, k, last, p);
-    CKL("k_upd");
-    return NLINV_OK;
+    return go(&k_upd<K>, pick(g), K::BS, (size_t)K::SMEM, "k_upd", C, k, last, p);
   }
   // coil maps c_j = W^-1 c^_j of x^ into the plan's c buffer
   int coils(const float2* xhat) const {
@@ -644,7 +666,6 @@ struct Ops {
   static int frame(const nlinv_plan_s* pl, cudaStream_t st, const FrameArgs& F) {
     const int mode = pl->prm.exec_mode;
     Ctx C = pl->C;
-    const int NN = pl->N * pl->N;
     if (mode == 3 && pl->cl_cs > 0) {
       CK(cudaMemsetAsync(C.bar, 0, 2 * sizeof(unsigned), st));
       cudaLaunchAttribute at[2];
@@ -660,10 +681,19 @@ struct Ops {
                                      (size_t)K::SMEM, st));
       return NLINV_OK;
     }
-    Launch<K> L{pl, st, pl->coop_grid};
+    if (mode == 4) return frame_graph(const_cast<nlinv_plan_s*>(pl), st, F);
+    return per_phase(pl, st, F, false);
+  }
+
+  // The frame as one launch per fused phase (every launch with the same CTA
+  // count, so that the CG partial sums line up), optionally with programmatic
+  // dependent launches.
+  static int per_phase(const nlinv_plan_s* pl, cudaStream_t st, const FrameArgs& F, bool pdl) {
+    Ctx C = pl->C;
+    const int NN = pl->N * pl->N;
+    Launch<K> L{pl, st, pl->coop_grid, pdl};
     const int ge = plan_grid((int)((C.nx + 255) / 256), 1);
-    k_init<<<ge, 256, 0, st>>>(C, F.io.xprev, F.damping);
-    CKL("k_init");
+    RC(L.go(&k_init, ge, 256, 0, "k_init", C, F.io.xprev, F.damping));
     for (int n = 0; n < F.M; ++n) {
       const float alpha = F.alpha[n];
       RC(L.coil_y(C.xn + NN, C.h));
@@ -682,8 +712,75 @@ struct Ops {
       }
     }
     RC(L.coils(C.xn));
-    k_final<<<ge, 256, 0, st>>>(C, F.io.xout, F.io.rho_out, F.io.img_out);
-    CKL("k_final");
+    return L.go(&k_final, ge, 256, 0, "k_final", C, F.io.xout, F.io.rho_out, F.io.img_out);
+  }
+
+  // The per-phase frame captured once into a CUDA graph (programmatic
+  // dependent launches between its kernels) and replayed for every frame:
+  // the graph reads and writes plan-owned staging buffers, so a frame is
+  // [copy Y, P, x_prev in] [graph] [copy x^, rho, image out].  The capture is
+  // redone when alpha_0 changes (the alpha_n are kernel arguments).
+  static int frame_graph(nlinv_plan_s* pl, cudaStream_t st, const FrameArgs& F) {
+    const size_t nx = (size_t)pl->nx, NN = (size_t)pl->N * pl->N;
+    const size_t ny = (size_t)pl->J * pl->G * pl->G, np = (size_t)pl->G * pl->G;
+    if (!pl->gmem) {
+      const size_t bytes = align_up(ny * sizeof(float2)) + align_up(np * sizeof(float)) +
+                           3 * align_up(nx * sizeof(float2)) + 2 * align_up(NN * sizeof(float2));
+      CK(cudaMalloc(&pl->gmem, bytes));
+      char* b = (char*)pl->gmem;
+      pl->gy = (float2*)b;
+      b += align_up(ny * sizeof(float2));
+      pl->gp = (float*)b;
+      b += align_up(np * sizeof(float));
+      pl->gxp = (float2*)b;
+      b += align_up(nx * sizeof(float2));
+      pl->gx = (float2*)b;
+      b += align_up(nx * sizeof(float2));
+      pl->grho = (float2*)b;
+      b += align_up(NN * sizeof(float2));
+      pl->gimg = (float2*)b;
+      CK(cudaStreamCreateWithFlags(&pl->gcap, cudaStreamNonBlocking));
+    }
+    if (!pl->gexec || pl->galpha0 != pl->prm.alpha0) {
+      if (pl->gexec) {
+        cudaGraphExecDestroy(pl->gexec);
+        pl->gexec = nullptr;
+      }
+      FrameArgs Fg = F;
+      Fg.io.Y = pl->gy;
+      Fg.io.P = pl->gp;
+      Fg.io.xprev = pl->gxp;
+      Fg.io.xout = pl->gx;
+      Fg.io.rho_out = pl->grho;
+      Fg.io.img_out = pl->gimg;
+      CK(cudaStreamBeginCapture(pl->gcap, cudaStreamCaptureModeThreadLocal));
+      const int rc = per_phase(pl, pl->gcap, Fg, true);
+      cudaGraph_t graph = nullptr;
+      const cudaError_t ec = cudaStreamEndCapture(pl->gcap, &graph);
+      if (rc != NLINV_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+      }
+      CK(ec);
+      const cudaError_t ei = cudaGraphInstantiate(&pl->gexec, graph, 0);
+      cudaGraphDestroy(graph);
+      CK(ei);
+      pl->galpha0 = pl->prm.alpha0;
+    }
+    CK(cudaMemcpyAsync(pl->gy, F.io.Y, ny * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(pl->gp, F.io.P, np * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    if (F.io.xprev) {
+      CK(cudaMemcpyAsync(pl->gxp, F.io.xprev, nx * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+    } else {
+      k_initial_value<<<plan_grid((int)((nx + 255) / 256), 1), 256, 0, st>>>((int)nx, (int)NN, pl->gxp);
+      CKL("k_initial_value");
+    }
+    CK(cudaGraphLaunch(pl->gexec, st));
+    CK(cudaMemcpyAsync(F.io.xout, pl->gx, nx * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+    if (F.io.rho_out)
+      CK(cudaMemcpyAsync(F.io.rho_out, pl->grho, NN * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+    if (F.io.img_out)
+      CK(cudaMemcpyAsync(F.io.img_out, pl->gimg, NN * sizeof(float2), cudaMemcpyDeviceToDevice, st));
     return NLINV_OK;
   }
 

@@ -273,7 +273,7 @@ int nlinv_plan(nlinv_plan_t* out, const nlinv_params_t* p, const float* psf, nli
   if (p->n_turns < 1 || p->n_turns > 1024) return NLINV_EINVAL;
   if (!(p->alpha0 > 0.0) || !(p->q > 0.0) || p->q > 1.0 || !(p->damping >= 0.0)) return NLINV_EINVAL;
   if (!(p->w_a >= 0.0) || !(p->w_l >= 0.0)) return NLINV_EINVAL;
-  if (p->exec_mode < 0 || p->exec_mode > 3) return NLINV_EINVAL;
+  if (p->exec_mode < 0 || p->exec_mode > 4) return NLINV_EINVAL;
   if (p->max_batch < 0 || p->max_batch > kMaxBatch) return NLINV_EINVAL;
   if (p->cluster_cs < 0 || p->cluster_cs > 16) return NLINV_EINVAL;
   if (psf && ((uintptr_t)psf & 3u)) return NLINV_EINVAL;
@@ -417,6 +417,9 @@ int nlinv_plan(nlinv_plan_t* out, const nlinv_params_t* p, const float* psf, nli
 
 int nlinv_plan_destroy(nlinv_plan_t pl) {
   if (!pl) return NLINV_EINVAL;
+  if (pl->gexec) cudaGraphExecDestroy(pl->gexec);
+  if (pl->gcap) cudaStreamDestroy(pl->gcap);
+  cudaFree(pl->gmem);
   if (pl->ev_fork) cudaEventDestroy(pl->ev_fork);
   if (pl->ev_done) cudaEventDestroy(pl->ev_done);
   if (pl->aux) cudaStreamDestroy(pl->aux);
@@ -437,7 +440,7 @@ int nlinv_plan_sizes(nlinv_plan_t pl, long long* nx, int* G, int* Gc) {
 int nlinv_plan_path(nlinv_plan_t pl, int* exec_path, int* cluster_size) {
   RC(check_plan(pl));
   const int m = pl->prm.exec_mode;
-  const int path = m == 1 ? 1 : (m == 3 && pl->cl_cs > 0 ? 3 : 2);
+  const int path = (m == 1 || m == 4) ? m : (m == 3 && pl->cl_cs > 0 ? 3 : 2);
   if (exec_path) *exec_path = path;
   if (cluster_size) *cluster_size = path == 3 ? pl->cl_cs : 0;
   return NLINV_OK;

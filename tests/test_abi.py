@@ -49,7 +49,7 @@ def test_defaults_and_strerror(lib):
 @pytest.mark.parametrize("field,value,code", [
     ("N", 0, -1), ("N", 100, -6), ("Gc", 1, -1), ("Gc", 1000, -1), ("G", 300, -1), ("G", 500, -6),
     ("newton_steps", 0, -1), ("newton_steps", 33, -1), ("cg_iters", -1, -1),
-    ("q", 1.5, -1), ("alpha0", 0.0, -1), ("n_turns", 0, -1), ("exec_mode", 4, -1), ("exec_mode", -1, -1),
+    ("q", 1.5, -1), ("alpha0", 0.0, -1), ("n_turns", 0, -1), ("exec_mode", 5, -1), ("exec_mode", -1, -1),
 ])
 def test_invalid_plans_are_rejected_on_host(lib, field, value, code):
     from paper_1701_08361_gb300 import nlinv as L

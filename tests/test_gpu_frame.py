@@ -36,7 +36,7 @@ def run_frames(plan, frames, xprev=None):
     return out
 
 
-@pytest.mark.parametrize("exec_mode", [0, 1, 2, 3])
+@pytest.mark.parametrize("exec_mode", [0, 1, 2, 3, 4])
 def test_cartesian_frame_C1(exec_mode):
     """64x64 image on the 128 grid, 4 coils, every 3rd line + 16 centre
     lines, sigma = 1e-3, 7 Newton x 10 CG, alpha0 = 1, q = 1/2."""
@@ -85,7 +85,7 @@ def test_frame_from_given_x_prev_and_modes_agree():
     prm = O.Params(newton_steps=4, cg_iters=6, alpha0=2.0, q=0.6, damping=0.8)
     ref = O.nlinv_frame(Y, P, xp, xp.scale(0.8), g, prm)
     outs = []
-    for mode in (1, 2, 3):
+    for mode in (1, 2, 3, 4):
         plan = make_plan(N, J, psf=P, newton_steps=4, cg_iters=6, alpha0=2.0, q=0.6,
                          damping=0.8, exec_mode=mode)
         (x, _, _), = run_frames(plan, [(Y, 0)], xprev=xp.flat())
@@ -94,6 +94,8 @@ def test_frame_from_given_x_prev_and_modes_agree():
     # the same arithmetic up to the order of the inner products' partial sums
     assert rel(outs[0], outs[1]) <= 1e-5
     assert rel(outs[2], outs[1]) <= 1e-5
+    # the graph replays exactly the per-phase launches
+    assert np.array_equal(outs[3], outs[0])
 
 
 @pytest.mark.slow
@@ -143,7 +145,7 @@ def test_frame_C4_size_modes_agree():
 
 
 @pytest.mark.parametrize("M,K,mode", [(1, 1, 2), (1, 0, 2), (2, 1, 1), (1, 3, 1), (3, 0, 1),
-                                      (1, 1, 3), (1, 0, 3), (2, 2, 3)])
+                                      (1, 1, 3), (1, 0, 3), (2, 2, 3), (1, 0, 4), (2, 2, 4)])
 def test_degenerate_iteration_counts(M, K, mode):
     """One Newton step, one CG iteration, or none (x^ stays the initial value):
     the drivers' edge cases against the oracle, ragged N=20 grid."""
@@ -187,3 +189,36 @@ def test_cluster_kernel_matches_oracle_and_grid_kernel(N, J, Gc, cs):
         assert e <= TOL
         xs.append(x)
     assert rel(xs[0], xs[1]) <= 1e-4
+
+
+def test_graph_path_replays_over_a_stream_and_follows_alpha0():
+    """exec_mode 4: the captured per-phase frame replayed for a chained
+    radial stream (different data, turns and x_prev per frame, outputs only
+    where asked) equals the per-phase launches bit for bit, and a change of
+    alpha_0 re-captures the graph."""
+    from paper_1701_08361_gb300 import nlinv as L
+    N, J, K, U = 32, 3, 13, 5
+    frames, Ps = [], []
+    coils = S.coil_maps(N, J, 4)
+    for n in range(4):
+        kx, ky, y, _, _ = S.radial_frame(N, J, K, U, n, seed=4, coils=coils)
+        frames.append(O.grid_data(kx, ky, y, N, 2 * N))
+        Ps.append(O.psf_kernel(kx, ky, N, 2 * N).real)
+    outs = {}
+    for mode in (1, 4):
+        plan = make_plan(N, J, turns=U, exec_mode=mode, newton_steps=3, cg_iters=4)
+        for u in range(4):
+            L.nlinv_set_psf(plan, u, to_dev(Ps[u], torch.float32))
+        x = torch.empty(plan.nx, dtype=torch.complex64, device="cuda")
+        res = []
+        for n, Y in enumerate(frames):
+            if n == 2:
+                L.nlinv_set_alpha0(plan, 0.5)
+            img = torch.zeros(N * N, dtype=torch.complex64, device="cuda") if n % 2 else None
+            L.nlinv_frame(plan, to_dev(Y), n, None if n == 0 else x, x, None, img)
+            assert L.nlinv_sync(plan) == 0
+            res.append((to_np(x), None if img is None else to_np(img)))
+        outs[mode] = res
+    for (a, ia), (b, ib) in zip(outs[1], outs[4]):
+        assert np.array_equal(a, b)
+        assert (ia is None and ib is None) or np.array_equal(ia, ib)
