@@ -284,6 +284,7 @@ def run_ours(args):
     pk, pk_src = peaks()
     path, cs = L.nlinv_plan_path(plan)
     kernel_name = {1: "per-phase launches (k_row_cg, k_col_c, ...)",
+                   4: "per-phase launches in a CUDA graph with programmatic dependent launch",
                    2: "k_frame (grid kernel, one launch per frame)",
                    3: "k_frame_cl (cluster kernel, one launch per frame, %d CTAs per channel)" % cs}[path]
     fl = flops_per_frame(N, G, Gc, J, CFG["M"], CFG["CG"])
@@ -301,14 +302,15 @@ def run_ours(args):
         "config": {"workload": "real-time radial stream: N=160, G=320, J=10, 13 spokes x 5 turns, "
                                "7 Newton x 10 CG, moving phantom, sigma=1e-3",
                    "frames_per_step": F,
-                   "exec_mode": ["automatic", "per-phase", "grid kernel", "cluster kernel"][args.exec_mode],
+                   "exec_mode": ["default", "per-phase", "grid kernel", "cluster kernel",
+                                 "per-phase CUDA graph"][args.exec_mode],
                    "l2": "inputs larger than L2 (%.0f MB of gridded data per step) and L2 flushed "
                          "between steps" % (Yall.numel() * 8 / 1e6),
                    "parallelism": "replicas" if world > 1 else "single"},
         "latency_ms": {"p50": round(statistics.median(lat), 4), "min": round(lat[0], 4)},
         "roofline": {"bound": "alu", "achieved": round(achieved, 3),
                      "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
-                     "frac": round(achieved / fp32_peak, 4), "traffic": profiled_traffic(["", "", "k_frame", "k_frame_cl"][path]),
+                     "frac": round(achieved / fp32_peak, 4), "traffic": profiled_traffic(["", "", "k_frame", "k_frame_cl", ""][path]),
                      "kernel": kernel_name,
                      "peak_source": "FP32: %d SMs x 128 lanes x 2 flop x sm_max_mhz (%s)" % (sm_count(), pk_src)},
         "hbm": {"achieved_gbs": round(hbm, 1), "peak_gbs": pk["hbm_gbs"],
@@ -747,7 +749,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--frames-per-step", type=int, default=25)
-    ap.add_argument("--exec-mode", type=int, default=0, choices=[0, 1, 2, 3])
+    ap.add_argument("--exec-mode", type=int, default=0, choices=[0, 1, 2, 3, 4])
     ap.add_argument("--cpu-frames", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-loop", type=int, default=1)

@@ -318,12 +318,25 @@ int nlinv_set_alpha0(nlinv_plan_t plan, double alpha0);
  *   xprev_bar_out  device [n_x]: dL/dx_prev through the initial value and
  *                  the regulariser x_ref = damping x_prev, or NULL (zero
  *                  when x_prev is NULL).
- * Y, turn and x_prev as in nlinv_frame.  Uses a plan-owned workspace that
- * is allocated on first use; reads scalars back, so the call returns after
- * the work on `stream` is complete. */
+ * Y, turn and x_prev as in nlinv_frame.  The scalars of the recomputed CG
+ * and of its reverse stay on the device (FP64); the call reads alpha0-bar
+ * back once at the end, so it returns after the work on `stream` is
+ * complete.  Uses a plan-owned workspace that is allocated on first use.
+ * Returns NLINV_ENUMERIC if the recomputed CG breaks down. */
 int nlinv_frame_vjp(nlinv_plan_t plan, const void* Y, int turn, const void* x_prev,
                     const void* gbar, void* Ybar_out, double* alpha0_bar_out,
                     void* xprev_bar_out, nlinv_stream_t stream);
+
+/* nlinv_frame_vjp of nframes independent frames of one plan (nframes <= its
+ * max_batch): host arrays of device pointers Y[f], x_prev[f] (the array or
+ * an entry may be NULL), gbar[f], Ybar_out[f], xprev_bar_out[f] (array or
+ * entry NULL: not wanted), host ints turns[f]; alpha0_bar_out: host double
+ * [nframes] (or NULL).  Each frame's reverse pass runs on its own stream and
+ * frame workspace of the plan, forked from and joined back into `stream`;
+ * the call returns once all are complete. */
+int nlinv_batch_vjp(nlinv_plan_t plan, int nframes, const void* const* Y, const int* turns,
+                    const void* const* x_prev, const void* const* gbar, void* const* Ybar_out,
+                    double* alpha0_bar_out, void* const* xprev_bar_out, nlinv_stream_t stream);
 
 /* Bounded device-side wait until *flag == expected (flag: device int),
  * polling at most spin_limit times; on expiry the plan latches

@@ -1,8 +1,9 @@
 """torch.autograd.Function wrappers of the NLINV frame.
 
-Forward runs nlinv_frame / nlinv_batch; backward runs nlinv_frame_vjp, the
-hand-written reverse pass through the unrolled IRGNM / CG (Sec. 2.2,
-Eqs. 2-5) with per-Newton-step recomputation.  Differentiable inputs: the
+Forward runs nlinv_frame / nlinv_batch; backward runs nlinv_frame_vjp /
+nlinv_batch_vjp, the hand-written reverse pass through the unrolled IRGNM /
+CG (Sec. 2.2, Eqs. 2-5) with per-Newton-step recomputation (the frames of a
+batch on their own streams).  Differentiable inputs: the
 gridded data Y (complex64), alpha_0 (0-d float64 tensor) and x_prev.
 Gradients follow torch's complex convention (dL/dRe + i dL/dIm).
 """
@@ -79,11 +80,12 @@ class NLINVBatch(torch.autograd.Function):
         Ybar = torch.empty_like(Ys)
         xpb = torch.empty_like(xps) if ctx.has_prev else None
         gxs = gxs.contiguous()
-        a0bar = 0.0
-        for b in range(Ys.shape[0]):
-            a0bar += L.nlinv_frame_vjp(plan, Ys[b], ctx.turns[b], xps[b] if ctx.has_prev else None,
-                                       gxs[b], Ybar[b], xpb[b] if ctx.has_prev else None)
-        ga = torch.tensor(a0bar, dtype=torch.float64, device=Ys.device)
+        B = Ys.shape[0]
+        a0 = L.nlinv_batch_vjp(plan, [Ys[b] for b in range(B)], ctx.turns,
+                               [xps[b] for b in range(B)] if ctx.has_prev else None,
+                               [gxs[b] for b in range(B)], [Ybar[b] for b in range(B)],
+                               [xpb[b] for b in range(B)] if ctx.has_prev else None)
+        ga = torch.tensor(sum(a0), dtype=torch.float64, device=Ys.device)
         return Ybar, ga, xpb, None, None
 
 

@@ -7,6 +7,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 
 #include "cluster.cuh"
 #include "nlinv.h"
@@ -129,6 +130,11 @@ struct nlinv_plan_s {
   void* gmem = nullptr;
   float2 *gy = nullptr, *gxp = nullptr, *gx = nullptr, *grho = nullptr, *gimg = nullptr;
   float* gp = nullptr;
+  // reverse passes: one stream and completion event per frame of a batch
+  std::vector<cudaStream_t> vjp_st;
+  std::vector<cudaEvent_t> vjp_ev;
+  cudaEvent_t vjp_fork = nullptr;
+  double* vjp_host = nullptr;  // pinned: alpha0-bar and breakdown flags
   cudaStream_t aux = nullptr; // stream of this plan's group inside nlinv_batch
   cudaEvent_t ev_fork = nullptr, ev_done = nullptr;
 };

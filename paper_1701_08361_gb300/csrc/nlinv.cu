@@ -417,6 +417,10 @@ int nlinv_plan(nlinv_plan_t* out, const nlinv_params_t* p, const float* psf, nli
 
 int nlinv_plan_destroy(nlinv_plan_t pl) {
   if (!pl) return NLINV_EINVAL;
+  for (cudaStream_t s2 : pl->vjp_st) cudaStreamDestroy(s2);
+  for (cudaEvent_t e2 : pl->vjp_ev) cudaEventDestroy(e2);
+  if (pl->vjp_fork) cudaEventDestroy(pl->vjp_fork);
+  if (pl->vjp_host) cudaFreeHost(pl->vjp_host);
   if (pl->gexec) cudaGraphExecDestroy(pl->gexec);
   if (pl->gcap) cudaStreamDestroy(pl->gcap);
   cudaFree(pl->gmem);
@@ -879,7 +883,16 @@ extern "C" int nlinv_apply_normal_static(int N, int J, int Gc, double w_a, doubl
   char* base = (char*)base_v;
   cudaStream_t st = (cudaStream_t)stream;
 
+  // a plan view of the static array: the per-size operations read the sizes
+  // from the plan and the buffers from its Ctx
   nlinv_plan_s tmp;
+  tmp.N = N;
+  tmp.G = G;
+  tmp.Gc = Gc;
+  tmp.J = J;
+  tmp.U = 1;
+  tmp.nx = (long long)N * N + (long long)J * Gc * Gc;
+  tmp.psf = const_cast<float*>(psf);
   Ctx& C = tmp.C;
   std::memset(&C, 0, sizeof(C));
   C.N = N;
@@ -924,7 +937,10 @@ extern "C" int nlinv_apply_normal_static(int N, int J, int Gc, double w_a, doubl
 //     -> x-bar += DF(bbar)^H z - DF(x)^H P DF(x) bbar - alpha bbar
 //        Y-bar += DF(x) bbar,  alpha-bar -= <bbar, x - x_ref>_R,  x_ref-bar += alpha bbar
 // The CG of each Newton step is recomputed from its checkpoint x^_n and
-// reversed step by step; scalars are handled on the host in FP64.
+// reversed step by step; its scalars (the CG tape and the adjoint scalars)
+// are computed and kept on the device in FP64, so a frame's reverse pass is
+// issued without host synchronisation and frames of a batch run on their own
+// streams.
 namespace {
 
 // y = a x + b y  (a as a float pair; b == 0 overwrites y)
@@ -1034,6 +1050,125 @@ __global__ void k_dots_final(int np, const double* part, double* out) {
   if (l == 0) out[blockIdx.x] = a;
 }
 
+// y = s x + b y with s = mul * (*sp), a device FP64 scalar applied as a float pair
+__global__ void k_axpby_s(long long n, float2* y, const float2* x, const double* sp, double mul, float b) {
+  const double sv = mul * *sp;
+  const float hi = (float)sv, lo = (float)(sv - (double)hi);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float2 xv = x[i];
+    float2 base = make_float2(0.f, 0.f);
+    if (b != 0.f) {
+      const float2 yv = y[i];
+      base = make_float2(b * yv.x, b * yv.y);
+    }
+    y[i] = make_float2(fmaf(hi, xv.x, fmaf(lo, xv.x, base.x)), fmaf(hi, xv.y, fmaf(lo, xv.y, base.y)));
+  }
+}
+
+// Device scalars of one frame's reverse pass (FP64), offsets into one array:
+// the CG tape of the Newton step being reversed (rho_k = |r_k|^2, a_k,
+// beta_k, gamma_k = Re<p_k, A p_k>, act_k = 1 for a step CG executed), the
+// adjoint scalars rhobar_k, the eight inner products D of a reverse step,
+// the coefficients of its vector updates, and alpha-bar / alpha0-bar.
+struct VjpSlots {
+  int rho, a, beta, gamma, act, rhobar, D, co, ab, a0b, t1, t2, c0, err, total;
+  explicit VjpSlots(int K) {
+    int o = 0;
+    auto take = [&](int n) {
+      const int r = o;
+      o += n;
+      return r;
+    };
+    rho = take(K + 1);
+    a = take(K > 0 ? K : 1);
+    beta = take(K > 0 ? K : 1);
+    gamma = take(K > 0 ? K : 1);
+    act = take(K > 0 ? K : 1);
+    rhobar = take(K + 1);
+    D = take(kMaxDots);
+    co = take(8);
+    ab = take(1);
+    a0b = take(1);
+    t1 = take(1);
+    t2 = take(1);
+    c0 = take(1);
+    err = take(1);
+    total = o;
+  }
+};
+
+// CG step k of the recomputation: a_k = rho_k / gamma_k for an executed
+// step (rho_k > 0; a breakdown gamma_k <= 0 flags an error and stops), else 0
+__global__ void k_cg_a(double* sc, VjpSlots S, int k) {
+  const double rho = sc[S.rho + k], g = sc[S.gamma + k];
+  double act = rho > 0.0 ? 1.0 : 0.0;
+  if (act != 0.0 && !(g > 0.0 && isfinite(g))) {
+    sc[S.err] = 1.0;
+    act = 0.0;
+  }
+  sc[S.act + k] = act;
+  sc[S.a + k] = act != 0.0 ? rho / g : 0.0;
+}
+
+// beta_k = rho_{k+1} / rho_k for an executed step, else 0
+__global__ void k_cg_beta(double* sc, VjpSlots S, int k) {
+  sc[S.beta + k] = sc[S.act + k] != 0.0 ? sc[S.rho + k + 1] / sc[S.rho + k] : 0.0;
+}
+
+// Reverse of CG step k from its inner products D (see nlinv_frame_vjp):
+// the adjoint scalars and the coefficients of the step's vector updates
+//   co0: rbar += co0 pbar   co1: pb = co1 pbar   co2: rbar += co2 r_{k+1}
+//   co3: qbar = co3 rbar    co4: pb += co4 xb    co5: pb += co5 q, qbar += co5 p
+// For a step CG did not execute every update is the identity.
+__global__ void k_rev_step(double* sc, VjpSlots S, int k) {
+  double* co = sc + S.co;
+  if (sc[S.act + k] == 0.0) {
+    co[0] = 0.0;
+    co[1] = 1.0;
+    co[2] = co[3] = co[4] = co[5] = 0.0;
+    return;
+  }
+  const double* D = sc + S.D;
+  const double a = sc[S.a + k], beta = sc[S.beta + k], gamma = sc[S.gamma + k];
+  const double rk = sc[S.rho + k], rk1 = sc[S.rho + k + 1];
+  double* rhobar = sc + S.rhobar;
+  const double betabar = D[0];                     // p_{k+1} = r_{k+1} + beta p_k
+  rhobar[k + 1] += betabar / rk;                   // beta = rho_{k+1} / rho_k
+  rhobar[k] -= betabar * rk1 / (rk * rk);
+  const double c = 2.0 * rhobar[k + 1];            // rho_{k+1} = <r, r>
+  const double abar = -(D[1] + D[2] + c * D[3]) + D[4];   // r -= a q; x += a p
+  rhobar[k] += abar / gamma;                       // a = rho_k / gamma_k
+  const double gammabar = -abar * rk / (gamma * gamma);
+  sc[S.ab] += -a * (D[5] + D[0] + c * D[6]) + gammabar * D[7];
+  co[0] = 1.0;
+  co[1] = beta;
+  co[2] = c;
+  co[3] = -a;
+  co[4] = a;
+  co[5] = gammabar;
+}
+
+// end of a reverse Newton step: 2 rhobar_0 (p_0 = r_0 = b) ...
+__global__ void k_rev_c0(double* sc, VjpSlots S) { sc[S.c0] = 2.0 * sc[S.rhobar]; }
+// ... and alpha-bar -= <bbar, x - x_ref>, alpha0-bar += q^n alpha-bar
+__global__ void k_rev_alpha(double* sc, VjpSlots S, double qn) {
+  sc[S.ab] -= sc[S.t1] - sc[S.t2];
+  sc[S.a0b] += qn * sc[S.ab];
+}
+
+__global__ void k_fill(double* p, int n, double v) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = v;
+}
+
+// out[f] = sc_f[S.a0b], out[nf + f] = sc_f[S.err] for the frames of a batch
+__global__ void k_gather_vjp(int nf, const double* sc0, size_t stride, VjpSlots S, double* out) {
+  const int f = threadIdx.x;
+  if (f < nf) {
+    out[f] = sc0[f * stride + S.a0b];
+    out[nf + f] = sc0[f * stride + S.err];
+  }
+}
+
 // z <- s P z on [J][G][G]
 __global__ void k_psf_scale(int J, int G, float2* z, const float* __restrict__ P, float s) {
   const long long n = (long long)J * G * G, g2 = (long long)G * G;
@@ -1059,12 +1194,11 @@ __global__ void k_init_x(int nx, int NN, float2* x) {
 constexpr int kDotBlocks = 256;
 
 struct GradOps {
-  nlinv_plan_s* pl;
+  const nlinv_plan_s* pl;   // the plan, or a view of it on one frame workspace
   cudaStream_t st;
   const float* P;
   long long nx, nk;
   double* part;   // [kMaxDots][kDotBlocks]
-  double* dres;   // device scalars [kMaxDots]
   const GridOps* ops;
   // The plan's coil-map buffer holds W^-1 of lin's coil part when
   // coils_at == lin.  lin is the Newton step's checkpoint x^_n, which is not
@@ -1097,23 +1231,26 @@ struct GradOps {
     CK(cudaMemsetAsync(y, 0, (size_t)n * sizeof(float2), st));
     return NLINV_OK;
   }
+  // Re<u, v> into the device scalar *out (FP64; nothing is read back)
   int dot(const float2* u, const float2* v, long long n, double* out) const {
     k_dot_part<<<kDotBlocks, 256, 0, st>>>(n, u, v, part);
     CKL("k_dot_part");
-    k_dot_final<<<1, 32, 0, st>>>(kDotBlocks, part, dres);
+    k_dot_final<<<1, 32, 0, st>>>(kDotBlocks, part, out);
     CKL("k_dot_final");
-    CK(cudaMemcpyAsync(out, dres, sizeof(double), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
     return NLINV_OK;
   }
-  // kMaxDots products Re<u_j, v_j> with one read-back
+  // kMaxDots products Re<u_j, v_j> into the device scalars out[0..kMaxDots)
   int dots(const DotSet& S, double* out) const {
     k_dots_part<kMaxDots><<<kDotBlocks, 256, 0, st>>>(nx, S, part);
     CKL("k_dots_part");
-    k_dots_final<<<kMaxDots, 32, 0, st>>>(kDotBlocks, part, dres);
+    k_dots_final<<<kMaxDots, 32, 0, st>>>(kDotBlocks, part, out);
     CKL("k_dots_final");
-    CK(cudaMemcpyAsync(out, dres, kMaxDots * sizeof(double), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    return NLINV_OK;
+  }
+  // y = (mul * *s) x + b y with the device scalar s
+  int axpby_s(float2* y, const float2* x, const double* s, double mul, double b, long long n) const {
+    k_axpby_s<<<grid(n), 256, 0, st>>>(n, y, x, s, mul, (float)b);
+    CKL("k_axpby_s");
     return NLINV_OK;
   }
   // z = DF(x)[d]
@@ -1140,17 +1277,24 @@ struct GradOps {
 
 struct GradWS {
   float2 *ck, *b, *z, *zt, *zt2, *tp, *tq, *tr, *xb, *xbn, *pbar, *rbar, *qbar, *pb, *t1, *xref, *xrefbar, *xcg;
-  double *part, *dres;
+  double *part, *sc;
 };
 
-int grad_workspace(nlinv_plan_s* pl, GradWS& w) {
+// bytes of one frame's reverse-pass workspace (a multiple of 256)
+size_t grad_ws_bytes(const nlinv_plan_s* pl) {
   const int M = pl->prm.newton_steps, Kc = pl->prm.cg_iters;
   const size_t nx = (size_t)pl->nx, nk = (size_t)pl->J * pl->G * pl->G;
   const size_t vb = align_up(nx * sizeof(float2)), kb = align_up(nk * sizeof(float2));
-  const size_t need = vb * ((M + 1) + 1 + Kc + Kc + (Kc + 1) + 10) + 3 * kb +
-                      align_up((size_t)kMaxDots * (kDotBlocks + 1) * sizeof(double));
-  RC(ensure_prep(pl, need));
-  char* p = (char*)pl->prep;
+  const size_t kt = Kc > 0 ? Kc : 1;   // p_k and q_k tapes (one vector even without CG)
+  return vb * ((M + 1) + 1 + 2 * kt + (Kc + 1) + 10) + 3 * kb +
+         align_up((size_t)kMaxDots * kDotBlocks * sizeof(double)) +
+         align_up((size_t)VjpSlots(Kc).total * sizeof(double));
+}
+
+void grad_ws_carve(const nlinv_plan_s* pl, char* p, GradWS& w) {
+  const int M = pl->prm.newton_steps, Kc = pl->prm.cg_iters;
+  const size_t nx = (size_t)pl->nx, nk = (size_t)pl->J * pl->G * pl->G;
+  const size_t vb = align_up(nx * sizeof(float2)), kb = align_up(nk * sizeof(float2));
   auto vec = [&](size_t count) {
     float2* r = (float2*)p;
     p += vb * count;
@@ -1178,14 +1322,9 @@ int grad_workspace(nlinv_plan_s* pl, GradWS& w) {
   w.zt2 = (float2*)p;
   p += kb;
   w.part = (double*)p;
-  w.dres = w.part + (size_t)kMaxDots * kDotBlocks;
-  return NLINV_OK;
+  p += align_up((size_t)kMaxDots * kDotBlocks * sizeof(double));
+  w.sc = (double*)p;
 }
-
-struct CgTape {
-  int K = 0;
-  std::vector<double> a, beta, gamma, rho;
-};
 
 // b = DF(x)^H (Y - P F^(x)) - alpha (x - xref); leaves the residual in w.z
 int grad_rhs(const GradOps& O, const GradWS& w, const float2* Y, const float2* x, double alpha, float2* b) {
@@ -1196,46 +1335,162 @@ int grad_rhs(const GradOps& O, const GradWS& w, const float2* Y, const float2* x
   return O.axpby(b, w.xref, alpha, 1.0, O.nx);
 }
 
-// CG from zero recording p_k, q_k, r_k (k = 0..) and the scalars; delta in w.xcg
-int grad_cg(const GradOps& O, const GradWS& w, const float2* x, double alpha, const float2* b, int iters,
-            CgTape& T) {
+// CG from zero recording p_k, q_k, r_k and the tape scalars (device); the
+// step delta in w.xcg.  Every one of the `iters` steps is issued: a step
+// after an exactly zero residual has a_k = beta_k = 0 and leaves the vectors
+// unchanged (the host cannot see the residual without a read-back).
+int grad_cg(const GradOps& O, const GradWS& w, const VjpSlots& S, const float2* x, double alpha, const float2* b,
+            int iters) {
   const long long nx = O.nx;
-  T = CgTape();
+  double* sc = w.sc;
   float2* r0 = w.tr;
   RC(O.copy(r0, b, nx));
   RC(O.zero(w.xcg, nx));
-  double rr = 0.0;
-  RC(O.dot(r0, r0, nx, &rr));
-  T.rho.push_back(rr);
+  RC(O.dot(r0, r0, nx, sc + S.rho));
   if (iters > 0) RC(O.copy(w.tp, r0, nx));
   for (int k = 0; k < iters; ++k) {
-    if (rr == 0.0) break;
     float2* p = w.tp + (size_t)k * (size_t)nx;
     float2* q = w.tq + (size_t)k * (size_t)nx;
     float2* r = w.tr + (size_t)k * (size_t)nx;
     float2* r1 = w.tr + (size_t)(k + 1) * (size_t)nx;
     RC(O.normal(x, p, alpha, q));
-    double pq = 0.0;
-    RC(O.dot(p, q, nx, &pq));
-    if (!(pq > 0.0) || !std::isfinite(pq)) return NLINV_ENUMERIC;
-    const double a = rr / pq;
-    RC(O.axpby(w.xcg, p, a, 1.0, nx));
+    RC(O.dot(p, q, nx, sc + S.gamma + k));
+    k_cg_a<<<1, 1, 0, O.st>>>(sc, S, k);
+    CKL("k_cg_a");
+    RC(O.axpby_s(w.xcg, p, sc + S.a + k, 1.0, 1.0, nx));
     RC(O.copy(r1, r, nx));
-    RC(O.axpby(r1, q, -a, 1.0, nx));
-    double rn = 0.0;
-    RC(O.dot(r1, r1, nx, &rn));
-    const double beta = rn / rr;
-    T.a.push_back(a);
-    T.gamma.push_back(pq);
-    T.beta.push_back(beta);
-    T.rho.push_back(rn);
-    T.K = k + 1;
+    RC(O.axpby_s(r1, q, sc + S.a + k, -1.0, 1.0, nx));
+    RC(O.dot(r1, r1, nx, sc + S.rho + k + 1));
+    k_cg_beta<<<1, 1, 0, O.st>>>(sc, S, k);
+    CKL("k_cg_beta");
     if (k + 1 < iters) {
       float2* p1 = w.tp + (size_t)(k + 1) * (size_t)nx;
       RC(O.copy(p1, r1, nx));
-      RC(O.axpby(p1, p, beta, 1.0, nx));
+      RC(O.axpby_s(p1, p, sc + S.beta + k, 1.0, 1.0, nx));
     }
-    rr = rn;
+  }
+  return NLINV_OK;
+}
+
+// The whole reverse pass of one frame, issued on `st` without any host
+// synchronisation; alpha0-bar and a breakdown flag end up in w.sc.
+int vjp_issue(const nlinv_plan_s* view, cudaStream_t st, const GradWS& w, const float* P, const float2* Yd,
+              const float2* xprev, const float2* gbar, float2* Ybar, float2* xprev_bar) {
+  const nlinv_params_t& prm = view->prm;
+  const int M = prm.newton_steps, Kc = prm.cg_iters;
+  const VjpSlots S(Kc);
+  double* sc = w.sc;
+  GradOps O{view, st, P, view->nx, (long long)view->J * view->G * view->G, w.part, grid_ops(view->G, view->N)};
+  const long long nx = O.nx, nk = O.nk;
+  k_fill<<<1, 256, 0, st>>>(sc, S.total, 0.0);
+  CKL("k_fill");
+  // x^_0 and x_ref
+  if (xprev) {
+    RC(O.copy(w.ck, xprev, nx));
+  } else {
+    k_init_x<<<O.grid(nx), 256, 0, st>>>((int)nx, view->N * view->N, w.ck);
+    CKL("k_init_x");
+  }
+  RC(O.copy(w.xref, w.ck, nx));
+  RC(O.axpby(w.xref, w.xref, 0.0, prm.damping, nx));
+  // forward: checkpoints x^_n
+  for (int n = 0; n < M; ++n) {
+    const float2* x = w.ck + (size_t)n * (size_t)nx;
+    float2* x1 = w.ck + (size_t)(n + 1) * (size_t)nx;
+    const double alpha = prm.alpha0 * std::pow(prm.q, n);
+    O.lin = x;
+    RC(grad_rhs(O, w, Yd, x, alpha, w.b));
+    RC(grad_cg(O, w, S, x, alpha, w.b, Kc));
+    RC(O.copy(x1, x, nx));
+    RC(O.axpby(x1, w.xcg, 1.0, 1.0, nx));
+  }
+  // reverse
+  RC(O.zero(Ybar, nk));
+  RC(O.zero(w.xrefbar, nx));
+  RC(O.copy(w.xb, gbar, nx));
+  GradWS v = w;   // pbar / pb and xb / xbn swap roles as host pointers
+  for (int n = M - 1; n >= 0; --n) {
+    const float2* x = w.ck + (size_t)n * (size_t)nx;
+    const double alpha = prm.alpha0 * std::pow(prm.q, n);
+    O.lin = x;
+    RC(grad_rhs(O, v, Yd, x, alpha, v.b));            // residual z stays in v.z
+    RC(grad_cg(O, v, S, x, alpha, v.b, Kc));
+    RC(O.copy(v.xbn, v.xb, nx));                      // x^_{n+1} = x^_n + delta
+    RC(O.zero(v.pbar, nx));
+    RC(O.zero(v.rbar, nx));
+    k_fill<<<1, 256, 0, st>>>(sc + S.rhobar, Kc + 1, 0.0);
+    CKL("k_fill");
+    k_fill<<<1, 32, 0, st>>>(sc + S.ab, 1, 0.0);
+    CKL("k_fill");
+    const double* co = sc + S.co;
+    for (int k = Kc - 1; k >= 0; --k) {
+      const float2* p = v.tp + (size_t)k * (size_t)nx;
+      const float2* q = v.tq + (size_t)k * (size_t)nx;
+      const float2* r1 = v.tr + (size_t)(k + 1) * (size_t)nx;
+      // every inner product this step needs, from the vectors as they enter
+      // it (the updates below are linear in them):
+      //   D0 <p, pbar>  D1 <q, rbar>  D2 <q, pbar>  D3 <q, r1>
+      //   D4 <p, xb>    D5 <p, rbar>  D6 <p, r1>    D7 <p, p>
+      DotSet DS;
+      const float2* U[kMaxDots] = {p, q, q, q, p, p, p, p};
+      const float2* V[kMaxDots] = {v.pbar, v.rbar, v.pbar, r1, v.xb, v.rbar, r1, p};
+      for (int j = 0; j < kMaxDots; ++j) {
+        DS.u[j] = U[j];
+        DS.v[j] = V[j];
+      }
+      RC(O.dots(DS, sc + S.D));
+      k_rev_step<<<1, 1, 0, st>>>(sc, S, k);          // adjoint scalars, coefficients co
+      CKL("k_rev_step");
+      RC(O.axpby_s(v.rbar, v.pbar, co + 0, 1.0, 1.0, nx));   // p_{k+1} = r_{k+1} + beta p_k
+      RC(O.axpby_s(v.pb, v.pbar, co + 1, 1.0, 0.0, nx));
+      RC(O.axpby_s(v.rbar, r1, co + 2, 1.0, 1.0, nx));       // rho_{k+1} = <r, r>
+      RC(O.axpby_s(v.qbar, v.rbar, co + 3, 1.0, 0.0, nx));   // r_{k+1} = r_k - a q_k
+      RC(O.axpby_s(v.pb, v.xb, co + 4, 1.0, 1.0, nx));       // x_{k+1} = x_k + a p_k
+      RC(O.axpby_s(v.pb, q, co + 5, 1.0, 1.0, nx));          // gamma = <p, q>
+      RC(O.axpby_s(v.qbar, p, co + 5, 1.0, 1.0, nx));
+      RC(O.normal(x, v.qbar, alpha, v.t1));                  // q = A p
+      RC(O.axpby(v.pb, v.t1, 1.0, 1.0, nx));
+      // A depends on x^_n: both DF at x^_n first, while its coil maps are current
+      RC(O.DF(x, p, v.zt));
+      RC(O.psf(v.zt, 1.f));
+      RC(O.DF(x, v.qbar, v.zt2));
+      RC(O.psf(v.zt2, 1.f));
+      RC(O.DFH(v.qbar, v.zt, v.t1));
+      RC(O.axpby(v.xbn, v.t1, 1.0, 1.0, nx));
+      RC(O.DFH(p, v.zt2, v.t1));
+      RC(O.axpby(v.xbn, v.t1, 1.0, 1.0, nx));
+      std::swap(v.pbar, v.pb);
+    }
+    // p_0 = r_0 = b, rho_0 = <r_0, r_0>:  b-bar
+    RC(O.axpby(v.rbar, v.pbar, 1.0, 1.0, nx));
+    k_rev_c0<<<1, 1, 0, st>>>(sc, S);
+    CKL("k_rev_c0");
+    RC(O.axpby_s(v.rbar, v.tr, sc + S.c0, 1.0, 1.0, nx));
+    const float2* bbar = v.rbar;
+    // right-hand side
+    RC(O.DFH(bbar, v.z, v.t1));
+    RC(O.axpby(v.xbn, v.t1, 1.0, 1.0, nx));
+    RC(O.DF(x, bbar, v.zt));
+    k_axpby<<<O.grid(nk), 256, 0, st>>>(nk, Ybar, v.zt, 1.f, 0.f, 1.f);   // Y-bar += DF(x) b-bar
+    CKL("k_axpby");
+    RC(O.psf(v.zt, 1.f));
+    RC(O.DFH(x, v.zt, v.t1));
+    RC(O.axpby(v.xbn, v.t1, -1.0, 1.0, nx));
+    RC(O.axpby(v.xbn, bbar, -alpha, 1.0, nx));
+    RC(O.dot(bbar, x, nx, sc + S.t1));
+    RC(O.dot(bbar, v.xref, nx, sc + S.t2));
+    k_rev_alpha<<<1, 1, 0, st>>>(sc, S, std::pow(prm.q, n));
+    CKL("k_rev_alpha");
+    RC(O.axpby(v.xrefbar, bbar, alpha, 1.0, nx));
+    std::swap(v.xb, v.xbn);
+  }
+  if (xprev_bar) {
+    if (xprev) {
+      RC(O.copy(xprev_bar, v.xb, nx));
+      RC(O.axpby(xprev_bar, v.xrefbar, prm.damping, 1.0, nx));
+    } else {
+      RC(O.zero(xprev_bar, nx));
+    }
   }
   return NLINV_OK;
 }
@@ -1248,146 +1503,68 @@ extern "C" int nlinv_set_alpha0(nlinv_plan_t pl, double alpha0) {
   return NLINV_OK;
 }
 
+extern "C" int nlinv_batch_vjp(nlinv_plan_t pl, int nframes, const void* const* Y, const int* turns,
+                               const void* const* x_prev, const void* const* gbar, void* const* Ybar_out,
+                               double* alpha0_bar_out, void* const* xprev_bar_out, nlinv_stream_t stream) {
+  RC(check_plan(pl));
+  if (nframes <= 0 || nframes > pl->max_batch || !Y || !turns || !gbar || !Ybar_out) return NLINV_EINVAL;
+  for (int f = 0; f < nframes; ++f) {
+    if (!Y[f] || !gbar[f] || !Ybar_out[f] || !aligned8(Y[f]) || !aligned8(gbar[f]) || !aligned8(Ybar_out[f]))
+      return NLINV_EINVAL;
+    if ((x_prev && x_prev[f] && !aligned8(x_prev[f])) || (xprev_bar_out && xprev_bar_out[f] && !aligned8(xprev_bar_out[f])))
+      return NLINV_EINVAL;
+    if (turns[f] < 0 || turns[f] >= pl->U) return NLINV_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t wsb = grad_ws_bytes(pl);
+  RC(ensure_prep(pl, wsb * nframes + align_up(2 * kMaxBatch * sizeof(double))));
+  double* gather = (double*)((char*)pl->prep + wsb * nframes);
+  if (!pl->vjp_host) CK(cudaMallocHost(&pl->vjp_host, 2 * kMaxBatch * sizeof(double)));
+  if (!pl->vjp_fork) CK(cudaEventCreateWithFlags(&pl->vjp_fork, cudaEventDisableTiming));
+  while ((int)pl->vjp_st.size() < nframes) {
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t e2 = nullptr;
+    CK(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+    pl->vjp_st.push_back(s2);
+    CK(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
+    pl->vjp_ev.push_back(e2);
+  }
+  CK(cudaEventRecord(pl->vjp_fork, st));
+  // each frame on its own stream, workspace and reverse-pass slot
+  for (int f = 0; f < nframes; ++f) {
+    nlinv_plan_s view(*pl);
+    view.C = frame_ctx(pl->C, (size_t)f * pl->fstride);
+    GradWS w;
+    grad_ws_carve(pl, (char*)pl->prep + wsb * f, w);
+    cudaStream_t sf = pl->vjp_st[f];
+    CK(cudaStreamWaitEvent(sf, pl->vjp_fork, 0));
+    RC(vjp_issue(&view, sf, w, pl->psf + (size_t)turns[f] * pl->G * pl->G, (const float2*)Y[f],
+                 x_prev ? (const float2*)x_prev[f] : nullptr, (const float2*)gbar[f], (float2*)Ybar_out[f],
+                 xprev_bar_out ? (float2*)xprev_bar_out[f] : nullptr));
+    CK(cudaEventRecord(pl->vjp_ev[f], sf));
+    CK(cudaStreamWaitEvent(st, pl->vjp_ev[f], 0));
+  }
+  GradWS w0;
+  grad_ws_carve(pl, (char*)pl->prep, w0);
+  k_gather_vjp<<<1, 64, 0, st>>>(nframes, w0.sc, wsb / sizeof(double), VjpSlots(pl->prm.cg_iters), gather);
+  CKL("k_gather_vjp");
+  CK(cudaMemcpyAsync(pl->vjp_host, gather, 2 * nframes * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int f = 0; f < nframes; ++f)
+    if (pl->vjp_host[nframes + f] != 0.0) return NLINV_ENUMERIC;
+  if (alpha0_bar_out)
+    for (int f = 0; f < nframes; ++f) alpha0_bar_out[f] = pl->vjp_host[f];
+  return NLINV_OK;
+}
+
 extern "C" int nlinv_frame_vjp(nlinv_plan_t pl, const void* Y, int turn, const void* x_prev, const void* gbar,
                                void* Ybar_out, double* alpha0_bar_out, void* xprev_bar_out,
                                nlinv_stream_t stream) {
   RC(check_plan(pl));
-  if (!Y || !gbar || !Ybar_out || !aligned8(Y) || !aligned8(gbar) || !aligned8(Ybar_out)) return NLINV_EINVAL;
-  if ((x_prev && !aligned8(x_prev)) || (xprev_bar_out && !aligned8(xprev_bar_out))) return NLINV_EINVAL;
-  if (turn < 0 || turn >= pl->U) return NLINV_EINVAL;
-  const nlinv_params_t& prm = pl->prm;
-  const int M = prm.newton_steps, Kc = prm.cg_iters;
-  GradWS w;
-  RC(grad_workspace(pl, w));
-  GradOps O{pl, (cudaStream_t)stream, pl->psf + (size_t)turn * pl->G * pl->G, pl->nx,
-            (long long)pl->J * pl->G * pl->G, w.part, w.dres, grid_ops(pl->G, pl->N)};
-  const long long nx = O.nx, nk = O.nk;
-  const float2* Yd = (const float2*)Y;
-  // x^_0 and x_ref
-  if (x_prev) {
-    RC(O.copy(w.ck, (const float2*)x_prev, nx));
-  } else {
-    k_init_x<<<O.grid(nx), 256, 0, O.st>>>((int)nx, pl->N * pl->N, w.ck);
-    CKL("k_init_x");
-  }
-  RC(O.copy(w.xref, w.ck, nx));
-  RC(O.axpby(w.xref, w.xref, 0.0, prm.damping, nx));
-  // forward: checkpoints x^_n
-  CgTape T;
-  for (int n = 0; n < M; ++n) {
-    const float2* x = w.ck + (size_t)n * (size_t)nx;
-    float2* x1 = w.ck + (size_t)(n + 1) * (size_t)nx;
-    const double alpha = prm.alpha0 * std::pow(prm.q, n);
-    O.lin = x;
-    RC(grad_rhs(O, w, Yd, x, alpha, w.b));
-    RC(grad_cg(O, w, x, alpha, w.b, Kc, T));
-    RC(O.copy(x1, x, nx));
-    RC(O.axpby(x1, w.xcg, 1.0, 1.0, nx));
-  }
-  // reverse
-  float2* Ybar = (float2*)Ybar_out;
-  RC(O.zero(Ybar, nk));
-  RC(O.zero(w.xrefbar, nx));
-  RC(O.copy(w.xb, (const float2*)gbar, nx));
-  double a0bar = 0.0;
-  for (int n = M - 1; n >= 0; --n) {
-    const float2* x = w.ck + (size_t)n * (size_t)nx;
-    const double alpha = prm.alpha0 * std::pow(prm.q, n);
-    O.lin = x;
-    RC(grad_rhs(O, w, Yd, x, alpha, w.b));            // residual z stays in w.z
-    RC(grad_cg(O, w, x, alpha, w.b, Kc, T));
-    double alpha_bar = 0.0;
-    RC(O.copy(w.xbn, w.xb, nx));                      // x^_{n+1} = x^_n + delta
-    RC(O.zero(w.pbar, nx));
-    RC(O.zero(w.rbar, nx));
-    std::vector<double> rhobar(T.K + 1, 0.0);
-    for (int k = T.K - 1; k >= 0; --k) {
-      const float2* p = w.tp + (size_t)k * (size_t)nx;
-      const float2* q = w.tq + (size_t)k * (size_t)nx;
-      const float2* r1 = w.tr + (size_t)(k + 1) * (size_t)nx;
-      const double a = T.a[k], beta = T.beta[k], gamma = T.gamma[k];
-      const double rk = T.rho[k], rk1 = T.rho[k + 1];
-      // every inner product this step needs, from the vectors as they enter
-      // it (the updates below are linear in them): one read-back per step
-      //   D0 <p, pbar>  D1 <q, rbar>  D2 <q, pbar>  D3 <q, r1>
-      //   D4 <p, xb>    D5 <p, rbar>  D6 <p, r1>    D7 <p, p>
-      DotSet S;
-      const float2* U[kMaxDots] = {p, q, q, q, p, p, p, p};
-      const float2* V[kMaxDots] = {w.pbar, w.rbar, w.pbar, r1, w.xb, w.rbar, r1, p};
-      for (int j = 0; j < kMaxDots; ++j) {
-        S.u[j] = U[j];
-        S.v[j] = V[j];
-      }
-      double D[kMaxDots];
-      RC(O.dots(S, D));
-      RC(O.axpby(w.rbar, w.pbar, 1.0, 1.0, nx));      // p_{k+1} = r_{k+1} + beta p_k
-      const double betabar = D[0];
-      RC(O.copy(w.pb, w.pbar, nx));
-      RC(O.axpby(w.pb, w.pb, 0.0, beta, nx));
-      rhobar[k + 1] += betabar / rk;                  // beta = rho_{k+1} / rho_k
-      rhobar[k] -= betabar * rk1 / (rk * rk);
-      const double c = 2.0 * rhobar[k + 1];
-      RC(O.axpby(w.rbar, r1, c, 1.0, nx));            // rho_{k+1} = <r, r>
-      double abar = -(D[1] + D[2] + c * D[3]);        // r_{k+1} = r_k - a q_k
-      RC(O.copy(w.qbar, w.rbar, nx));
-      RC(O.axpby(w.qbar, w.qbar, 0.0, -a, nx));
-      abar += D[4];                                   // x_{k+1} = x_k + a p_k
-      RC(O.axpby(w.pb, w.xb, a, 1.0, nx));
-      rhobar[k] += abar / gamma;                      // a = rho_k / gamma_k
-      const double gammabar = -abar * rk / (gamma * gamma);
-      RC(O.axpby(w.pb, q, gammabar, 1.0, nx));        // gamma = <p, q>
-      RC(O.axpby(w.qbar, p, gammabar, 1.0, nx));
-      RC(O.normal(x, w.qbar, alpha, w.t1));           // q = A p
-      RC(O.axpby(w.pb, w.t1, 1.0, 1.0, nx));
-      // A depends on alpha and x^_n: <p, qbar>, qbar = -a rbar' + gammabar p
-      alpha_bar += -a * (D[5] + D[0] + c * D[6]) + gammabar * D[7];
-      // both DF at x^_n first, while its coil maps are current
-      RC(O.DF(x, p, w.zt));
-      RC(O.psf(w.zt, 1.f));
-      RC(O.DF(x, w.qbar, w.zt2));
-      RC(O.psf(w.zt2, 1.f));
-      RC(O.DFH(w.qbar, w.zt, w.t1));
-      RC(O.axpby(w.xbn, w.t1, 1.0, 1.0, nx));
-      RC(O.DFH(p, w.zt2, w.t1));
-      RC(O.axpby(w.xbn, w.t1, 1.0, 1.0, nx));
-      std::swap(w.pbar, w.pb);
-    }
-    // p_0 = r_0 = b, rho_0 = <r_0, r_0>:  b-bar
-    RC(O.axpby(w.rbar, w.pbar, 1.0, 1.0, nx));
-    RC(O.axpby(w.rbar, w.tr, 2.0 * rhobar[0], 1.0, nx));
-    const float2* bbar = w.rbar;
-    // right-hand side
-    RC(O.DFH(bbar, w.z, w.t1));
-    RC(O.axpby(w.xbn, w.t1, 1.0, 1.0, nx));
-    RC(O.DF(x, bbar, w.zt));
-    {  // Y-bar += DF(x) b-bar
-      const float hi = 1.f;
-      k_axpby<<<O.grid(nk), 256, 0, O.st>>>(nk, Ybar, w.zt, hi, 0.f, 1.f);
-      CKL("k_axpby");
-    }
-    RC(O.psf(w.zt, 1.f));
-    RC(O.DFH(x, w.zt, w.t1));
-    RC(O.axpby(w.xbn, w.t1, -1.0, 1.0, nx));
-    RC(O.axpby(w.xbn, bbar, -alpha, 1.0, nx));
-    double t1 = 0.0, t2 = 0.0;
-    RC(O.dot(bbar, x, nx, &t1));
-    RC(O.dot(bbar, w.xref, nx, &t2));
-    alpha_bar -= (t1 - t2);
-    a0bar += std::pow(prm.q, n) * alpha_bar;
-    RC(O.axpby(w.xrefbar, bbar, alpha, 1.0, nx));
-    std::swap(w.xb, w.xbn);
-  }
-  if (alpha0_bar_out) *alpha0_bar_out = a0bar;
-  if (xprev_bar_out) {
-    if (x_prev) {
-      RC(O.copy((float2*)xprev_bar_out, w.xb, nx));
-      RC(O.axpby((float2*)xprev_bar_out, w.xrefbar, prm.damping, 1.0, nx));
-    } else {
-      RC(O.zero((float2*)xprev_bar_out, nx));
-    }
-  }
-  CK(cudaStreamSynchronize(O.st));
-  return NLINV_OK;
+  if (!Y || !gbar || !Ybar_out) return NLINV_EINVAL;
+  const void* xp = x_prev;
+  void* xb = xprev_bar_out;
+  return nlinv_batch_vjp(pl, 1, &Y, &turn, &xp, &gbar, &Ybar_out, alpha0_bar_out, &xb, stream);
 }
 
 #ifdef NLINV_TIMELINE

@@ -92,6 +92,7 @@ _SIGS = {
     "nlinv_wait_flag": (_I, [_VP, _VP, _I, ctypes.c_longlong, _VP]),
     "nlinv_set_alpha0": (_I, [_VP, ctypes.c_double]),
     "nlinv_frame_vjp": (_I, [_VP, _VP, _I, _VP, _VP, _VP, ctypes.POINTER(ctypes.c_double), _VP, _VP]),
+    "nlinv_batch_vjp": (_I, [_VP, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "nlinv_sync": (_I, [_VP, _VP]),
     "nlinv_strerror": (ctypes.c_char_p, [_I]),
     "nlinv_last_cuda_error": (ctypes.c_char_p, []),
@@ -368,6 +369,25 @@ def nlinv_frame_vjp(plan: Plan, Y, turn: int, x_prev, gbar, Ybar_out, xprev_bar_
                                   ctypes.byref(a0), _ptr(xprev_bar_out, numel=plan.nx, name="xprev_bar_out"),
                                   _stream(stream)), "nlinv_frame_vjp")
     return a0.value
+
+
+def nlinv_batch_vjp(plan: Plan, Ys, turns, x_prevs, gbars, Ybars, xprev_bars=None, stream=None):
+    """nlinv_frame_vjp of several frames (lists of device tensors; x_prevs or
+    xprev_bars may be None or hold None entries); returns the list of
+    dL/dalpha_0 per frame."""
+    B = len(Ys)
+    nk = plan.J * plan.G * plan.G
+    VP = ctypes.c_void_p * B
+    Y = VP(*[_ptr(y, numel=nk, name="Y") for y in Ys])
+    T = (ctypes.c_int * B)(*[int(t) for t in turns])
+    XP = VP(*[_ptr(x, numel=plan.nx, name="x_prev") for x in x_prevs]) if x_prevs is not None else None
+    GB = VP(*[_ptr(g, numel=plan.nx, name="gbar") for g in gbars])
+    YB = VP(*[_ptr(y, numel=nk, name="Ybar") for y in Ybars])
+    XB = VP(*[_ptr(x, numel=plan.nx, name="xprev_bar") for x in xprev_bars]) if xprev_bars is not None else None
+    a0 = (ctypes.c_double * B)()
+    _check(_lib().nlinv_batch_vjp(plan.handle, B, Y, T, XP, GB, YB, a0, XB, _stream(stream)),
+           "nlinv_batch_vjp")
+    return list(a0)
 
 
 def nlinv_wait_flag(plan: Plan, flag, expected: int, spin_limit: int, stream=None):
