@@ -166,6 +166,13 @@ int nlinv_grid(nlinv_plan_t plan, int S, const double* kxy, const void* y, void*
 int nlinv_grid_nufft(nlinv_plan_t plan, int S, const double* kxy, const void* y, int W, void* Y_out,
                      nlinv_stream_t stream);
 
+/* Temporal median filter of the post-processing stage (Sec. 3.1): for a
+ * window of T consecutive images (T odd, 1..15; imgs: host array of T
+ * device pointers to complex64 [n], e.g. the img_out of T frames),
+ * out[i] = the median of |img_t[i]| over t (device float [n]).  One launch,
+ * asynchronous on `stream`; needs no plan. */
+int nlinv_median(const void* const* imgs, int T, long long n, float* out, nlinv_stream_t stream);
+
 /* DF at x^_n applied to dx (Eq. 5 before the PSF):
  *   z_j = U pad_N(c_j drho + rho W^-1 dc^_j),  c_j = W^-1 c^_j of x^_n.
  * xhat, dx: device complex64 [n_x]; z: device complex64 [J][G][G]. */

@@ -450,3 +450,15 @@ def grid_data_kb(kx: np.ndarray, ky: np.ndarray, y: np.ndarray, N: int, G: int, 
     dap = kb_ft((np.arange(N, dtype=np.float64) - c) / G, W, beta)
     img = z / (2 * N * dap[:, None] * dap[None, :])[None]
     return fft2u(pad_img(img, G))
+
+
+# ---------------------------------------------------------------------------
+# post-processing (Sec. 3.1): temporal median filter of the displayed images
+# ---------------------------------------------------------------------------
+
+def temporal_median(imgs: np.ndarray) -> np.ndarray:
+    """Pixel-wise median over a window of T (odd) consecutive frames of the
+    magnitude images |rho ||c|||: imgs [T, ...] complex -> [...] real."""
+    imgs = np.asarray(imgs)
+    assert imgs.shape[0] % 2 == 1, "odd window"
+    return np.median(np.abs(imgs), axis=0)

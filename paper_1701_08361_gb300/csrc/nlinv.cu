@@ -41,6 +41,43 @@ const GridOps* grid_ops(int G, int N) {
 
 namespace {
 
+// ------------------------------------------------ temporal median filter
+// out[i] = median over the window of |img_t[i]| (T odd, T <= kMaxMedian):
+// one thread per pixel, the T magnitudes sorted in registers (insertion
+// sort over compile-time-bounded loops)
+constexpr int kMaxMedian = 15;
+struct MedianWindow {
+  const float2* img[kMaxMedian];
+};
+__global__ void k_median(int T, long long n, MedianWindow W, float* out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    float v[kMaxMedian];
+#pragma unroll
+    for (int t = 0; t < kMaxMedian; ++t) {
+      if (t < T) {
+        const float2 z = W.img[t][i];
+        v[t] = sqrtf(z.x * z.x + z.y * z.y);
+      }
+    }
+#pragma unroll
+    for (int a = 1; a < kMaxMedian; ++a) {
+      if (a < T) {
+#pragma unroll
+        for (int b = a; b > 0; --b) {
+          const float lo = fminf(v[b - 1], v[b]), hi = fmaxf(v[b - 1], v[b]);
+          v[b - 1] = lo;
+          v[b] = hi;
+        }
+      }
+    }
+    float m = v[0];
+#pragma unroll
+    for (int t = 0; t < kMaxMedian; ++t)
+      if (t == T / 2) m = v[t];
+    out[i] = m;
+  }
+}
+
 // ------------------------------------------- convolution gridding (NUFFT)
 // Kaiser-Bessel gridding of the preprocessing stage (Sec. 3.1): kernel
 // phi(u) = I0(beta sqrt(1 - (2u/W)^2)) on W grid points, modulated by the
@@ -535,6 +572,22 @@ int nlinv_grid_nufft(nlinv_plan_t pl, int S, const double* kxy, const void* y, i
   k_kb_spread<<<(int)((nt + 255) / 256), 256, 0, st>>>(S, J, G, W, (const float2*)y, w, f0, Z);
   CKL("k_kb_spread");
   return grid_ops(pl->G, pl->N)->grid_kb(pl, st, Z, dap, (float)((double)G / (2.0 * N)), (float2*)Y_out);
+}
+
+int nlinv_median(const void* const* imgs, int T, long long n, float* out, nlinv_stream_t stream) {
+  if (!imgs || !out || n <= 0 || T < 1 || T > kMaxMedian || (T % 2) == 0 || ((uintptr_t)out & 3u))
+    return NLINV_EINVAL;
+  MedianWindow W;
+  std::memset(&W, 0, sizeof(W));
+  for (int t = 0; t < T; ++t) {
+    if (!imgs[t] || !aligned8(imgs[t])) return NLINV_EINVAL;
+    W.img[t] = (const float2*)imgs[t];
+  }
+  long long g = (n + 255) / 256;
+  if (g > 4096) g = 4096;
+  k_median<<<(int)g, 256, 0, (cudaStream_t)stream>>>(T, n, W, out);
+  CKL("k_median");
+  return NLINV_OK;
 }
 
 int nlinv_apply_DF(nlinv_plan_t pl, const void* xhat, const void* dx, void* z, nlinv_stream_t stream) {

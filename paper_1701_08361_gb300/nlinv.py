@@ -79,6 +79,7 @@ _SIGS = {
     "nlinv_psf": (_I, [_VP, _I, _I, _VP, _VP, _VP]),
     "nlinv_grid": (_I, [_VP, _I, _VP, _VP, _VP, _VP]),
     "nlinv_grid_nufft": (_I, [_VP, _I, _VP, _VP, _I, _VP, _VP]),
+    "nlinv_median": (_I, [_VP, _I, ctypes.c_longlong, _VP, _VP]),
     "nlinv_apply_DF": (_I, [_VP, _VP, _VP, _VP, _VP]),
     "nlinv_apply_DFH": (_I, [_VP, _VP, _VP, _VP, _VP]),
     "nlinv_apply_normal": (_I, [_VP, _VP, _VP, _I, ctypes.c_double, _VP, _VP]),
@@ -236,6 +237,16 @@ def nlinv_grid_nufft(plan: Plan, kxy, y, W: int, Y_out, stream=None):
                                    _ptr(y, numel=plan.J * S, name="y"), int(W),
                                    _ptr(Y_out, numel=plan.J * plan.G * plan.G, name="Y_out"),
                                    _stream(stream)), "nlinv_grid_nufft")
+
+
+def nlinv_median(imgs, out, stream=None):
+    """Pixel-wise median of |img| over the window `imgs` (list of an odd
+    number of complex64 device tensors of equal size) into the float32
+    device tensor `out`."""
+    n = out.numel()
+    T = len(imgs)
+    arr = (ctypes.c_void_p * max(1, T))(*[_ptr(t, numel=n, name="img") for t in imgs])
+    _check(_lib().nlinv_median(arr, T, n, _ptr(out, torch.float32, n, "out"), _stream(stream)), "nlinv_median")
 
 
 def nlinv_apply_DF(plan: Plan, xhat, dx, z, stream=None):

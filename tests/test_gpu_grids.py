@@ -150,3 +150,26 @@ def test_autotuner_record_and_pick():
     L.nlinv_frame(plan, to_dev(Y), 0, None, x)
     assert L.nlinv_sync(plan) == 0
     assert rel(to_np(x), ref.flat()) <= 1e-3
+
+
+@pytest.mark.parametrize("T,n", [(1, 1000), (3, 25600), (5, 65536), (15, 777)])
+def test_temporal_median_matches_oracle(T, n):
+    """nlinv_median (post-processing, Sec. 3.1) against the oracle's
+    pixel-wise median of the magnitudes, on images with outlier frames."""
+    from paper_1701_08361_gb300 import nlinv as L
+    imgs = S.random_complex((T, n), 500 + T)
+    imgs[T // 2, ::7] *= 50.0                 # outliers the median must reject
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    L.nlinv_median([to_dev(imgs[t]) for t in range(T)], out)
+    torch.cuda.synchronize()
+    want = O.temporal_median(imgs.astype(np.complex64).astype(np.complex128))
+    assert np.max(np.abs(to_np(out) - want) / np.maximum(want, 1e-30)) <= 1e-6
+
+
+def test_temporal_median_rejects_even_or_long_windows():
+    from paper_1701_08361_gb300 import nlinv as L
+    a = torch.zeros(16, dtype=torch.complex64, device="cuda")
+    out = torch.empty(16, dtype=torch.float32, device="cuda")
+    for T in (2, 17):
+        with pytest.raises(L.NlinvError):
+            L.nlinv_median([a] * T, out)
