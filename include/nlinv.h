@@ -69,10 +69,9 @@ typedef struct {
   double w_a, w_l;    /* Sobolev weight constants (220, 32) */
   long long spin_limit; /* polls before a device-side wait gives up; 0 -> default */
   int exec_mode;      /* how nlinv_frame runs a frame:
-                         0: default -- the grid kernel (2), which measured
-                            faster than the cluster kernel (3) on the
-                            configurations' sizes; the tuner (tune.py)
-                            records which is faster per size;
+                         0: default -- the CUDA graph of 4, which measured
+                            fastest on the configurations' sizes (the tuner,
+                            tune.py, records the fastest per size);
                          1: one launch per phase (unfused comparator);
                          2: one persistent cooperative launch, CTAs
                             synchronised by grid barriers between phases;
@@ -107,8 +106,8 @@ typedef struct {
 int nlinv_grid_list(int* G_out, int* N_out, int cap);
 
 /* Fill `p` with the defaults for an N x N image and J channels:
- * Gc = G/4, 7 Newton steps x 10 CG, alpha0 = 1, q = 1/2, damping 1,
- * w_a = 220, w_l = 32, one turn, persistent execution. */
+ * G = 2N, Gc = G/4, 7 Newton steps x 10 CG, alpha0 = 1, q = 1/2, damping 1,
+ * w_a = 220, w_l = 32, one turn, the default execution (exec_mode 0). */
 int nlinv_default_params(nlinv_params_t* p, int N, int J);
 
 /* Create a plan (Sec. 2.2, Fig. 4 set-up: twiddles, D_W^-1 table, PSFs,
@@ -340,7 +339,10 @@ int nlinv_frame_vjp(nlinv_plan_t plan, const void* Y, int turn, const void* x_pr
  * entry NULL: not wanted), host ints turns[f]; alpha0_bar_out: host double
  * [nframes] (or NULL).  Each frame's reverse pass runs on its own stream and
  * frame workspace of the plan, forked from and joined back into `stream`;
- * the call returns once all are complete. */
+ * the call returns once all are complete.  A slot's reverse pass is captured
+ * into a CUDA graph on its first use (and again when alpha_0, the turn or the
+ * presence of x_prev / xprev_bar_out change) and replayed through the slot's
+ * staging buffers; do not call while the calling thread captures a stream. */
 int nlinv_batch_vjp(nlinv_plan_t plan, int nframes, const void* const* Y, const int* turns,
                     const void* const* x_prev, const void* const* gbar, void* const* Ybar_out,
                     double* alpha0_bar_out, void* const* xprev_bar_out, nlinv_stream_t stream);

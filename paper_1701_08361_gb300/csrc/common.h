@@ -130,11 +130,21 @@ struct nlinv_plan_s {
   void* gmem = nullptr;
   float2 *gy = nullptr, *gxp = nullptr, *gx = nullptr, *grho = nullptr, *gimg = nullptr;
   float* gp = nullptr;
-  // reverse passes: one stream and completion event per frame of a batch
+  // reverse passes: one stream, completion event, captured graph and staging
+  // buffers per frame slot of a batch, and their own workspace allocation
   std::vector<cudaStream_t> vjp_st;
   std::vector<cudaEvent_t> vjp_ev;
   cudaEvent_t vjp_fork = nullptr;
   double* vjp_host = nullptr;  // pinned: alpha0-bar and breakdown flags
+  void* vjp_mem = nullptr;     // slots' workspaces, then the gather area
+  size_t vjp_bytes = 0;
+  struct VjpGraph {
+    cudaGraphExec_t exec = nullptr;
+    double alpha0 = 0.0;
+    int turn = -1, has_xprev = -1, want_xprev_bar = -1;
+    void* stage = nullptr;     // Y, Y-bar [J][G][G]; gbar, x_prev, x_prev-bar [n_x]
+  };
+  std::vector<VjpGraph> vjp_graphs;
   cudaStream_t aux = nullptr; // stream of this plan's group inside nlinv_batch
   cudaEvent_t ev_fork = nullptr, ev_done = nullptr;
 };

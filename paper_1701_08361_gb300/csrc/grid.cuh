@@ -673,7 +673,7 @@ struct Ops {
       CK(cudaLaunchKernelEx(&cfg, k_frame_cl<K>, C, F, pl->cl_lay));
       return NLINV_OK;
     }
-    if (mode == 0 || mode == 2) {
+    if (mode == 2) {
       CK(cudaMemsetAsync(C.bar, 0, 2 * sizeof(unsigned), st));
       FrameArgs Fa = F;
       void* args[] = {(void*)&C, (void*)&Fa};
@@ -681,7 +681,7 @@ struct Ops {
                                      (size_t)K::SMEM, st));
       return NLINV_OK;
     }
-    if (mode == 4) return frame_graph(const_cast<nlinv_plan_s*>(pl), st, F);
+    if (mode == 0 || mode == 4) return frame_graph(const_cast<nlinv_plan_s*>(pl), st, F);
     return per_phase(pl, st, F, false);
   }
 

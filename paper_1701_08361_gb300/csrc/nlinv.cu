@@ -454,6 +454,11 @@ int nlinv_plan(nlinv_plan_t* out, const nlinv_params_t* p, const float* psf, nli
 
 int nlinv_plan_destroy(nlinv_plan_t pl) {
   if (!pl) return NLINV_EINVAL;
+  for (auto& g : pl->vjp_graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    cudaFree(g.stage);
+  }
+  cudaFree(pl->vjp_mem);
   for (cudaStream_t s2 : pl->vjp_st) cudaStreamDestroy(s2);
   for (cudaEvent_t e2 : pl->vjp_ev) cudaEventDestroy(e2);
   if (pl->vjp_fork) cudaEventDestroy(pl->vjp_fork);
@@ -481,7 +486,7 @@ int nlinv_plan_sizes(nlinv_plan_t pl, long long* nx, int* G, int* Gc) {
 int nlinv_plan_path(nlinv_plan_t pl, int* exec_path, int* cluster_size) {
   RC(check_plan(pl));
   const int m = pl->prm.exec_mode;
-  const int path = (m == 1 || m == 4) ? m : (m == 3 && pl->cl_cs > 0 ? 3 : 2);
+  const int path = m == 0 ? 4 : ((m == 1 || m == 4) ? m : (m == 3 && pl->cl_cs > 0 ? 3 : 2));
   if (exec_path) *exec_path = path;
   if (cluster_size) *cluster_size = path == 3 ? pl->cl_cs : 0;
   return NLINV_OK;
@@ -1570,8 +1575,21 @@ extern "C" int nlinv_batch_vjp(nlinv_plan_t pl, int nframes, const void* const* 
   }
   cudaStream_t st = (cudaStream_t)stream;
   const size_t wsb = grad_ws_bytes(pl);
-  RC(ensure_prep(pl, wsb * nframes + align_up(2 * kMaxBatch * sizeof(double))));
-  double* gather = (double*)((char*)pl->prep + wsb * nframes);
+  const size_t need = wsb * nframes + align_up(2 * kMaxBatch * sizeof(double));
+  if (pl->vjp_bytes < need) {   // a new workspace: every captured reverse pass is stale
+    for (auto& g : pl->vjp_graphs)
+      if (g.exec) {
+        cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
+      }
+    if (pl->vjp_mem) CK(cudaFree(pl->vjp_mem));
+    pl->vjp_mem = nullptr;
+    pl->vjp_bytes = 0;
+    CK(cudaMalloc(&pl->vjp_mem, need));
+    pl->vjp_bytes = need;
+  }
+  char* wbase = (char*)pl->vjp_mem;
+  double* gather = (double*)(wbase + wsb * nframes);
   if (!pl->vjp_host) CK(cudaMallocHost(&pl->vjp_host, 2 * kMaxBatch * sizeof(double)));
   if (!pl->vjp_fork) CK(cudaEventCreateWithFlags(&pl->vjp_fork, cudaEventDisableTiming));
   while ((int)pl->vjp_st.size() < nframes) {
@@ -1581,24 +1599,65 @@ extern "C" int nlinv_batch_vjp(nlinv_plan_t pl, int nframes, const void* const* 
     pl->vjp_st.push_back(s2);
     CK(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
     pl->vjp_ev.push_back(e2);
+    pl->vjp_graphs.emplace_back();
   }
+  const size_t nx = (size_t)pl->nx, nk = (size_t)pl->J * pl->G * pl->G;
+  const size_t sy = align_up(nk * sizeof(float2)), sx = align_up(nx * sizeof(float2));
   CK(cudaEventRecord(pl->vjp_fork, st));
-  // each frame on its own stream, workspace and reverse-pass slot
+  // each frame on its own stream, workspace and reverse-pass slot: the slot's
+  // reverse pass is captured once into a CUDA graph (no host synchronisation
+  // inside it) reading and writing the slot's staging buffers, and replayed
   for (int f = 0; f < nframes; ++f) {
-    nlinv_plan_s view(*pl);
-    view.C = frame_ctx(pl->C, (size_t)f * pl->fstride);
-    GradWS w;
-    grad_ws_carve(pl, (char*)pl->prep + wsb * f, w);
+    nlinv_plan_s::VjpGraph& vg = pl->vjp_graphs[f];
+    if (!vg.stage) CK(cudaMalloc(&vg.stage, 2 * sy + 3 * sx));
+    float2* sY = (float2*)vg.stage;
+    float2* sYbar = (float2*)((char*)vg.stage + sy);
+    float2* sg = (float2*)((char*)vg.stage + 2 * sy);
+    float2* sxp = (float2*)((char*)vg.stage + 2 * sy + sx);
+    float2* sxpb = (float2*)((char*)vg.stage + 2 * sy + 2 * sx);
+    const int has_xp = (x_prev && x_prev[f]) ? 1 : 0;
+    const int want_xpb = (xprev_bar_out && xprev_bar_out[f]) ? 1 : 0;
     cudaStream_t sf = pl->vjp_st[f];
+    if (!vg.exec || vg.alpha0 != pl->prm.alpha0 || vg.turn != turns[f] || vg.has_xprev != has_xp ||
+        vg.want_xprev_bar != want_xpb) {
+      if (vg.exec) {
+        cudaGraphExecDestroy(vg.exec);
+        vg.exec = nullptr;
+      }
+      nlinv_plan_s view(*pl);
+      view.C = frame_ctx(pl->C, (size_t)f * pl->fstride);
+      GradWS w;
+      grad_ws_carve(pl, wbase + wsb * f, w);
+      CK(cudaStreamBeginCapture(sf, cudaStreamCaptureModeThreadLocal));
+      const int rc = vjp_issue(&view, sf, w, pl->psf + (size_t)turns[f] * pl->G * pl->G, sY,
+                               has_xp ? sxp : nullptr, sg, sYbar, want_xpb ? sxpb : nullptr);
+      cudaGraph_t graph = nullptr;
+      const cudaError_t ec = cudaStreamEndCapture(sf, &graph);
+      if (rc != NLINV_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+      }
+      CK(ec);
+      const cudaError_t ei = cudaGraphInstantiate(&vg.exec, graph, 0);
+      cudaGraphDestroy(graph);
+      CK(ei);
+      vg.alpha0 = pl->prm.alpha0;
+      vg.turn = turns[f];
+      vg.has_xprev = has_xp;
+      vg.want_xprev_bar = want_xpb;
+    }
     CK(cudaStreamWaitEvent(sf, pl->vjp_fork, 0));
-    RC(vjp_issue(&view, sf, w, pl->psf + (size_t)turns[f] * pl->G * pl->G, (const float2*)Y[f],
-                 x_prev ? (const float2*)x_prev[f] : nullptr, (const float2*)gbar[f], (float2*)Ybar_out[f],
-                 xprev_bar_out ? (float2*)xprev_bar_out[f] : nullptr));
+    CK(cudaMemcpyAsync(sY, Y[f], nk * sizeof(float2), cudaMemcpyDeviceToDevice, sf));
+    CK(cudaMemcpyAsync(sg, gbar[f], nx * sizeof(float2), cudaMemcpyDeviceToDevice, sf));
+    if (has_xp) CK(cudaMemcpyAsync(sxp, x_prev[f], nx * sizeof(float2), cudaMemcpyDeviceToDevice, sf));
+    CK(cudaGraphLaunch(vg.exec, sf));
+    CK(cudaMemcpyAsync(Ybar_out[f], sYbar, nk * sizeof(float2), cudaMemcpyDeviceToDevice, sf));
+    if (want_xpb) CK(cudaMemcpyAsync(xprev_bar_out[f], sxpb, nx * sizeof(float2), cudaMemcpyDeviceToDevice, sf));
     CK(cudaEventRecord(pl->vjp_ev[f], sf));
     CK(cudaStreamWaitEvent(st, pl->vjp_ev[f], 0));
   }
   GradWS w0;
-  grad_ws_carve(pl, (char*)pl->prep, w0);
+  grad_ws_carve(pl, wbase, w0);
   k_gather_vjp<<<1, 64, 0, st>>>(nframes, w0.sc, wsb / sizeof(double), VjpSlots(pl->prm.cg_iters), gather);
   CKL("k_gather_vjp");
   CK(cudaMemcpyAsync(pl->vjp_host, gather, 2 * nframes * sizeof(double), cudaMemcpyDeviceToHost, st));
