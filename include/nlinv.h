@@ -316,19 +316,22 @@ int nlinv_set_alpha0(nlinv_plan_t plan, double alpha0);
 
 /* Reverse-mode derivative of nlinv_frame through the unrolled IRGNM / CG
  * (Sec. 2.2, Eqs. 2-5: every Newton step and CG iteration exactly as
- * computed, with the data-dependent step lengths), recomputing each Newton
- * step from its checkpoint x^_n.  With gbar = dL/dx^_M (device [n_x]; for
+ * computed, with the data-dependent step lengths).  A forward sweep records
+ * every Newton step (checkpoint x^_n, residual, the CG vectors p_k, q_k, r_k)
+ * in the workspace and the reverse sweep reads that record: per frame
+ * (M + 1 + M (3 K + 1) + 13) n_x + (M + 2) J G^2 complex64 values, ~0.24 GB
+ * at N = 160, J = 10, G = 320, M = 7, K = 10.  With gbar = dL/dx^_M (device [n_x]; for
  * complex vectors the gradient of a real L is dL/dRe + i dL/dIm):
  *   Ybar_out       device [J][G][G] complex64: dL/dY
  *   alpha0_bar_out host double: dL/dalpha_0 (alpha_n = alpha0 q^n), or NULL
  *   xprev_bar_out  device [n_x]: dL/dx_prev through the initial value and
  *                  the regulariser x_ref = damping x_prev, or NULL (zero
  *                  when x_prev is NULL).
- * Y, turn and x_prev as in nlinv_frame.  The scalars of the recomputed CG
+ * Y, turn and x_prev as in nlinv_frame.  The scalars of the recorded CG
  * and of its reverse stay on the device (FP64); the call reads alpha0-bar
  * back once at the end, so it returns after the work on `stream` is
  * complete.  Uses a plan-owned workspace that is allocated on first use.
- * Returns NLINV_ENUMERIC if the recomputed CG breaks down. */
+ * Returns NLINV_ENUMERIC if the recorded CG breaks down. */
 int nlinv_frame_vjp(nlinv_plan_t plan, const void* Y, int turn, const void* x_prev,
                     const void* gbar, void* Ybar_out, double* alpha0_bar_out,
                     void* xprev_bar_out, nlinv_stream_t stream);

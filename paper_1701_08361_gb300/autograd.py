@@ -2,8 +2,9 @@
 
 Forward runs nlinv_frame / nlinv_batch; backward runs nlinv_frame_vjp /
 nlinv_batch_vjp, the hand-written reverse pass through the unrolled IRGNM /
-CG (Sec. 2.2, Eqs. 2-5) with per-Newton-step recomputation (the frames of a
-batch on their own streams).  Differentiable inputs: the
+CG (Sec. 2.2, Eqs. 2-5): one forward sweep records every Newton step's CG
+in device memory, the reverse sweep reads it (the frames of a batch on their
+own streams).  Differentiable inputs: the
 gridded data Y (complex64), alpha_0 (0-d float64 tensor) and x_prev.
 Gradients follow torch's complex convention (dL/dRe + i dL/dIm).
 """

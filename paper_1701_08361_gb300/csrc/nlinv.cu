@@ -994,11 +994,13 @@ extern "C" int nlinv_apply_normal_static(int N, int J, int Gc, double w_a, doubl
 //   b(x) = DF(x)^H z - alpha (x - x_ref),  z = Y - P F^(x),  F^(x) = B(x, x) / 2
 //     -> x-bar += DF(bbar)^H z - DF(x)^H P DF(x) bbar - alpha bbar
 //        Y-bar += DF(x) bbar,  alpha-bar -= <bbar, x - x_ref>_R,  x_ref-bar += alpha bbar
-// The CG of each Newton step is recomputed from its checkpoint x^_n and
-// reversed step by step; its scalars (the CG tape and the adjoint scalars)
-// are computed and kept on the device in FP64, so a frame's reverse pass is
-// issued without host synchronisation and frames of a batch run on their own
-// streams.
+// A forward sweep records every Newton step: the checkpoint x^_n, the
+// residual z and the whole CG tape (p_k, q_k, r_k; 3 K + 1 vectors per step,
+// ~0.24 GB per frame at N = 160 with 10 channels), and the reverse sweep
+// reverses each CG step by step from that record.  All scalars (the CG tape
+// and the adjoint scalars) are computed and kept on the device in FP64, so a
+// frame's reverse pass is issued without host synchronisation and frames of
+// a batch run on their own streams.
 namespace {
 
 // y = a x + b y  (a as a float pair; b == 0 overwrites y)
@@ -1155,22 +1157,72 @@ struct VjpSlots {
   }
 };
 
-// CG step k of the recomputation: a_k = rho_k / gamma_k for an executed
-// step (rho_k > 0; a breakdown gamma_k <= 0 flags an error and stops), else 0
-__global__ void k_cg_a(double* sc, VjpSlots S, int k) {
-  const double rho = sc[S.rho + k], g = sc[S.gamma + k];
-  double act = rho > 0.0 ? 1.0 : 0.0;
-  if (act != 0.0 && !(g > 0.0 && isfinite(g))) {
-    sc[S.err] = 1.0;
-    act = 0.0;
+// float pair (hi, lo) of an FP64 coefficient: hi + lo carries it to ~2^-48
+struct Coef {
+  float hi, lo;
+  __device__ explicit Coef(double v) : hi((float)v), lo((float)(v - (double)(float)v)) {}
+  // c * x + y, in the rounding order of k_axpby / k_axpby_s with b = 1
+  __device__ float2 fma2(float2 x, float2 y) const {
+    return make_float2(fmaf(hi, x.x, fmaf(lo, x.x, y.x)), fmaf(hi, x.y, fmaf(lo, x.y, y.y)));
   }
-  sc[S.act + k] = act;
-  sc[S.a + k] = act != 0.0 ? rho / g : 0.0;
+  // c * x (b = 0)
+  __device__ float2 mul2(float2 x) const {
+    return make_float2(fmaf(hi, x.x, fmaf(lo, x.x, 0.f)), fmaf(hi, x.y, fmaf(lo, x.y, 0.f)));
+  }
+};
+
+// block sum of an FP64 partial into part[blockIdx.x]
+__device__ __forceinline__ void block_partial(double acc, double* part) {
+  __shared__ double sw[32];
+  acc = warp_sum_f64(acc);
+  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += sw[w];
+    part[blockIdx.x] = a;
+  }
 }
 
-// beta_k = rho_{k+1} / rho_k for an executed step, else 0
-__global__ void k_cg_beta(double* sc, VjpSlots S, int k) {
-  sc[S.beta + k] = sc[S.act + k] != 0.0 ? sc[S.rho + k + 1] / sc[S.rho + k] : 0.0;
+// CG step k of the recorded forward sweep in one pass: a_k = rho_k / gamma_k
+// for an executed step (rho_k > 0; a breakdown gamma_k <= 0 flags an error
+// and stops), else 0 -- every block derives it, block 0 records it --, then
+// x += a_k p_k, r_{k+1} = r_k - a_k q_k and the per-block FP64 partials of
+// |r_{k+1}|^2.  Launched with kDotBlocks x 256 threads, so the partials are
+// those k_dot_part forms over r_{k+1}.
+__global__ void k_cg_step(long long n, double* sc, VjpSlots S, int k, float2* xcg, const float2* __restrict__ p,
+                          const float2* __restrict__ q, const float2* r, float2* r1, double* part) {
+  const double rho = sc[S.rho + k], g = sc[S.gamma + k];
+  double act = rho > 0.0 ? 1.0 : 0.0;
+  const bool broke = act != 0.0 && !(g > 0.0 && isfinite(g));
+  if (broke) act = 0.0;
+  const double a = act != 0.0 ? rho / g : 0.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (broke) sc[S.err] = 1.0;
+    sc[S.act + k] = act;
+    sc[S.a + k] = a;
+  }
+  const Coef ca(a), cn(-a);
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    xcg[i] = ca.fma2(p[i], xcg[i]);
+    const float2 rv = cn.fma2(q[i], r[i]);
+    r1[i] = rv;
+    acc = fma((double)rv.x, (double)rv.x, fma((double)rv.y, (double)rv.y, acc));
+  }
+  block_partial(acc, part);
+}
+
+// beta_k = rho_{k+1} / rho_k for an executed step, else 0 (block 0 records
+// it) and, when p1 is given, the next direction p_{k+1} = r_{k+1} + beta_k p_k
+__global__ void k_cg_dir(long long n, double* sc, VjpSlots S, int k, float2* p1, const float2* __restrict__ r1,
+                         const float2* __restrict__ p) {
+  const double beta = sc[S.act + k] != 0.0 ? sc[S.rho + k + 1] / sc[S.rho + k] : 0.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) sc[S.beta + k] = beta;
+  if (!p1) return;
+  const Coef cb(beta);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    p1[i] = cb.fma2(p[i], r1[i]);
 }
 
 // Reverse of CG step k from its inner products D (see nlinv_frame_vjp):
@@ -1206,6 +1258,40 @@ __global__ void k_rev_step(double* sc, VjpSlots S, int k) {
   co[5] = gammabar;
 }
 
+// the vector updates of reverse CG step k with the coefficients co of
+// k_rev_step, in the order (and rounding) of seven k_axpby_s passes:
+//   rbar += co0 pbar;  pb = co1 pbar;  rbar += co2 r1;  qbar = co3 rbar;
+//   pb += co4 xb;  pb += co5 q;  qbar += co5 p
+__global__ void k_rev_update(long long n, const double* __restrict__ co, float2* rbar, const float2* __restrict__ pbar,
+                             float2* pb, const float2* __restrict__ r1, float2* qbar, const float2* __restrict__ xb,
+                             const float2* __restrict__ q, const float2* __restrict__ p) {
+  const Coef c0(co[0]), c1(co[1]), c2(co[2]), c3(co[3]), c4(co[4]), c5(co[5]);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float2 pv = pbar[i];
+    float2 rv = c0.fma2(pv, rbar[i]);
+    float2 bv = c1.mul2(pv);
+    rv = c2.fma2(r1[i], rv);
+    float2 qv = c3.mul2(rv);
+    bv = c4.fma2(xb[i], bv);
+    bv = c5.fma2(q[i], bv);
+    qv = c5.fma2(p[i], qv);
+    rbar[i] = rv;
+    pb[i] = bv;
+    qbar[i] = qv;
+  }
+}
+
+// pb += t0;  xbn = (xbn + t1) + t2  (three k_axpby passes with a = b = 1)
+__global__ void k_rev_acc(long long n, float2* pb, const float2* __restrict__ t0, float2* xbn,
+                          const float2* __restrict__ t1, const float2* __restrict__ t2) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float2 a = pb[i], b = t0[i];
+    pb[i] = make_float2(a.x + b.x, a.y + b.y);
+    const float2 x = xbn[i], u = t1[i], v = t2[i];
+    xbn[i] = make_float2((x.x + u.x) + v.x, (x.y + u.y) + v.y);
+  }
+}
+
 // end of a reverse Newton step: 2 rhobar_0 (p_0 = r_0 = b) ...
 __global__ void k_rev_c0(double* sc, VjpSlots S) { sc[S.c0] = 2.0 * sc[S.rhobar]; }
 // ... and alpha-bar -= <bbar, x - x_ref>, alpha0-bar += q^n alpha-bar
@@ -1218,12 +1304,21 @@ __global__ void k_fill(double* p, int n, double v) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = v;
 }
 
-// out[f] = sc_f[S.a0b], out[nf + f] = sc_f[S.err] for the frames of a batch
-__global__ void k_gather_vjp(int nf, const double* sc0, size_t stride, VjpSlots S, double* out) {
+// Each Newton step n of a frame keeps its scalars in its own block of
+// S.total doubles.  out[f] = alpha0-bar of frame f, the sum of the blocks'
+// a0b in the order the reverse sweep reaches them (n = M-1 .. 0);
+// out[nf + f] = 1 if any block flagged a breakdown.
+__global__ void k_gather_vjp(int nf, int M, const double* sc0, size_t stride, VjpSlots S, double* out) {
   const int f = threadIdx.x;
   if (f < nf) {
-    out[f] = sc0[f * stride + S.a0b];
-    out[nf + f] = sc0[f * stride + S.err];
+    const double* sc = sc0 + f * stride;
+    double a = 0.0, e = 0.0;
+    for (int n = M - 1; n >= 0; --n) {
+      a += sc[(size_t)n * S.total + S.a0b];
+      if (sc[(size_t)n * S.total + S.err] != 0.0) e = 1.0;
+    }
+    out[f] = a;
+    out[nf + f] = e;
   }
 }
 
@@ -1232,6 +1327,16 @@ __global__ void k_psf_scale(int J, int G, float2* z, const float* __restrict__ P
   const long long n = (long long)J * G * G, g2 = (long long)G * G;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     z[i] = cscale(z[i], s * P[i % g2]);
+}
+
+// z1 <- s P z1, z2 <- s P z2 on [J][G][G]
+__global__ void k_psf_scale2(int J, int G, float2* z1, float2* z2, const float* __restrict__ P, float s) {
+  const long long n = (long long)J * G * G, g2 = (long long)G * G;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float pk = s * P[i % g2];
+    z1[i] = cscale(z1[i], pk);
+    z2[i] = cscale(z2[i], pk);
+  }
 }
 
 // z <- Y - s P z
@@ -1333,48 +1438,69 @@ struct GradOps {
   }
 };
 
+// One frame's reverse-pass workspace.  The forward sweep keeps, for every
+// Newton step n, its CG tape (p_k, q_k, r_k), its residual z = Y - P F(x^_n)
+// and its block of device scalars; at(n) points tp / tq / tr / z / sc at
+// step n's copies.  The other vectors are shared by the steps.
 struct GradWS {
-  float2 *ck, *b, *z, *zt, *zt2, *tp, *tq, *tr, *xb, *xbn, *pbar, *rbar, *qbar, *pb, *t1, *xref, *xrefbar, *xcg;
+  float2 *ck, *b, *z, *zt, *zt2, *tp, *tq, *tr, *xb, *xbn, *pbar, *rbar, *qbar, *pb, *t0, *t1, *t2, *xref,
+      *xrefbar, *xcg;
   double *part, *sc;
+  size_t vn = 0;                             // elements of one vector slot (256-byte aligned)
+  size_t spq = 0, sr = 0, sz = 0, ssc = 0;   // elements between two Newton steps' tapes / z / scalars
+  GradWS at(int n) const {
+    GradWS u = *this;
+    u.tp += (size_t)n * spq;
+    u.tq += (size_t)n * spq;
+    u.tr += (size_t)n * sr;
+    u.z += (size_t)n * sz;
+    u.sc += (size_t)n * ssc;
+    return u;
+  }
 };
 
-// bytes of one frame's reverse-pass workspace (a multiple of 256)
+// bytes of one frame's reverse-pass workspace (a multiple of 256): M + 1
+// checkpoints, M tapes of 2 kt + Kc + 1 vectors, 13 shared vectors, M + 2
+// k-space arrays, the dot partials and M scalar blocks
 size_t grad_ws_bytes(const nlinv_plan_s* pl) {
   const int M = pl->prm.newton_steps, Kc = pl->prm.cg_iters;
   const size_t nx = (size_t)pl->nx, nk = (size_t)pl->J * pl->G * pl->G;
   const size_t vb = align_up(nx * sizeof(float2)), kb = align_up(nk * sizeof(float2));
   const size_t kt = Kc > 0 ? Kc : 1;   // p_k and q_k tapes (one vector even without CG)
-  return vb * ((M + 1) + 1 + 2 * kt + (Kc + 1) + 10) + 3 * kb +
+  return vb * ((M + 1) + (size_t)M * (2 * kt + Kc + 1) + 13) + (M + 2) * kb +
          align_up((size_t)kMaxDots * kDotBlocks * sizeof(double)) +
-         align_up((size_t)VjpSlots(Kc).total * sizeof(double));
+         align_up((size_t)M * VjpSlots(Kc).total * sizeof(double));
 }
 
 void grad_ws_carve(const nlinv_plan_s* pl, char* p, GradWS& w) {
   const int M = pl->prm.newton_steps, Kc = pl->prm.cg_iters;
   const size_t nx = (size_t)pl->nx, nk = (size_t)pl->J * pl->G * pl->G;
   const size_t vb = align_up(nx * sizeof(float2)), kb = align_up(nk * sizeof(float2));
+  const size_t kt = Kc > 0 ? Kc : 1;
   auto vec = [&](size_t count) {
     float2* r = (float2*)p;
     p += vb * count;
     return r;
   };
   w.ck = vec(M + 1);
+  w.tp = vec(M * kt);
+  w.tq = vec(M * kt);
+  w.tr = vec((size_t)M * (Kc + 1));
   w.b = vec(1);
-  w.tp = vec(Kc > 0 ? Kc : 1);
-  w.tq = vec(Kc > 0 ? Kc : 1);
-  w.tr = vec(Kc + 1);
   w.xb = vec(1);
   w.xbn = vec(1);
   w.pbar = vec(1);
   w.rbar = vec(1);
   w.qbar = vec(1);
   w.pb = vec(1);
+  w.t0 = vec(1);
   w.t1 = vec(1);
+  w.t2 = vec(1);
   w.xref = vec(1);
   w.xrefbar = vec(1);
   w.xcg = vec(1);
   w.z = (float2*)p;
-  p += kb;
+  p += kb * M;
   w.zt = (float2*)p;
   p += kb;
   w.zt2 = (float2*)p;
@@ -1382,6 +1508,11 @@ void grad_ws_carve(const nlinv_plan_s* pl, char* p, GradWS& w) {
   w.part = (double*)p;
   p += align_up((size_t)kMaxDots * kDotBlocks * sizeof(double));
   w.sc = (double*)p;
+  w.vn = vb / sizeof(float2);
+  w.spq = kt * w.vn;
+  w.sr = (size_t)(Kc + 1) * w.vn;
+  w.sz = kb / sizeof(float2);
+  w.ssc = (size_t)VjpSlots(Kc).total;
 }
 
 // b = DF(x)^H (Y - P F^(x)) - alpha (x - xref); leaves the residual in w.z
@@ -1393,10 +1524,12 @@ int grad_rhs(const GradOps& O, const GradWS& w, const float2* Y, const float2* x
   return O.axpby(b, w.xref, alpha, 1.0, O.nx);
 }
 
-// CG from zero recording p_k, q_k, r_k and the tape scalars (device); the
-// step delta in w.xcg.  Every one of the `iters` steps is issued: a step
-// after an exactly zero residual has a_k = beta_k = 0 and leaves the vectors
-// unchanged (the host cannot see the residual without a read-back).
+// CG from zero recording p_k, q_k, r_k and the tape scalars (device) in w's
+// Newton-step copies; the step delta in w.xcg.  Every one of the `iters`
+// steps is issued: a step after an exactly zero residual has a_k = beta_k = 0
+// and leaves the vectors unchanged (the host cannot see the residual without
+// a read-back).  Per step: q = A p, <p, q>, one pass for a_k, x, r_{k+1} and
+// the partials of |r_{k+1}|^2, their sum, one pass for beta_k and p_{k+1}.
 int grad_cg(const GradOps& O, const GradWS& w, const VjpSlots& S, const float2* x, double alpha, const float2* b,
             int iters) {
   const long long nx = O.nx;
@@ -1407,40 +1540,37 @@ int grad_cg(const GradOps& O, const GradWS& w, const VjpSlots& S, const float2* 
   RC(O.dot(r0, r0, nx, sc + S.rho));
   if (iters > 0) RC(O.copy(w.tp, r0, nx));
   for (int k = 0; k < iters; ++k) {
-    float2* p = w.tp + (size_t)k * (size_t)nx;
-    float2* q = w.tq + (size_t)k * (size_t)nx;
-    float2* r = w.tr + (size_t)k * (size_t)nx;
-    float2* r1 = w.tr + (size_t)(k + 1) * (size_t)nx;
+    float2* p = w.tp + (size_t)k * w.vn;
+    float2* q = w.tq + (size_t)k * w.vn;
+    float2* r = w.tr + (size_t)k * w.vn;
+    float2* r1 = w.tr + (size_t)(k + 1) * w.vn;
     RC(O.normal(x, p, alpha, q));
     RC(O.dot(p, q, nx, sc + S.gamma + k));
-    k_cg_a<<<1, 1, 0, O.st>>>(sc, S, k);
-    CKL("k_cg_a");
-    RC(O.axpby_s(w.xcg, p, sc + S.a + k, 1.0, 1.0, nx));
-    RC(O.copy(r1, r, nx));
-    RC(O.axpby_s(r1, q, sc + S.a + k, -1.0, 1.0, nx));
-    RC(O.dot(r1, r1, nx, sc + S.rho + k + 1));
-    k_cg_beta<<<1, 1, 0, O.st>>>(sc, S, k);
-    CKL("k_cg_beta");
-    if (k + 1 < iters) {
-      float2* p1 = w.tp + (size_t)(k + 1) * (size_t)nx;
-      RC(O.copy(p1, r1, nx));
-      RC(O.axpby_s(p1, p, sc + S.beta + k, 1.0, 1.0, nx));
-    }
+    k_cg_step<<<kDotBlocks, 256, 0, O.st>>>(nx, sc, S, k, w.xcg, p, q, r, r1, O.part);
+    CKL("k_cg_step");
+    k_dot_final<<<1, 32, 0, O.st>>>(kDotBlocks, O.part, sc + S.rho + k + 1);
+    CKL("k_dot_final");
+    float2* p1 = k + 1 < iters ? w.tp + (size_t)(k + 1) * w.vn : nullptr;
+    k_cg_dir<<<p1 ? O.grid(nx) : 1, 256, 0, O.st>>>(p1 ? nx : 0, sc, S, k, p1, r1, p);
+    CKL("k_cg_dir");
   }
   return NLINV_OK;
 }
 
 // The whole reverse pass of one frame, issued on `st` without any host
-// synchronisation; alpha0-bar and a breakdown flag end up in w.sc.
+// synchronisation; alpha0-bar and the breakdown flags end up in the Newton
+// steps' scalar blocks (k_gather_vjp).  The forward sweep records every
+// Newton step's CG (the workspace holds all M tapes), so the reverse sweep
+// reads them instead of recomputing the step from its checkpoint.
 int vjp_issue(const nlinv_plan_s* view, cudaStream_t st, const GradWS& w, const float* P, const float2* Yd,
               const float2* xprev, const float2* gbar, float2* Ybar, float2* xprev_bar) {
   const nlinv_params_t& prm = view->prm;
   const int M = prm.newton_steps, Kc = prm.cg_iters;
   const VjpSlots S(Kc);
-  double* sc = w.sc;
   GradOps O{view, st, P, view->nx, (long long)view->J * view->G * view->G, w.part, grid_ops(view->G, view->N)};
   const long long nx = O.nx, nk = O.nk;
-  k_fill<<<1, 256, 0, st>>>(sc, S.total, 0.0);
+  const int nfill = M * S.total;
+  k_fill<<<(nfill + 255) / 256, 256, 0, st>>>(w.sc, nfill, 0.0);
   CKL("k_fill");
   // x^_0 and x_ref
   if (xprev) {
@@ -1451,14 +1581,15 @@ int vjp_issue(const nlinv_plan_s* view, cudaStream_t st, const GradWS& w, const 
   }
   RC(O.copy(w.xref, w.ck, nx));
   RC(O.axpby(w.xref, w.xref, 0.0, prm.damping, nx));
-  // forward: checkpoints x^_n
+  // forward: checkpoints x^_n, each Newton step's residual and CG tape
   for (int n = 0; n < M; ++n) {
-    const float2* x = w.ck + (size_t)n * (size_t)nx;
-    float2* x1 = w.ck + (size_t)(n + 1) * (size_t)nx;
+    const GradWS u = w.at(n);
+    const float2* x = w.ck + (size_t)n * w.vn;
+    float2* x1 = w.ck + (size_t)(n + 1) * w.vn;
     const double alpha = prm.alpha0 * std::pow(prm.q, n);
     O.lin = x;
-    RC(grad_rhs(O, w, Yd, x, alpha, w.b));
-    RC(grad_cg(O, w, S, x, alpha, w.b, Kc));
+    RC(grad_rhs(O, u, Yd, x, alpha, w.b));
+    RC(grad_cg(O, u, S, x, alpha, w.b, Kc));
     RC(O.copy(x1, x, nx));
     RC(O.axpby(x1, w.xcg, 1.0, 1.0, nx));
   }
@@ -1466,32 +1597,27 @@ int vjp_issue(const nlinv_plan_s* view, cudaStream_t st, const GradWS& w, const 
   RC(O.zero(Ybar, nk));
   RC(O.zero(w.xrefbar, nx));
   RC(O.copy(w.xb, gbar, nx));
-  GradWS v = w;   // pbar / pb and xb / xbn swap roles as host pointers
+  GradWS v = w;   // xb / xbn swap roles per Newton step as host pointers
   for (int n = M - 1; n >= 0; --n) {
-    const float2* x = w.ck + (size_t)n * (size_t)nx;
+    GradWS u = v.at(n);   // step n's tape, residual and scalars; pbar / pb swap per CG step
+    double* sc = u.sc;
+    const float2* x = w.ck + (size_t)n * w.vn;
     const double alpha = prm.alpha0 * std::pow(prm.q, n);
     O.lin = x;
-    RC(grad_rhs(O, v, Yd, x, alpha, v.b));            // residual z stays in v.z
-    RC(grad_cg(O, v, S, x, alpha, v.b, Kc));
-    RC(O.copy(v.xbn, v.xb, nx));                      // x^_{n+1} = x^_n + delta
-    RC(O.zero(v.pbar, nx));
-    RC(O.zero(v.rbar, nx));
-    k_fill<<<1, 256, 0, st>>>(sc + S.rhobar, Kc + 1, 0.0);
-    CKL("k_fill");
-    k_fill<<<1, 32, 0, st>>>(sc + S.ab, 1, 0.0);
-    CKL("k_fill");
-    const double* co = sc + S.co;
+    RC(O.copy(u.xbn, u.xb, nx));                      // x^_{n+1} = x^_n + delta
+    RC(O.zero(u.pbar, nx));
+    RC(O.zero(u.rbar, nx));
     for (int k = Kc - 1; k >= 0; --k) {
-      const float2* p = v.tp + (size_t)k * (size_t)nx;
-      const float2* q = v.tq + (size_t)k * (size_t)nx;
-      const float2* r1 = v.tr + (size_t)(k + 1) * (size_t)nx;
+      const float2* p = u.tp + (size_t)k * w.vn;
+      const float2* q = u.tq + (size_t)k * w.vn;
+      const float2* r1 = u.tr + (size_t)(k + 1) * w.vn;
       // every inner product this step needs, from the vectors as they enter
       // it (the updates below are linear in them):
       //   D0 <p, pbar>  D1 <q, rbar>  D2 <q, pbar>  D3 <q, r1>
       //   D4 <p, xb>    D5 <p, rbar>  D6 <p, r1>    D7 <p, p>
       DotSet DS;
       const float2* U[kMaxDots] = {p, q, q, q, p, p, p, p};
-      const float2* V[kMaxDots] = {v.pbar, v.rbar, v.pbar, r1, v.xb, v.rbar, r1, p};
+      const float2* V[kMaxDots] = {u.pbar, u.rbar, u.pbar, r1, u.xb, u.rbar, r1, p};
       for (int j = 0; j < kMaxDots; ++j) {
         DS.u[j] = U[j];
         DS.v[j] = V[j];
@@ -1499,53 +1625,52 @@ int vjp_issue(const nlinv_plan_s* view, cudaStream_t st, const GradWS& w, const 
       RC(O.dots(DS, sc + S.D));
       k_rev_step<<<1, 1, 0, st>>>(sc, S, k);          // adjoint scalars, coefficients co
       CKL("k_rev_step");
-      RC(O.axpby_s(v.rbar, v.pbar, co + 0, 1.0, 1.0, nx));   // p_{k+1} = r_{k+1} + beta p_k
-      RC(O.axpby_s(v.pb, v.pbar, co + 1, 1.0, 0.0, nx));
-      RC(O.axpby_s(v.rbar, r1, co + 2, 1.0, 1.0, nx));       // rho_{k+1} = <r, r>
-      RC(O.axpby_s(v.qbar, v.rbar, co + 3, 1.0, 0.0, nx));   // r_{k+1} = r_k - a q_k
-      RC(O.axpby_s(v.pb, v.xb, co + 4, 1.0, 1.0, nx));       // x_{k+1} = x_k + a p_k
-      RC(O.axpby_s(v.pb, q, co + 5, 1.0, 1.0, nx));          // gamma = <p, q>
-      RC(O.axpby_s(v.qbar, p, co + 5, 1.0, 1.0, nx));
-      RC(O.normal(x, v.qbar, alpha, v.t1));                  // q = A p
-      RC(O.axpby(v.pb, v.t1, 1.0, 1.0, nx));
+      // p_{k+1} = r_{k+1} + beta p_k;  rho_{k+1} = <r, r>;  r_{k+1} = r_k - a q_k;
+      // x_{k+1} = x_k + a p_k;  gamma = <p, q>
+      k_rev_update<<<O.grid(nx), 256, 0, st>>>(nx, sc + S.co, u.rbar, u.pbar, u.pb, r1, u.qbar, u.xb, q, p);
+      CKL("k_rev_update");
+      RC(O.normal(x, u.qbar, alpha, u.t0));                  // q = A p
       // A depends on x^_n: both DF at x^_n first, while its coil maps are current
-      RC(O.DF(x, p, v.zt));
-      RC(O.psf(v.zt, 1.f));
-      RC(O.DF(x, v.qbar, v.zt2));
-      RC(O.psf(v.zt2, 1.f));
-      RC(O.DFH(v.qbar, v.zt, v.t1));
-      RC(O.axpby(v.xbn, v.t1, 1.0, 1.0, nx));
-      RC(O.DFH(p, v.zt2, v.t1));
-      RC(O.axpby(v.xbn, v.t1, 1.0, 1.0, nx));
-      std::swap(v.pbar, v.pb);
+      RC(O.DF(x, p, u.zt));
+      RC(O.DF(x, u.qbar, u.zt2));
+      k_psf_scale2<<<O.grid(nk), 256, 0, st>>>(view->J, view->G, u.zt, u.zt2, P, 1.f);
+      CKL("k_psf_scale2");
+      RC(O.DFH(u.qbar, u.zt, u.t1));
+      RC(O.DFH(p, u.zt2, u.t2));
+      k_rev_acc<<<O.grid(nx), 256, 0, st>>>(nx, u.pb, u.t0, u.xbn, u.t1, u.t2);
+      CKL("k_rev_acc");
+      std::swap(u.pbar, u.pb);
     }
     // p_0 = r_0 = b, rho_0 = <r_0, r_0>:  b-bar
-    RC(O.axpby(v.rbar, v.pbar, 1.0, 1.0, nx));
+    RC(O.axpby(u.rbar, u.pbar, 1.0, 1.0, nx));
     k_rev_c0<<<1, 1, 0, st>>>(sc, S);
     CKL("k_rev_c0");
-    RC(O.axpby_s(v.rbar, v.tr, sc + S.c0, 1.0, 1.0, nx));
-    const float2* bbar = v.rbar;
+    RC(O.axpby_s(u.rbar, u.tr, sc + S.c0, 1.0, 1.0, nx));
+    const float2* bbar = u.rbar;
     // right-hand side
-    RC(O.DFH(bbar, v.z, v.t1));
-    RC(O.axpby(v.xbn, v.t1, 1.0, 1.0, nx));
-    RC(O.DF(x, bbar, v.zt));
-    k_axpby<<<O.grid(nk), 256, 0, st>>>(nk, Ybar, v.zt, 1.f, 0.f, 1.f);   // Y-bar += DF(x) b-bar
+    RC(O.DFH(bbar, u.z, u.t1));
+    RC(O.axpby(u.xbn, u.t1, 1.0, 1.0, nx));
+    RC(O.DF(x, bbar, u.zt));
+    k_axpby<<<O.grid(nk), 256, 0, st>>>(nk, Ybar, u.zt, 1.f, 0.f, 1.f);   // Y-bar += DF(x) b-bar
     CKL("k_axpby");
-    RC(O.psf(v.zt, 1.f));
-    RC(O.DFH(x, v.zt, v.t1));
-    RC(O.axpby(v.xbn, v.t1, -1.0, 1.0, nx));
-    RC(O.axpby(v.xbn, bbar, -alpha, 1.0, nx));
+    RC(O.psf(u.zt, 1.f));
+    RC(O.DFH(x, u.zt, u.t1));
+    RC(O.axpby(u.xbn, u.t1, -1.0, 1.0, nx));
+    RC(O.axpby(u.xbn, bbar, -alpha, 1.0, nx));
     RC(O.dot(bbar, x, nx, sc + S.t1));
-    RC(O.dot(bbar, v.xref, nx, sc + S.t2));
+    RC(O.dot(bbar, w.xref, nx, sc + S.t2));
     k_rev_alpha<<<1, 1, 0, st>>>(sc, S, std::pow(prm.q, n));
     CKL("k_rev_alpha");
-    RC(O.axpby(v.xrefbar, bbar, alpha, 1.0, nx));
-    std::swap(v.xb, v.xbn);
+    RC(O.axpby(w.xrefbar, bbar, alpha, 1.0, nx));
+    v.xb = u.xbn;
+    v.xbn = u.xb;
+    v.pbar = u.pbar;
+    v.pb = u.pb;
   }
   if (xprev_bar) {
     if (xprev) {
       RC(O.copy(xprev_bar, v.xb, nx));
-      RC(O.axpby(xprev_bar, v.xrefbar, prm.damping, 1.0, nx));
+      RC(O.axpby(xprev_bar, w.xrefbar, prm.damping, 1.0, nx));
     } else {
       RC(O.zero(xprev_bar, nx));
     }
@@ -1658,7 +1783,8 @@ extern "C" int nlinv_batch_vjp(nlinv_plan_t pl, int nframes, const void* const* 
   }
   GradWS w0;
   grad_ws_carve(pl, wbase, w0);
-  k_gather_vjp<<<1, 64, 0, st>>>(nframes, w0.sc, wsb / sizeof(double), VjpSlots(pl->prm.cg_iters), gather);
+  k_gather_vjp<<<1, 64, 0, st>>>(nframes, pl->prm.newton_steps, w0.sc, wsb / sizeof(double),
+                                 VjpSlots(pl->prm.cg_iters), gather);
   CKL("k_gather_vjp");
   CK(cudaMemcpyAsync(pl->vjp_host, gather, 2 * nframes * sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));

@@ -6,8 +6,9 @@ database of measured reconstruction times (Sec. 3.3).  Here the unit that is
 timed is a whole NLINV frame on this GPU: for an N x N image with J channels
 (M Newton steps x K CG iterations) the tuner runs frames for every compiled
 grid with gamma in a given range and every execution path a plan can take on
-it -- one launch per fused phase, the grid kernel, and the cluster kernel for
-each cluster size whose J clusters are co-resident -- and keeps the fastest.  The pick and every
+it -- the per-phase frame replayed as a CUDA graph, one launch per fused
+phase, the grid kernel, and the cluster kernel for each cluster size whose J
+clusters are co-resident -- and keeps the fastest.  The pick and every
 candidate's time (CUDA events, median of the timed frames) are stored in a
 JSON database keyed by the GPU name, so that later plans for the same sizes
 are made from the record (tuned_params) instead of being re-measured.
@@ -55,6 +56,7 @@ def candidates(N, J, M=7, K=10, gamma=(1.0, 2.0)):
     out = []
     grids = sorted(G for G, n in L.nlinv_grid_list() if n == N and 2 * N * gamma[0] <= G <= 2 * N * gamma[1])
     for G in grids:
+        out.append(dict(G=G, exec_mode=4, cluster_cs=0))
         out.append(dict(G=G, exec_mode=2, cluster_cs=0))
         out.append(dict(G=G, exec_mode=1, cluster_cs=0))
         for cs in CLUSTER_SIZES:
