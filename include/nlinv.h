@@ -73,6 +73,10 @@ typedef struct {
                             fastest on the configurations' sizes (the tuner,
                             tune.py, records the fastest per size);
                          1: one launch per phase (unfused comparator);
+                            each launch covers every frame of the call
+                            (nlinv_batch: CTA b works on frame b / n_b);
+                            the frames' pointers are read from a plan-owned
+                            device table written at the start of the call;
                          2: one persistent cooperative launch, CTAs
                             synchronised by grid barriers between phases;
                          3: one persistent cooperative launch with one
@@ -82,13 +86,13 @@ typedef struct {
                             and the CG inner products); nlinv_plan returns
                             NLINV_EUNSUPPORTED when the J clusters cannot be
                             co-resident;
-                         4: the launches of 1 captured once into a CUDA graph
+                         4: the launches of 1 captured into a CUDA graph
                             with programmatic dependent launches between the
-                            phases, replayed per frame through plan-owned
-                            staging buffers (captured on the first frame and
-                            again after nlinv_set_alpha0; the capture is on a
-                            plan-owned stream, so the first frame must not be
-                            issued while the calling thread captures) */
+                            phases, one graph per frame count, replayed per
+                            call (captured on first use and again after
+                            nlinv_set_alpha0; the capture is on a plan-owned
+                            stream, so such a call must not be issued while
+                            the calling thread captures) */
   int max_batch;      /* frames of this plan one nlinv_batch call may hold, 1..64;
                          0 -> 1 (the plan allocates one workspace per frame) */
   int G;              /* grid side: 0 -> 2N (gamma = 1); else a grid G = 2 gamma N
@@ -253,11 +257,15 @@ typedef struct {
  * are reconstructed at the same time).  Each frame is nlinv_frame with its
  * own inputs (and, with x_last, another regulariser in its last Newton
  * step); frames may belong to different plans (grid sizes, channel counts).
- * Frames of one plan (at most its max_batch) run in one persistent
- * cooperative launch whose CTAs are split into one group per frame, each
- * group with its own barrier; different plans run concurrently on the plans'
- * own streams, each on a share of the SMs proportional to its work, and the
- * call is ordered on `stream` before and after.  Which frame serves as whose
+ * Frames of one plan (at most its max_batch) run together: on the
+ * per-phase path (exec_mode 0, 1, 4) every phase is one launch over all of
+ * them, each frame on its own workspace with the same CTA count; with
+ * exec_mode 2 or 3, or when a frame's last step waits for another frame of
+ * the call, in one persistent cooperative launch whose CTAs are split into
+ * one group per frame, each group with its own barrier.  Different plans run
+ * concurrently on the plans' own streams (the persistent launches each on a
+ * share of the SMs proportional to its work), and the call is ordered on
+ * `stream` before and after.  Which frame serves as whose
  * x_prev (the schedule) is the caller's choice: no frame's x_prev may be
  * another frame's x_out of the same call (x_last may, see above). */
 int nlinv_batch(const nlinv_frame_desc_t* frames, int nframes, nlinv_stream_t stream);

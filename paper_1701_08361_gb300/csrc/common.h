@@ -123,13 +123,19 @@ struct nlinv_plan_s {
   int batch_occ = 0;          // co-resident CTAs per SM of k_batch
   int cl_cs = 0;              // CTAs per cluster of k_frame_cl (0: it does not fit)
   nlinv::cl::Lay cl_lay;             // its shared-memory layout
-  // exec_mode 4: the captured per-phase frame and its staging buffers
-  cudaGraphExec_t gexec = nullptr;
-  double galpha0 = 0.0;       // alpha_0 the graph was captured with
+  // per-phase execution (exec_mode 0, 1, 4): CTAs per frame of a one-phase
+  // launch, the device table of the frames' inputs and outputs that the
+  // phase kernels read, and the phase sequences captured into CUDA graphs
+  // (one per frame count and alpha_0)
+  int phase_grid = 0;
+  nlinv::FrameIO* io_dev = nullptr;
   cudaStream_t gcap = nullptr;
-  void* gmem = nullptr;
-  float2 *gy = nullptr, *gxp = nullptr, *gx = nullptr, *grho = nullptr, *gimg = nullptr;
-  float* gp = nullptr;
+  struct PhaseGraph {
+    int nf = 0;
+    double alpha0 = 0.0;
+    cudaGraphExec_t exec = nullptr;
+  };
+  std::vector<PhaseGraph> pgraphs;
   // reverse passes: one stream, completion event, captured graph and staging
   // buffers per frame slot of a batch, and their own workspace allocation
   std::vector<cudaStream_t> vjp_st;
@@ -179,7 +185,9 @@ struct GridOps {
                  float2* Y);
   // one whole frame on the plan's execution path
   int (*frame)(const nlinv_plan_s* pl, cudaStream_t st, const FrameArgs& F);
-  // frames of one plan in one cooperative launch of `grid` CTAs
+  // frames of one plan together: one launch per phase over all frames
+  // (exec_mode 0, 1, 4, when no frame waits for another), else one
+  // cooperative launch of `grid` CTAs
   int (*batch)(const nlinv_plan_s* pl, cudaStream_t st, const BatchArgs& B, int grid);
 #ifdef NLINV_TIMELINE
   int (*timeline)(unsigned long long* host, int n);

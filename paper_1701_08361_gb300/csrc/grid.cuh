@@ -15,6 +15,13 @@
 
 #include "common.h"
 
+// CTAs per SM the frame-indexed phase kernels (kf_*) are compiled for (caps
+// their registers; one measured fastest at the 320 grid: two cost 34 % per
+// frame in register spills)
+#ifndef NLINV_PMINB
+#define NLINV_PMINB 1
+#endif
+
 namespace nlinv {
 namespace {
 
@@ -38,23 +45,14 @@ __device__ __forceinline__ Ctx phase_entry(const Ctx& C0) {
 }
 
 template <class K>
-__global__ void __launch_bounds__(K::BS) k_coil_y(Ctx C0, const float2* src, float2* hout) {
+__global__ void __launch_bounds__(K::BS, K::OMINB) k_coil_y(Ctx C0, const float2* src, float2* hout) {
   const Ctx C = phase_entry(C0);
   extern __shared__ float2 sm[];
   phase_coil_y<K>(C, sm, src, hout);
 }
 
 template <class K>
-__global__ void __launch_bounds__(K::BS) k_row_cg(Ctx C0, int k, const float2* p_old, float2* p_new,
-                                                  float2* vout) {
-  const Ctx C = phase_entry(C0);
-  extern __shared__ float2 sm[];
-  __shared__ float2 sred[32];
-  phase_row_cg<K>(C, sm, sred, k, p_old, p_new, vout);
-}
-
-template <class K>
-__global__ void __launch_bounds__(K::BS) k_row_b(Ctx C0, int mode, const float2* hin, const float2* rho,
+__global__ void __launch_bounds__(K::BS, K::OMINB) k_row_b(Ctx C0, int mode, const float2* hin, const float2* rho,
                                                  const float2* drho, const float2* img, float2* vout) {
   const Ctx C = phase_entry(C0);
   extern __shared__ float2 sm[];
@@ -62,14 +60,14 @@ __global__ void __launch_bounds__(K::BS) k_row_b(Ctx C0, int mode, const float2*
 }
 
 template <class K>
-__global__ void __launch_bounds__(K::BS) k_row_deapod(Ctx C0, const float* dap, float scale, float2* v) {
+__global__ void __launch_bounds__(K::BS, K::OMINB) k_row_deapod(Ctx C0, const float* dap, float scale, float2* v) {
   const Ctx C = phase_entry(C0);
   extern __shared__ float2 sm[];
   phase_row_deapod<K>(C, sm, dap, scale, v);
 }
 
 template <class K>
-__global__ void __launch_bounds__(K::BS) k_col_c(Ctx C0, int mode, const float* P, const float2* Yin,
+__global__ void __launch_bounds__(K::BS, K::OMINB) k_col_c(Ctx C0, int mode, const float* P, const float2* Yin,
                                                  float2* zout, float2* vio, int k) {
   const Ctx C = phase_entry(C0);
   extern __shared__ float2 sm[];
@@ -77,7 +75,7 @@ __global__ void __launch_bounds__(K::BS) k_col_c(Ctx C0, int mode, const float* 
 }
 
 template <class K>
-__global__ void __launch_bounds__(K::BS) k_row_d(Ctx C0, const float2* rho, const float2* win, float2* sout,
+__global__ void __launch_bounds__(K::BS, K::OMINB) k_row_d(Ctx C0, const float2* rho, const float2* win, float2* sout,
                                                  float2* kbout) {
   const Ctx C = phase_entry(C0);
   extern __shared__ float2 sm[];
@@ -85,7 +83,7 @@ __global__ void __launch_bounds__(K::BS) k_row_d(Ctx C0, const float2* rho, cons
 }
 
 template <class K>
-__global__ void __launch_bounds__(K::BS) k_col_e(Ctx C0, int mode, float alpha, int k, const float2* kbin,
+__global__ void __launch_bounds__(K::BS, K::OMINB) k_col_e(Ctx C0, int mode, float alpha, int k, const float2* kbin,
                                                  const float2* sin, const float2* p_old, float2* p_new,
                                                  float2* out, float2* hout, int slot) {
   const Ctx C = phase_entry(C0);
@@ -99,28 +97,129 @@ __global__ void __launch_bounds__(K::BS) k_col_e(Ctx C0, int mode, float alpha, 
   }
 }
 
+// ------------------------------------------ frame-indexed phase kernels
+// The per-phase path launches each phase of the IRGNM / CG once for nf frames
+// of one plan: CTA b works on frame f = b / nbf as CTA b % nbf of nbf, on
+// frame f's workspace (frame_ctx), so every frame sees the same CTA count in
+// every phase and its CG partial sums line up.  The frames' inputs and
+// outputs come from a device table written before the sequence (k_set_io),
+// so one captured sequence serves every call with the same frame count.
+struct PhaseBatch {
+  size_t fstride;       // bytes between the frames' workspaces
+  int nbf;              // CTAs per frame
+  const FrameIO* io;    // device [nf]
+};
+
+__device__ __forceinline__ Ctx frame_entry(const Ctx& C0, const PhaseBatch& B, int& f) {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  f = (int)(blockIdx.x / (unsigned)B.nbf);
+  Ctx C = frame_ctx(C0, (size_t)f * B.fstride);
+  C.bid = (int)blockIdx.x - f * B.nbf;
+  C.nb = B.nbf;
+  return C;
+}
+
+struct IOTable {
+  FrameIO io[kMaxBatch];
+};
+__global__ void k_set_io(IOTable T, int nf, FrameIO* dst) {
+  const int f = threadIdx.x;
+  if (f < nf) dst[f] = T.io[f];
+}
+
+// x^_0 = x_prev (or rho = 1, c^ = 0), x_ref = damping x_prev
+__global__ void kf_init(Ctx C0, PhaseBatch B, float damping) {
+  int f;
+  const Ctx C = frame_entry(C0, B, f);
+  phase_init(C, B.io[f].xprev, damping);
+}
+
+// the coil part of x^_n through W^-1 along y
 template <class K>
-__global__ void __launch_bounds__(K::BS) k_upd(Ctx C0, int k, int last, const float2* p) {
-  const Ctx C = phase_entry(C0);
+__global__ void __launch_bounds__(K::BS, NLINV_PMINB) kf_coil_y(Ctx C0, PhaseBatch B) {
+  int f;
+  const Ctx C = frame_entry(C0, B, f);
+  extern __shared__ float2 sm[];
+  phase_coil_y<K>(C, sm, C.xn + (size_t)C.N * C.N, C.h);
+}
+
+// ROW_COIL: coil maps and rho c_j rows through the padded row FFT;
+// ROW_COILONLY: the coil maps alone
+template <class K>
+__global__ void __launch_bounds__(K::BS, NLINV_PMINB) kf_row_b(Ctx C0, PhaseBatch B, int mode) {
+  int f;
+  const Ctx C = frame_entry(C0, B, f);
+  extern __shared__ float2 sm[];
+  if (mode == ROW_COIL)
+    phase_row_b<K>(C, sm, ROW_COIL, C.h, C.xn, nullptr, nullptr, C.v);
+  else
+    phase_row_b<K>(C, sm, ROW_COILONLY, C.h, nullptr, nullptr, nullptr, nullptr);
+}
+
+// COL_RHS: column pass of the residual against the frame's data;
+// COL_CG: column pass of CG iteration k (both with the frame's PSF)
+template <class K>
+__global__ void __launch_bounds__(K::BS, NLINV_PMINB) kf_col_c(Ctx C0, PhaseBatch B, int mode, int k) {
+  int f;
+  const Ctx C = frame_entry(C0, B, f);
+  extern __shared__ float2 sm[];
+  const FrameIO& io = B.io[f];
+  phase_col_c<K>(C, sm, mode, io.P, mode == COL_RHS ? io.Y : nullptr, nullptr, C.v, k);
+}
+
+template <class K>
+__global__ void __launch_bounds__(K::BS, NLINV_PMINB) kf_row_d(Ctx C0, PhaseBatch B) {
+  int f;
+  const Ctx C = frame_entry(C0, B, f);
+  extern __shared__ float2 sm[];
+  phase_row_d<K>(C, sm, C.xn, C.v, C.s, C.kb);
+}
+
+// E_RHS: the Newton right-hand side r_0 (the last step regularised towards
+// damping * x_last when `last` and the frame has one); E_CG: A p_k of CG
+// iteration k and the partials of Re<p_k, A p_k>
+template <class K>
+__global__ void __launch_bounds__(K::BS, NLINV_PMINB) kf_col_e(Ctx C0, PhaseBatch B, int mode, float alpha,
+                                                               int k, int last, float damping) {
+  int f;
+  const Ctx C = frame_entry(C0, B, f);
   extern __shared__ float2 sm[];
   __shared__ float2 sred[32];
-  phase_upd<K>(C, sm, sred, k, last != 0, p);
+  if (mode == E_RHS) {
+    const float2* xl = last ? B.io[f].xlast : nullptr;
+    phase_col_e<K, E_RHS>(C, sm, sred, alpha, 0, C.kb, C.s, nullptr, nullptr, C.rb[0], C.Hr, SLOT_RR0, xl,
+                          xl ? damping : 1.f);
+  } else {
+    phase_col_e<K, E_CG>(C, sm, sred, alpha, k, C.kb, C.s, C.pb[(k + 1) & 1], C.pb[k & 1], C.q, nullptr,
+                         SLOT_PQ);
+  }
 }
 
-// x = (rho = 1, c^ = 0): the first frame's initial value (Sec. 3.3)
-__global__ void k_initial_value(int nx, int NN, float2* x) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nx; i += gridDim.x * blockDim.x)
-    x[i] = make_float2(i < NN ? 1.f : 0.f, 0.f);
+template <class K>
+__global__ void __launch_bounds__(K::BS, NLINV_PMINB) kf_row_cg(Ctx C0, PhaseBatch B, int k) {
+  int f;
+  const Ctx C = frame_entry(C0, B, f);
+  extern __shared__ float2 sm[];
+  __shared__ float2 sred[32];
+  phase_row_cg<K>(C, sm, sred, k, C.pb[(k + 1) & 1], C.pb[k & 1], C.v);
 }
 
-__global__ void k_init(Ctx C0, const float2* xprev, float damping) {
-  const Ctx C = phase_entry(C0);
-  phase_init(C, xprev, damping);
+template <class K>
+__global__ void __launch_bounds__(K::BS, NLINV_PMINB) kf_upd(Ctx C0, PhaseBatch B, int k, int last) {
+  int f;
+  const Ctx C = frame_entry(C0, B, f);
+  extern __shared__ float2 sm[];
+  __shared__ float2 sred[32];
+  phase_upd<K>(C, sm, sred, k, last != 0, C.pb[k & 1]);
 }
 
-__global__ void k_final(Ctx C0, float2* xout, float2* rho_out, float2* img_out) {
-  const Ctx C = phase_entry(C0);
-  phase_final(C, xout, rho_out, img_out);
+// outputs: x^, rho, rho * sqrt(sum_j |c_j|^2)
+__global__ void kf_final(Ctx C0, PhaseBatch B) {
+  int f;
+  const Ctx C = frame_entry(C0, B, f);
+  const FrameIO& io = B.io[f];
+  phase_final(C, io.xout, io.rho_out, io.img_out);
 }
 
 
@@ -415,8 +514,13 @@ int set_smem_attrs() {
     CK(cudaFuncSetAttribute(k_col_c<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(k_row_d<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(k_col_e<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
-    CK(cudaFuncSetAttribute(k_row_cg<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
-    CK(cudaFuncSetAttribute(k_upd<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
+    CK(cudaFuncSetAttribute(kf_coil_y<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
+    CK(cudaFuncSetAttribute(kf_row_b<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
+    CK(cudaFuncSetAttribute(kf_col_c<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
+    CK(cudaFuncSetAttribute(kf_row_d<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
+    CK(cudaFuncSetAttribute(kf_col_e<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
+    CK(cudaFuncSetAttribute(kf_row_cg<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
+    CK(cudaFuncSetAttribute(kf_upd<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(k_frame<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(k_batch<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
   }
@@ -513,11 +617,6 @@ struct Launch {
     const int g = plan_grid(C.J * ((C.Gc + K::TW - 1) / K::TW), 1);
     return go(&k_coil_y<K>, pick(g), K::BS, (size_t)K::SMEM, "k_coil_y", C, src, hout);
   }
-  int row_cg(int k, const float2* p_old, float2* p_new, float2* vout) const {
-    const Ctx& C = pl->C;
-    const int g = plan_grid(C.J * ((C.N + K::TW - 1) / K::TW), 1);
-    return go(&k_row_cg<K>, pick(g), K::BS, (size_t)K::SMEM, "k_row_cg", C, k, p_old, p_new, vout);
-  }
   int row_b(int mode, const float2* hin, const float2* rho, const float2* drho, const float2* img,
             float2* vout) const {
     const Ctx& C = pl->C;
@@ -545,12 +644,6 @@ struct Launch {
     const int items = C.J * ((C.Gc + K::TW - 1) / K::TW);
     const int g = plan_grid(items, (C.N * C.N + K::BS - 1) / K::BS);
     return go(&k_col_e<K>, pick(g), K::BS, (size_t)K::SMEM, "k_col_e", C, mode, alpha, k, kbin, sin, p_old, p_new, out, hout, slot);
-  }
-  int upd(int k, int last, const float2* p) const {
-    const Ctx& C = pl->C;
-    const int items = C.J * ((C.Gc + K::TW - 1) / K::TW);
-    const int g = plan_grid(items, (C.N * C.N + K::BS - 1) / K::BS);
-    return go(&k_upd<K>, pick(g), K::BS, (size_t)K::SMEM, "k_upd", C, k, last, p);
   }
   // coil maps c_j = W^-1 c^_j of x^ into the plan's c buffer
   int coils(const float2* xhat) const {
@@ -606,6 +699,23 @@ struct Ops {
     int nbb = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nbb, k_batch<K>, K::BS, K::SMEM));
     pl->batch_occ = nbb;
+    // one-phase launches: the co-resident CTAs of the phase kernels, but no
+    // more than the largest phase has items (+ the elementwise share)
+    int occ = 1 << 20;
+    const void* kf[] = {(const void*)kf_coil_y<K>, (const void*)kf_row_b<K>, (const void*)kf_col_c<K>,
+                        (const void*)kf_row_d<K>,  (const void*)kf_col_e<K>, (const void*)kf_row_cg<K>,
+                        (const void*)kf_upd<K>};
+    for (const void* fn : kf) {
+      int o = 0;
+      CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, K::BS, K::SMEM));
+      occ = o < occ ? o : occ;
+    }
+    const int most = pl->J * ((pl->G + K::TW - 1) / K::TW) + kElemCTAs;
+    int pg = occ * pl->nsm;
+    if (pg > most) pg = most;
+    if (pg > kMaxPart) pg = kMaxPart;
+    pl->phase_grid = pg;
+    if (pg <= 0) return NLINV_ECUDA;
     if (pl->prm.exec_mode == 3) {
       RC(pick_cluster<K>(pl));
       if (pl->cl_cs == 0) return NLINV_EUNSUPPORTED;
@@ -681,80 +791,73 @@ struct Ops {
                                      (size_t)K::SMEM, st));
       return NLINV_OK;
     }
-    if (mode == 0 || mode == 4) return frame_graph(const_cast<nlinv_plan_s*>(pl), st, F);
-    return per_phase(pl, st, F, false);
+    return phased_run(const_cast<nlinv_plan_s*>(pl), st, &F.io, 1, F.M, F.K, F.damping, F.alpha);
   }
 
-  // The frame as one launch per fused phase (every launch with the same CTA
-  // count, so that the CG partial sums line up), optionally with programmatic
-  // dependent launches.
-  static int per_phase(const nlinv_plan_s* pl, cudaStream_t st, const FrameArgs& F, bool pdl) {
-    Ctx C = pl->C;
-    const int NN = pl->N * pl->N;
-    Launch<K> L{pl, st, pl->coop_grid, pdl};
-    const int ge = plan_grid((int)((C.nx + 255) / 256), 1);
-    RC(L.go(&k_init, ge, 256, 0, "k_init", C, F.io.xprev, F.damping));
-    for (int n = 0; n < F.M; ++n) {
-      const float alpha = F.alpha[n];
-      RC(L.coil_y(C.xn + NN, C.h));
-      RC(L.row_b(ROW_COIL, C.h, C.xn, nullptr, nullptr, C.v));
-      RC(L.col_c(COL_RHS, F.io.P, F.io.Y, nullptr, C.v));
-      RC(L.row_d(C.xn, C.v, C.s, C.kb));
-      RC(L.col_e(E_RHS, alpha, 0, C.kb, C.s, nullptr, nullptr, C.rb[0], C.Hr, SLOT_RR0));
-      for (int kk = 0; kk < F.K; ++kk) {
-        float2* pk = C.pb[kk & 1];
-        const float2* pm = C.pb[(kk + 1) & 1];
-        RC(L.row_cg(kk, pm, pk, C.v));
-        RC(L.col_c(COL_CG, F.io.P, nullptr, nullptr, C.v, kk));
-        RC(L.row_d(C.xn, C.v, C.s, C.kb));
-        RC(L.col_e(E_CG, alpha, kk, C.kb, C.s, pm, pk, C.q, nullptr, SLOT_PQ));
-        RC(L.upd(kk, kk == F.K - 1, pk));
+  // nf frames of the plan as one launch per fused phase, each launch over
+  // all frames (frame_entry); the frames' inputs and outputs are read from
+  // the plan's device table io_dev.  Optionally with programmatic dependent
+  // launches between the kernels.
+  static int phased(const nlinv_plan_s* pl, cudaStream_t st, int nf, int M, int Kcg, float damping,
+                    const float* alpha, bool pdl) {
+    const Ctx& C = pl->C;
+    Launch<K> L{pl, st, 0, pdl};
+    const PhaseBatch B{pl->fstride, pl->phase_grid, pl->io_dev};
+    const PhaseBatch Be{pl->fstride, plan_grid((int)((C.nx + 255) / 256), 1), pl->io_dev};
+    const int gp = nf * B.nbf, ge = nf * Be.nbf;
+    const size_t sm = (size_t)K::SMEM;
+    RC(L.go(&kf_init, ge, 256, 0, "kf_init", C, Be, damping));
+    for (int n = 0; n < M; ++n) {
+      const float al = alpha[n];
+      RC(L.go(&kf_coil_y<K>, gp, K::BS, sm, "kf_coil_y", C, B));
+      RC(L.go(&kf_row_b<K>, gp, K::BS, sm, "kf_row_b", C, B, (int)ROW_COIL));
+      RC(L.go(&kf_col_c<K>, gp, K::BS, sm, "kf_col_c", C, B, (int)COL_RHS, 0));
+      RC(L.go(&kf_row_d<K>, gp, K::BS, sm, "kf_row_d", C, B));
+      RC(L.go(&kf_col_e<K>, gp, K::BS, sm, "kf_col_e", C, B, (int)E_RHS, al, 0, n == M - 1 ? 1 : 0, damping));
+      for (int k = 0; k < Kcg; ++k) {
+        RC(L.go(&kf_row_cg<K>, gp, K::BS, sm, "kf_row_cg", C, B, k));
+        RC(L.go(&kf_col_c<K>, gp, K::BS, sm, "kf_col_c", C, B, (int)COL_CG, k));
+        RC(L.go(&kf_row_d<K>, gp, K::BS, sm, "kf_row_d", C, B));
+        RC(L.go(&kf_col_e<K>, gp, K::BS, sm, "kf_col_e", C, B, (int)E_CG, al, k, 0, damping));
+        RC(L.go(&kf_upd<K>, gp, K::BS, sm, "kf_upd", C, B, k, k == Kcg - 1 ? 1 : 0));
       }
     }
-    RC(L.coils(C.xn));
-    return L.go(&k_final, ge, 256, 0, "k_final", C, F.io.xout, F.io.rho_out, F.io.img_out);
+    RC(L.go(&kf_coil_y<K>, gp, K::BS, sm, "kf_coil_y", C, B));
+    RC(L.go(&kf_row_b<K>, gp, K::BS, sm, "kf_row_b", C, B, (int)ROW_COILONLY));
+    return L.go(&kf_final, ge, 256, 0, "kf_final", C, Be);
   }
 
-  // The per-phase frame captured once into a CUDA graph (programmatic
-  // dependent launches between its kernels) and replayed for every frame:
-  // the graph reads and writes plan-owned staging buffers, so a frame is
-  // [copy Y, P, x_prev in] [graph] [copy x^, rho, image out].  The capture is
-  // redone when alpha_0 changes (the alpha_n are kernel arguments).
-  static int frame_graph(nlinv_plan_s* pl, cudaStream_t st, const FrameArgs& F) {
-    const size_t nx = (size_t)pl->nx, NN = (size_t)pl->N * pl->N;
-    const size_t ny = (size_t)pl->J * pl->G * pl->G, np = (size_t)pl->G * pl->G;
-    if (!pl->gmem) {
-      const size_t bytes = align_up(ny * sizeof(float2)) + align_up(np * sizeof(float)) +
-                           3 * align_up(nx * sizeof(float2)) + 2 * align_up(NN * sizeof(float2));
-      CK(cudaMalloc(&pl->gmem, bytes));
-      char* b = (char*)pl->gmem;
-      pl->gy = (float2*)b;
-      b += align_up(ny * sizeof(float2));
-      pl->gp = (float*)b;
-      b += align_up(np * sizeof(float));
-      pl->gxp = (float2*)b;
-      b += align_up(nx * sizeof(float2));
-      pl->gx = (float2*)b;
-      b += align_up(nx * sizeof(float2));
-      pl->grho = (float2*)b;
-      b += align_up(NN * sizeof(float2));
-      pl->gimg = (float2*)b;
-      CK(cudaStreamCreateWithFlags(&pl->gcap, cudaStreamNonBlocking));
+  // Frames io[0..nf) of the plan on the per-phase path: their table is
+  // written to the device (as a kernel argument, so the host array may be
+  // reused at once), then the phase sequence runs -- launched one kernel at
+  // a time (exec_mode 1) or replayed from a CUDA graph captured once per
+  // frame count and alpha_0 (exec_mode 0 and 4).
+  static int phased_run(nlinv_plan_s* pl, cudaStream_t st, const FrameIO* io, int nf, int M, int Kcg,
+                        float damping, const float* alpha) {
+    if (nf <= 0 || nf > kMaxBatch || nf > pl->max_batch) return NLINV_EINVAL;
+    if (!pl->io_dev) CK(cudaMalloc(&pl->io_dev, kMaxBatch * sizeof(FrameIO)));
+    IOTable T;
+    std::memset(&T, 0, sizeof(T));
+    for (int f = 0; f < nf; ++f) T.io[f] = io[f];
+    k_set_io<<<1, kMaxBatch, 0, st>>>(T, nf, pl->io_dev);
+    CKL("k_set_io");
+    if (pl->prm.exec_mode == 1) return phased(pl, st, nf, M, Kcg, damping, alpha, false);
+    nlinv_plan_s::PhaseGraph* g = nullptr;
+    for (auto& e : pl->pgraphs)
+      if (e.nf == nf) g = &e;
+    if (!g) {
+      pl->pgraphs.emplace_back();
+      g = &pl->pgraphs.back();
+      g->nf = nf;
     }
-    if (!pl->gexec || pl->galpha0 != pl->prm.alpha0) {
-      if (pl->gexec) {
-        cudaGraphExecDestroy(pl->gexec);
-        pl->gexec = nullptr;
+    if (!g->exec || g->alpha0 != pl->prm.alpha0) {
+      if (g->exec) {
+        cudaGraphExecDestroy(g->exec);
+        g->exec = nullptr;
       }
-      FrameArgs Fg = F;
-      Fg.io.Y = pl->gy;
-      Fg.io.P = pl->gp;
-      Fg.io.xprev = pl->gxp;
-      Fg.io.xout = pl->gx;
-      Fg.io.rho_out = pl->grho;
-      Fg.io.img_out = pl->gimg;
+      if (!pl->gcap) CK(cudaStreamCreateWithFlags(&pl->gcap, cudaStreamNonBlocking));
       CK(cudaStreamBeginCapture(pl->gcap, cudaStreamCaptureModeThreadLocal));
-      const int rc = per_phase(pl, pl->gcap, Fg, true);
+      const int rc = phased(pl, pl->gcap, nf, M, Kcg, damping, alpha, true);
       cudaGraph_t graph = nullptr;
       const cudaError_t ec = cudaStreamEndCapture(pl->gcap, &graph);
       if (rc != NLINV_OK) {
@@ -762,29 +865,21 @@ struct Ops {
         return rc;
       }
       CK(ec);
-      const cudaError_t ei = cudaGraphInstantiate(&pl->gexec, graph, 0);
+      const cudaError_t ei = cudaGraphInstantiate(&g->exec, graph, 0);
       cudaGraphDestroy(graph);
       CK(ei);
-      pl->galpha0 = pl->prm.alpha0;
+      g->alpha0 = pl->prm.alpha0;
     }
-    CK(cudaMemcpyAsync(pl->gy, F.io.Y, ny * sizeof(float2), cudaMemcpyDeviceToDevice, st));
-    CK(cudaMemcpyAsync(pl->gp, F.io.P, np * sizeof(float), cudaMemcpyDeviceToDevice, st));
-    if (F.io.xprev) {
-      CK(cudaMemcpyAsync(pl->gxp, F.io.xprev, nx * sizeof(float2), cudaMemcpyDeviceToDevice, st));
-    } else {
-      k_initial_value<<<plan_grid((int)((nx + 255) / 256), 1), 256, 0, st>>>((int)nx, (int)NN, pl->gxp);
-      CKL("k_initial_value");
-    }
-    CK(cudaGraphLaunch(pl->gexec, st));
-    CK(cudaMemcpyAsync(F.io.xout, pl->gx, nx * sizeof(float2), cudaMemcpyDeviceToDevice, st));
-    if (F.io.rho_out)
-      CK(cudaMemcpyAsync(F.io.rho_out, pl->grho, NN * sizeof(float2), cudaMemcpyDeviceToDevice, st));
-    if (F.io.img_out)
-      CK(cudaMemcpyAsync(F.io.img_out, pl->gimg, NN * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+    CK(cudaGraphLaunch(g->exec, st));
     return NLINV_OK;
   }
 
   static int batch(const nlinv_plan_s* pl, cudaStream_t st, const BatchArgs& B, int grid) {
+    const int mode = pl->prm.exec_mode;
+    bool waits = false;
+    for (int f = 0; f < B.nf; ++f) waits = waits || B.io[f].wait || B.io[f].done;
+    if ((mode == 0 || mode == 1 || mode == 4) && !waits)
+      return phased_run(const_cast<nlinv_plan_s*>(pl), st, B.io, B.nf, B.M, B.K, B.damping, B.alpha);
     Ctx C = pl->C;
     BatchArgs Ba = B;
     CK(cudaMemsetAsync(C.bar, 0, (size_t)B.nf * kBarStride * sizeof(unsigned), st));

@@ -463,9 +463,10 @@ int nlinv_plan_destroy(nlinv_plan_t pl) {
   for (cudaEvent_t e2 : pl->vjp_ev) cudaEventDestroy(e2);
   if (pl->vjp_fork) cudaEventDestroy(pl->vjp_fork);
   if (pl->vjp_host) cudaFreeHost(pl->vjp_host);
-  if (pl->gexec) cudaGraphExecDestroy(pl->gexec);
+  for (auto& g : pl->pgraphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
   if (pl->gcap) cudaStreamDestroy(pl->gcap);
-  cudaFree(pl->gmem);
+  cudaFree(pl->io_dev);
   if (pl->ev_fork) cudaEventDestroy(pl->ev_fork);
   if (pl->ev_done) cudaEventDestroy(pl->ev_done);
   if (pl->aux) cudaStreamDestroy(pl->aux);

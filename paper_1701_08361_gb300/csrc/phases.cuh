@@ -155,6 +155,10 @@ struct Cfg {
   static constexpr int NBUF = 1;
   static constexpr int SMEM = SMEM_X + NBUF * CT;  // dynamic smem bytes
   static_assert(SMEM <= SMEM_LIM, "staging buffer does not fit");
+  // CTAs per SM the single-call operator kernels (DF, DF^H, the normal
+  // operator: many of them run side by side on several streams) are compiled
+  // for: two where two blocks of at most 256 threads fit the shared memory
+  static constexpr int OMINB = (BS <= 256 && 2 * (SMEM + 1024) <= 228 * 1024) ? 2 : 1;
   static_assert(TW % 4 == 0 && (G % 2) == 0, "16-byte staging chunks (even rows of float2)");
   static_assert(2 * NR <= G, "the field of view is at most half the grid");
   // the block reductions use full-warp shuffles over blockDim / 32 warps
