@@ -172,14 +172,22 @@ def dist_init(args):
 
 
 def barrier_max(x, world):
-    """Barrier, then the maximum of x over ranks."""
+    """Barrier, then the maximum of x over ranks (on the GPU under NCCL, on
+    the host under gloo)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_seed(rank):
+    """Seed of rank's replica stream: each rank reconstructs its own
+    independent stream (no data is exchanged between ranks)."""
+    return CFG["seed"] + 1000 * rank
 
 
 def barrier(world):
@@ -197,7 +205,7 @@ def run_ours(args):
     N, J, U = CFG["N"], CFG["J"], CFG["U"]
     G = 2 * N
     F = args.frames_per_step
-    seed = CFG["seed"] + 1000 * rank          # independent replica stream per rank
+    seed = replica_seed(rank)                 # independent replica stream per rank
     raw = make_raw_frames(F, seed)
     p = L.nlinv_default_params(N, J)
     p.n_turns = U
