@@ -331,10 +331,11 @@ def run_ours(args):
     }
     if path in (1, 4):
         M, C = CFG["M"], CFG["CG"]
-        # init, per Newton step 5 right-hand-side and 5 per CG iteration,
-        # the final coil maps (2) and the outputs (the same kernels whether
-        # launched one by one or replayed from the CUDA graph)
-        out["gpu_launches"] = K * F * (1 + M * (5 + 5 * C) + 2 + 1)
+        # the pointer table, init, per Newton step 5 right-hand-side phases,
+        # 4 per CG iteration and the CG's last step, the final coil maps (2)
+        # and the outputs (the same kernels whether launched one by one or
+        # replayed from the CUDA graph)
+        out["gpu_launches"] = K * F * (2 + M * (5 + 4 * C + (1 if C > 0 else 0)) + 2 + 1)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_frames)
     if rank == 0 and args.plain_loop:

@@ -91,6 +91,11 @@ __host__ __device__ __forceinline__ Ctx frame_ctx(Ctx C, size_t off) {
   NLINV_ADV(float2, part);
   NLINV_ADV(float2, Hr);
   NLINV_ADV(float2, vold);
+  NLINV_ADV(float2, sb[0]);
+  NLINV_ADV(float2, sb[1]);
+  NLINV_ADV(float2, Hw);
+  NLINV_ADV(float2, Hs);
+  NLINV_ADV(double, cgs);
 #undef NLINV_ADV
   return C;
 }

@@ -14,6 +14,7 @@
 #include <mutex>
 
 #include "common.h"
+#include "phases_cgr.cuh"
 
 // CTAs per SM the frame-indexed phase kernels (kf_*) are compiled for (caps
 // their registers; one measured fastest at the 320 grid: two cost 34 % per
@@ -158,7 +159,7 @@ __global__ void __launch_bounds__(K::BS, NLINV_PMINB) kf_row_b(Ctx C0, PhaseBatc
 }
 
 // COL_RHS: column pass of the residual against the frame's data;
-// COL_CG: column pass of CG iteration k (both with the frame's PSF)
+// COL_TOEP: the PSF column pass of a CG iteration (both with the frame's PSF)
 template <class K>
 __global__ void __launch_bounds__(K::BS, NLINV_PMINB) kf_col_c(Ctx C0, PhaseBatch B, int mode, int k) {
   int f;
@@ -177,41 +178,39 @@ __global__ void __launch_bounds__(K::BS, NLINV_PMINB) kf_row_d(Ctx C0, PhaseBatc
 }
 
 // E_RHS: the Newton right-hand side r_0 (the last step regularised towards
-// damping * x_last when `last` and the frame has one); E_CG: A p_k of CG
-// iteration k and the partials of Re<p_k, A p_k>
-template <class K>
-__global__ void __launch_bounds__(K::BS, NLINV_PMINB) kf_col_e(Ctx C0, PhaseBatch B, int mode, float alpha,
-                                                               int k, int last, float damping) {
+// damping * x_last when `last` and the frame has one) and H r_0;
+// E_CGR: w_k = A r_k, the partials of Re<r_k, w_k> and |r_k|^2, and H w_k
+template <class K, int MODE>
+__global__ void __launch_bounds__(K::BS, NLINV_PMINB) kf_col_e(Ctx C0, PhaseBatch B, float alpha, int k,
+                                                               int last, float damping) {
   int f;
   const Ctx C = frame_entry(C0, B, f);
   extern __shared__ float2 sm[];
   __shared__ float2 sred[32];
-  if (mode == E_RHS) {
+  if (MODE == E_RHS) {
     const float2* xl = last ? B.io[f].xlast : nullptr;
     phase_col_e<K, E_RHS>(C, sm, sred, alpha, 0, C.kb, C.s, nullptr, nullptr, C.rb[0], C.Hr, SLOT_RR0, xl,
                           xl ? damping : 1.f);
   } else {
-    phase_col_e<K, E_CG>(C, sm, sred, alpha, k, C.kb, C.s, C.pb[(k + 1) & 1], C.pb[k & 1], C.q, nullptr,
-                         SLOT_PQ);
+    phase_col_e<K, E_CGR>(C, sm, sred, alpha, k, C.kb, C.s, nullptr, C.rb[k & 1], C.q, C.Hw, SLOT_PQ);
   }
 }
 
+// the row pass of r_k, with step k-1's update (phases_cgr.cuh)
 template <class K>
-__global__ void __launch_bounds__(K::BS, NLINV_PMINB) kf_row_cg(Ctx C0, PhaseBatch B, int k) {
+__global__ void __launch_bounds__(K::BS, NLINV_PMINB) kf_row_cgr(Ctx C0, PhaseBatch B, int k) {
   int f;
   const Ctx C = frame_entry(C0, B, f);
   extern __shared__ float2 sm[];
-  __shared__ float2 sred[32];
-  phase_row_cg<K>(C, sm, sred, k, C.pb[(k + 1) & 1], C.pb[k & 1], C.v);
+  phase_row_cgr<K>(C, sm, k);
 }
 
+// the CG's last step: x^_{n+1} = x^_n + x_K
 template <class K>
-__global__ void __launch_bounds__(K::BS, NLINV_PMINB) kf_upd(Ctx C0, PhaseBatch B, int k, int last) {
+__global__ void __launch_bounds__(K::BS, NLINV_PMINB) kf_cgr_final(Ctx C0, PhaseBatch B, int Kcg) {
   int f;
   const Ctx C = frame_entry(C0, B, f);
-  extern __shared__ float2 sm[];
-  __shared__ float2 sred[32];
-  phase_upd<K>(C, sm, sred, k, last != 0, C.pb[k & 1]);
+  phase_cgr_final<K>(C, Kcg);
 }
 
 // outputs: x^, rho, rho * sqrt(sum_j |c_j|^2)
@@ -518,9 +517,10 @@ int set_smem_attrs() {
     CK(cudaFuncSetAttribute(kf_row_b<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(kf_col_c<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(kf_row_d<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
-    CK(cudaFuncSetAttribute(kf_col_e<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
-    CK(cudaFuncSetAttribute(kf_row_cg<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
-    CK(cudaFuncSetAttribute(kf_upd<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
+    CK(cudaFuncSetAttribute(kf_col_e<K, E_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
+    CK(cudaFuncSetAttribute(kf_col_e<K, E_CGR>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
+    CK(cudaFuncSetAttribute(kf_row_cgr<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
+    CK(cudaFuncSetAttribute(kf_cgr_final<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(k_frame<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(k_batch<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
   }
@@ -702,9 +702,10 @@ struct Ops {
     // one-phase launches: the co-resident CTAs of the phase kernels, but no
     // more than the largest phase has items (+ the elementwise share)
     int occ = 1 << 20;
-    const void* kf[] = {(const void*)kf_coil_y<K>, (const void*)kf_row_b<K>, (const void*)kf_col_c<K>,
-                        (const void*)kf_row_d<K>,  (const void*)kf_col_e<K>, (const void*)kf_row_cg<K>,
-                        (const void*)kf_upd<K>};
+    const void* kf[] = {(const void*)kf_coil_y<K>,        (const void*)kf_row_b<K>,
+                        (const void*)kf_col_c<K>,         (const void*)kf_row_d<K>,
+                        (const void*)kf_col_e<K, E_RHS>,  (const void*)kf_col_e<K, E_CGR>,
+                        (const void*)kf_row_cgr<K>,       (const void*)kf_cgr_final<K>};
     for (const void* fn : kf) {
       int o = 0;
       CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, K::BS, K::SMEM));
@@ -813,14 +814,15 @@ struct Ops {
       RC(L.go(&kf_row_b<K>, gp, K::BS, sm, "kf_row_b", C, B, (int)ROW_COIL));
       RC(L.go(&kf_col_c<K>, gp, K::BS, sm, "kf_col_c", C, B, (int)COL_RHS, 0));
       RC(L.go(&kf_row_d<K>, gp, K::BS, sm, "kf_row_d", C, B));
-      RC(L.go(&kf_col_e<K>, gp, K::BS, sm, "kf_col_e", C, B, (int)E_RHS, al, 0, n == M - 1 ? 1 : 0, damping));
+      RC(L.go(&kf_col_e<K, E_RHS>, gp, K::BS, sm, "kf_col_e", C, B, al, 0, n == M - 1 ? 1 : 0, damping));
+      // CG with the operator applied to the residual: four phases per iteration
       for (int k = 0; k < Kcg; ++k) {
-        RC(L.go(&kf_row_cg<K>, gp, K::BS, sm, "kf_row_cg", C, B, k));
-        RC(L.go(&kf_col_c<K>, gp, K::BS, sm, "kf_col_c", C, B, (int)COL_CG, k));
+        RC(L.go(&kf_row_cgr<K>, gp, K::BS, sm, "kf_row_cgr", C, B, k));
+        RC(L.go(&kf_col_c<K>, gp, K::BS, sm, "kf_col_c", C, B, (int)COL_TOEP, k));
         RC(L.go(&kf_row_d<K>, gp, K::BS, sm, "kf_row_d", C, B));
-        RC(L.go(&kf_col_e<K>, gp, K::BS, sm, "kf_col_e", C, B, (int)E_CG, al, k, 0, damping));
-        RC(L.go(&kf_upd<K>, gp, K::BS, sm, "kf_upd", C, B, k, k == Kcg - 1 ? 1 : 0));
+        RC(L.go(&kf_col_e<K, E_CGR>, gp, K::BS, sm, "kf_col_e", C, B, al, k, 0, damping));
       }
+      if (Kcg > 0) RC(L.go(&kf_cgr_final<K>, gp, K::BS, sm, "kf_cgr_final", C, B, Kcg));
     }
     RC(L.go(&kf_coil_y<K>, gp, K::BS, sm, "kf_coil_y", C, B));
     RC(L.go(&kf_row_b<K>, gp, K::BS, sm, "kf_row_b", C, B, (int)ROW_COILONLY));

@@ -364,6 +364,11 @@ int nlinv_plan(nlinv_plan_t* out, const nlinv_params_t* p, const float* psf, nli
   take(nx * f2);                         // 18 r1 (second residual buffer)
   take((size_t)J * N * Gc * f2);         // 19 Hr
   take((size_t)J * N * G * f2);          // 20 vold
+  take(nx * f2);                         // 21 s_0 (A p of the per-phase CG)
+  take(nx * f2);                         // 22 s_1
+  take((size_t)J * N * Gc * f2);         // 23 Hw
+  take((size_t)J * N * Gc * f2);         // 24 Hs
+  take(6 * sizeof(double));              // 25 cgs
   pl->fstride = tot - shared_bytes;
   tot = shared_bytes + pl->fstride * (size_t)pl->max_batch;
   e = cudaMalloc(&pl->mem, tot);
@@ -404,6 +409,11 @@ int nlinv_plan(nlinv_plan_t* out, const nlinv_params_t* p, const float* psf, nli
   C.part = (float2*)(base + off[17]);
   C.Hr = (float2*)(base + off[19]);
   C.vold = (float2*)(base + off[20]);
+  C.sb[0] = (float2*)(base + off[21]);
+  C.sb[1] = (float2*)(base + off[22]);
+  C.Hw = (float2*)(base + off[23]);
+  C.Hs = (float2*)(base + off[24]);
+  C.cgs = (double*)(base + off[25]);
   C.spin_limit = pl->prm.spin_limit;
 
   // host tables in FP64, rounded once

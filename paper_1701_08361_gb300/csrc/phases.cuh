@@ -98,7 +98,7 @@ enum { DEV_ETIMEOUT = -4, DEV_ENUMERIC = -5 };
 
 enum RowMode { ROW_COIL = 0, ROW_COILONLY = 1, ROW_LIN = 2, ROW_IMG = 3 };
 enum ColMode { COL_TOEP = 0, COL_RHS = 1, COL_FWD = 2, COL_INV = 3, COL_CG = 4 };
-enum EMode { E_CG = 0, E_RHS = 1, E_DFH = 2, E_NORMAL = 3 };
+enum EMode { E_CG = 0, E_RHS = 1, E_DFH = 2, E_NORMAL = 3, E_CGR = 4 };
 
 struct Ctx {
   int N, G, Gc, J, nx, U;
@@ -112,6 +112,13 @@ struct Ctx {
   float2* pb[2];        // CG direction p_k lives in pb[k & 1]
   float2* Hr;           // y pass of W^-1 applied to r: [J][N][Gc]
   float2* vold;         // row pass of the previous CG direction p_{k-1}: [J][N][G]
+  // the per-phase path's CG (operator applied to the residual): s_k = A p_k
+  // in sb[k & 1], H w_k and H s_k ([J][N][Gc]), and (gamma, a) of the last
+  // two steps in cgs[2 (k & 1)], cgs[2 (k & 1) + 1], gamma_0 in cgs[4], the
+  // stop flag in cgs[5]
+  float2* sb[2];
+  float2 *Hw, *Hs;
+  double* cgs;
   float2* part;         // [NSLOT][kMaxPart] per-CTA partials (float pairs hi, lo)
   int* err;             // latched device error
   unsigned* bar;        // barrier counter of the CTAs working on this frame
@@ -1045,8 +1052,10 @@ __device__ NLINV_PHASE void phase_row_d(const Ctx& C, float2* sm, const float2* 
 //           x_ref = xr_s * xr_in when xr_in is given (else the plan's x_ref)
 // E_DFH   : out = DF^H z
 // E_NORMAL: out = (DF^H P DF + alpha) dx                      (dx = p_new)
-// H is the y pass of W^-1 (as phase A computes it); for E_RHS the column
-// values are still in registers, so it costs one more exchange.
+// E_CGR   : w = out = (DF^H P DF + alpha) r_k (r_k = p_new), partials of
+//           Re<r_k, w> (slot) and |r_k|^2 (SLOT_RR0); hout = H w
+// H is the y pass of W^-1 (as phase A computes it); for E_RHS and E_CGR the
+// column values are still in registers, so it costs one more exchange.
 template <class K, int mode>
 __device__ NLINV_PHASE void phase_col_e(const Ctx& C, float2* sm, float2* sred, float alpha, int k,
                             const float2* kbin, const float2* sin, const float2* p_old,
@@ -1056,12 +1065,13 @@ __device__ NLINV_PHASE void phase_col_e(const Ctx& C, float2* sm, float2* sred, 
   constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW;
   const int N = C.N, Gc = C.Gc, J = C.J, NN = N * N;
   const int t = phase_tid();
-  const bool withH = (mode == E_RHS);
+  const bool withH = (mode == E_RHS || mode == E_CGR);
   STG_BEGIN();
   const int tiles = (Gc + TW - 1) / TW;
   const int items = J * tiles;
   const Roles R = roles(C, items);
   float acc = 0.f;   // this thread's few terms; CTA and grid sums in float pairs
+  float acc2 = 0.f;  // E_CGR: |r_k|^2
   if (R.items) for (int it = C.bid; it < items; it += R.istride) {
     const int j = it / tiles;
     const int fx = (it - j * tiles) * TW + (t % TW);
@@ -1087,7 +1097,7 @@ __device__ NLINV_PHASE void phase_col_e(const Ctx& C, float2* sm, float2* sred, 
       if (ok && iy >= 0) {
         const size_t e = (size_t)NN + ((size_t)j * Gc + iy) * Gc + fx;
         dv[k1] = __ldg(C.dinv + iy * Gc + fx);
-        if (mode == E_CG || mode == E_NORMAL) {
+        if (mode == E_CG || mode == E_NORMAL || mode == E_CGR) {
           o1[k1] = ldcg(p_new + e);
         } else if (mode == E_RHS) {
           o1[k1] = ldcg(C.xn + e);
@@ -1125,9 +1135,10 @@ __device__ NLINV_PHASE void phase_col_e(const Ctx& C, float2* sm, float2* sred, 
         const size_t e = (size_t)NN + ((size_t)j * Gc + iy) * Gc + fx;
         const float2 val = cscale(b[k1], C.inv_G * dv[k1]);
         float2 res;
-        if (mode == E_CG) {
+        if (mode == E_CG || mode == E_CGR) {
           res = cfma(o1[k1], alpha, val);
           acc = fmaf(o1[k1].x, res.x, fmaf(o1[k1].y, res.y, acc));
+          if (mode == E_CGR) acc2 = fmaf(o1[k1].x, o1[k1].x, fmaf(o1[k1].y, o1[k1].y, acc2));
         } else if (mode == E_RHS) {
           res = cfma(cfma(o2[k1], -xr_s, o1[k1]), -alpha, val);
           acc = fmaf(res.x, res.x, fmaf(res.y, res.y, acc));
@@ -1171,7 +1182,7 @@ __device__ NLINV_PHASE void phase_col_e(const Ctx& C, float2* sm, float2* sred, 
   // rho part: channel sum of s_j = conj(c_j) t_j (needs no CG scalar)
   if (R.elems) for (int e = R.ebid * blockDim.x + t; e < NN; e += R.enb * blockDim.x) {
     float2 o = czero(), o2v = czero();
-    if (mode == E_CG || mode == E_NORMAL) o = ldcg(p_new + e);
+    if (mode == E_CG || mode == E_NORMAL || mode == E_CGR) o = ldcg(p_new + e);
     if (mode == E_RHS) {
       o = ldcg(C.xn + e);
       o2v = ldcg(xr + e);
@@ -1179,10 +1190,11 @@ __device__ NLINV_PHASE void phase_col_e(const Ctx& C, float2* sm, float2* sred, 
     float2 sv = czero();
 #pragma unroll 8
     for (int j = 0; j < J; ++j) sv = cadd(sv, ldcg(sin + (size_t)j * NN + e));
-    if (mode == E_CG) {
+    if (mode == E_CG || mode == E_CGR) {
       const float2 qv = cfma(o, alpha, sv);
       out[e] = qv;
       acc = fmaf(o.x, qv.x, fmaf(o.y, qv.y, acc));
+      if (mode == E_CGR) acc2 = fmaf(o.x, o.x, fmaf(o.y, o.y, acc2));
     } else if (mode == E_RHS) {
       const float2 bv = cfma(cfma(o2v, -xr_s, o), -alpha, sv);
       out[e] = bv;
@@ -1194,7 +1206,8 @@ __device__ NLINV_PHASE void phase_col_e(const Ctx& C, float2* sm, float2* sred, 
     }
   }
   STG(2, 3);
-  if (mode == E_CG || mode == E_RHS) block_partial(C, acc, slot, sred);
+  if (mode == E_CG || mode == E_RHS || mode == E_CGR) block_partial(C, acc, slot, sred);
+  if (mode == E_CGR) block_partial(C, acc2, SLOT_RR0, sred);
   STG(2, 4);
 }
 
