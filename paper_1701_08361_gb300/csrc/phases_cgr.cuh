@@ -16,6 +16,34 @@
 
 namespace nlinv {
 
+// slot_sum of two slots in one pass: both slots' loads are issued before
+// any add (one L2 round trip instead of two); each sum is formed in the same
+// order as slot_sum forms it
+__device__ __forceinline__ void slot_sum2(const Ctx& C, int sa, int sb, DF32& ra, DF32& rb) {
+  const int l = threadIdx.x & 31;
+  const float2* A = C.part + sa * kMaxPart;
+  const float2* B = C.part + sb * kMaxPart;
+  DF32 a{0.f, 0.f}, b{0.f, 0.f};
+  for (int base = 0; base < C.nb; base += 32 * 8) {
+    float2 va[8], vb[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = base + u * 32 + l;
+      va[u] = (i < C.nb) ? __ldcg(A + i) : make_float2(0.f, 0.f);
+      vb[u] = (i < C.nb) ? __ldcg(B + i) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      a = df_add(a, DF32{va[u].x, va[u].y});
+      b = df_add(b, DF32{vb[u].x, vb[u].y});
+    }
+  }
+  a = df_warp_sum(a);
+  b = df_warp_sum(b);
+  ra = DF32{__shfl_sync(0xffffffffu, a.hi, 0), __shfl_sync(0xffffffffu, a.lo, 0)};
+  rb = DF32{__shfl_sync(0xffffffffu, b.hi, 0), __shfl_sync(0xffffffffu, b.lo, 0)};
+}
+
 // Convergence to the rounding floor: once gamma_k <= kCgrFloor gamma_0, the
 // denominator delta_k - beta_k gamma_k / a_{k-1} is the difference of two
 // rounding-level terms and may lose its sign; the CG then stops (a = 0 for the
@@ -30,8 +58,8 @@ constexpr double kCgrFloor = 1e-8;
 __device__ __forceinline__ void cgr_scalars(const Ctx& C, int k, Scal2& a, Scal2& beta) {
   __shared__ Scal2 s_ab[2];
   if (threadIdx.x < 32) {
-    const DF32 gs = slot_sum(C, SLOT_RR0);
-    const DF32 ds = slot_sum(C, SLOT_PQ);
+    DF32 gs, ds;
+    slot_sum2(C, SLOT_RR0, SLOT_PQ, gs, ds);
     if (threadIdx.x == 0) {
       const double g = df_to_double(gs), d = df_to_double(ds);
       const double g0 = k == 1 ? g : C.cgs[4];
@@ -83,8 +111,9 @@ __device__ __forceinline__ float2 cgr_r(float2 r_old, float2 s, Scal2 na) { retu
 // s_{k-1}) and its y-transformed coil part by linearity of H,
 //   H s_{k-1} = H w_{k-1} + beta H s_{k-2},  H r_k = H r_{k-1} - a H s_{k-1},
 // both written back in place (every element belongs to one thread of one
-// item).  Then every CTA applies step k-1 to its share of the whole vector:
-// p_{k-1}, s_{k-1}, x_k, r_k (new buffers; the old ones are only read).
+// item).  Every CTA first applies step k-1 to its share of the whole vector:
+// p_{k-1}, s_{k-1}, x_k, r_k (new buffers; the old ones are only read, so the
+// items may form their rows from them at the same time).
 template <class K>
 __device__ NLINV_PHASE void phase_row_cgr(const Ctx& C, float2* sm, int k) {
   constexpr int G1 = K::G1, G2 = K::G2, G = K::G, TW = K::TW, RS = K::RS;
@@ -100,8 +129,46 @@ __device__ NLINV_PHASE void phase_row_cgr(const Ctx& C, float2* sm, int k) {
   const float2* p_old = C.pb[k & 1];         // p_{k-2}
   float2* p_new = C.pb[(k + 1) & 1];         // p_{k-1}
   Scal2 a{0.f, 0.f}, beta{0.f, 0.f};
+  // step k-1 on this CTA's share of the whole vector; the first round's loads
+  // are issued before the scalars are fetched, so the two latencies overlap
+  float2 rp[EU], wv[EU], so[EU], po[EU], xv[EU];
+  const int stride = C.nb * blockDim.x;
+  auto load = [&](int base) {
+#pragma unroll
+    for (int u = 0; u < EU; ++u) {
+      const int e = base + t + u * stride;
+      rp[u] = wv[u] = so[u] = po[u] = xv[u] = czero();
+      if (e < C.nx) {
+        rp[u] = ldcg(r_old + e);
+        wv[u] = ldcg(w + e);
+        if (rec) {
+          so[u] = ldcg(s_old + e);
+          po[u] = ldcg(p_old + e);
+          xv[u] = ldcg(C.xcg + e);
+        }
+      }
+    }
+  };
+  if (upd) load(C.bid * blockDim.x);
   if (upd) cgr_scalars(C, k, a, beta);
   const Scal2 na{-a.hi, -a.lo};
+  if (upd) {
+    for (int base = C.bid * blockDim.x; base < C.nx; base += EU * stride) {   // CTA-uniform
+      if (base != C.bid * blockDim.x) load(base);
+#pragma unroll
+      for (int u = 0; u < EU; ++u) {
+        const int e = base + t + u * stride;
+        if (e < C.nx) {
+          const float2 s = cgr_s(wv[u], so[u], beta, rec);
+          const float2 p = rec ? axpy2(po[u], beta, rp[u]) : rp[u];
+          s_new[e] = s;
+          p_new[e] = p;
+          C.xcg[e] = axpy2(p, a, xv[u]);
+          r_new[e] = cgr_r(rp[u], s, na);
+        }
+      }
+    }
+  }
   const int groups = (N + TW - 1) / TW;
   const int items = J * groups;
   for (int it = C.bid; it < items; it += C.nb) {
@@ -191,39 +258,6 @@ __device__ NLINV_PHASE void phase_row_cgr(const Ctx& C, float2* sm, int k) {
       }
     }
     __syncthreads();
-  }
-  // step k-1 on this CTA's share of the whole vector (a round's loads first)
-  if (upd) {
-    const int stride = C.nb * blockDim.x;
-    for (int base = C.bid * blockDim.x; base < C.nx; base += EU * stride) {
-      float2 rp[EU], wv[EU], so[EU], po[EU], xv[EU];
-#pragma unroll
-      for (int u = 0; u < EU; ++u) {
-        const int e = base + t + u * stride;
-        rp[u] = wv[u] = so[u] = po[u] = xv[u] = czero();
-        if (e < C.nx) {
-          rp[u] = ldcg(r_old + e);
-          wv[u] = ldcg(w + e);
-          if (rec) {
-            so[u] = ldcg(s_old + e);
-            po[u] = ldcg(p_old + e);
-            xv[u] = ldcg(C.xcg + e);
-          }
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < EU; ++u) {
-        const int e = base + t + u * stride;
-        if (e < C.nx) {
-          const float2 s = cgr_s(wv[u], so[u], beta, rec);
-          const float2 p = rec ? axpy2(po[u], beta, rp[u]) : rp[u];
-          s_new[e] = s;
-          p_new[e] = p;
-          C.xcg[e] = axpy2(p, a, xv[u]);
-          r_new[e] = cgr_r(rp[u], s, na);
-        }
-      }
-    }
   }
 }
 
