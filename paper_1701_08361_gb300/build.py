@@ -51,25 +51,28 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(d) <= t for d in deps())
 
 
-def units(extra=(), sizes=None):
+def units(extra=(), sizes=None, obj=OBJ):
     """(object path, nvcc compile command) of every translation unit."""
     base = [nvcc(), *FLAGS, *ARCH, *extra, "-I", INCLUDE, "-I", CSRC, "-c"]
-    out = [(os.path.join(OBJ, "nlinv.o"), base + [os.path.join(CSRC, "nlinv.cu")])]
+    out = [(os.path.join(obj, "nlinv.o"), base + [os.path.join(CSRC, "nlinv.cu")])]
     for g1, g2, n, tw, mb in (sizes or grid_sizes()):
-        o = os.path.join(OBJ, f"grid_{g1}x{g2}_{n}.o")
+        o = os.path.join(obj, f"grid_{g1}x{g2}_{n}.o")
         out.append((o, base + [f"-DNLINV_G1={g1}", f"-DNLINV_G2={g2}", f"-DNLINV_NR={n}", f"-DNLINV_TWU={tw}",
                                f"-DNLINV_MINBU={mb}", os.path.join(CSRC, "grid.cu")]))
     return out
 
 
-def build(force: bool = False, verbose: bool = False, extra=(), sizes=None, lib: str = LIB) -> str:
+def build(force: bool = False, verbose: bool = False, extra=(), sizes=None, lib: str = LIB, obj: str = OBJ,
+          workers: int = 0) -> str:
     """Compile every unit (in parallel) and link libnlinv.so (static cudart).
     `sizes` restricts the grid sizes (quick builds; the others are then
-    unsupported), `extra` adds nvcc flags, `lib` names the output."""
+    unsupported), `extra` adds nvcc flags, `lib` names the output, `obj` the
+    folder of the objects (one per concurrent build), `workers` caps the
+    parallel compilers (0: one per core)."""
     if not force and lib == LIB and not extra and sizes is None and up_to_date():
         return lib
-    os.makedirs(OBJ, exist_ok=True)
-    jobs = units(extra, sizes)
+    os.makedirs(obj, exist_ok=True)
+    jobs = units(extra, sizes, obj)
 
     def run(job):
         o, cmd = job
@@ -79,7 +82,8 @@ def build(force: bool = False, verbose: bool = False, extra=(), sizes=None, lib:
         subprocess.run(cmd, check=True)
         return o
 
-    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 1))) as ex:
+    cap = workers if workers > 0 else (os.cpu_count() or 1)
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(jobs), cap))) as ex:
         objs = list(ex.map(run, jobs))
     subprocess.run([nvcc(), *ARCH, "-shared", "-o", lib + ".tmp", *objs], check=True)
     os.replace(lib + ".tmp", lib)

@@ -49,7 +49,7 @@
 // elementwise parts: elements per thread per round, and the fewest CTAs left
 // over for them before a phase splits its CTAs between items and elements
 #ifndef NLINV_EU
-#define NLINV_EU 4
+#define NLINV_EU 2
 #endif
 #ifndef NLINV_ELEM_CTAS
 #define NLINV_ELEM_CTAS 32

@@ -143,6 +143,112 @@ def tuned_params(N, J, M=7, K=10, gamma=(1.0, 2.0), db=DB_PATH, measure_if_missi
     return p
 
 
+# ------------------------------------------------ compile-time knobs
+# Per compiled grid the tile width TW (columns of a column item, rows of a row
+# item), the elements per thread and round of the elementwise parts
+# (NLINV_EU) and the CTAs per SM the frame-indexed phase kernels are compiled
+# for (NLINV_PMINB) are fixed when the library is built.  compile_sweep
+# builds one library per variant (only this grid's unit, all variants in
+# parallel, each in its own object folder), times each in a child process on
+# the default execution path and records every time and the fastest.
+
+def _fits(g1, g2, n, tw, mb, stage_psf=0):
+    """Whether Cfg<g1, g2, n, tw, mb> compiles: 16-byte staging chunks, whole
+    warps within 1024 threads, the shared memory of one CTA within the limit
+    for mb CTAs per SM (the conditions the Cfg static_asserts check)."""
+    G, mx = g1 * g2, max(g1, g2)
+    bs = (tw * mx + 31) // 32 * 32
+    smem = tw * (G + mx) * 8 + 2 * n * tw * 8 + (G * tw * 4 if stage_psf else 0)
+    lim = 227 * 1024 if mb == 1 else 228 * 1024 // mb - 1024
+    return tw % 4 == 0 and G % 2 == 0 and bs <= 1024 and smem <= lim and 2 * n <= G
+
+
+def built_in_knob(name):
+    """The library's default of a compile-time knob (the #define in the
+    kernel sources)."""
+    import re
+    src = open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc", "phases.cuh")).read()
+    m = re.search(r"#define %s (\d+)" % name, src)
+    if not m:
+        src = open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc", "grid.cuh")).read()
+        m = re.search(r"#define %s (\d+)" % name, src)
+    return int(m.group(1))
+
+
+def compile_variants(N, G=None, tws=(8, 12, 16), eus=(2, 4, 8), pminbs=(1, 2)):
+    """Variants of the compiled grid for (G, N) (G = 2N by default): the
+    built-in one, each tile width in `tws`, each EU in `eus` and each PMINB in
+    `pminbs` (one knob changed at a time).  Returns dicts with the grid tuple
+    (G1, G2, N, TW, MINB) and the nvcc -D flags."""
+    from . import build as B
+    G = 2 * N if G is None else G
+    base = [t for t in B.grid_sizes() if t[0] * t[1] == G and t[2] == N]
+    if not base:
+        raise ValueError(f"no compiled grid for G={G}, N={N}")
+    g1, g2, n, tw0, mb = base[0]
+    eu0, pm0 = built_in_knob("NLINV_EU"), built_in_knob("NLINV_PMINB")
+    out = [dict(grid=(g1, g2, n, tw0, mb), eu=eu0, pminb=pm0)]
+    out += [dict(grid=(g1, g2, n, tw, mb), eu=eu0, pminb=pm0) for tw in tws if tw != tw0]
+    out += [dict(grid=(g1, g2, n, tw0, mb), eu=eu, pminb=pm0) for eu in eus if eu != eu0]
+    out += [dict(grid=(g1, g2, n, tw0, mb), eu=eu0, pminb=pm) for pm in pminbs if pm != pm0]
+    out = [v for v in out if _fits(*v["grid"])]
+    for v in out:
+        v["flags"] = [f"-DNLINV_EU={v['eu']}", f"-DNLINV_PMINB={v['pminb']}"]
+        v["name"] = "tw{}_eu{}_pm{}".format(v["grid"][3], v["eu"], v["pminb"])
+    return out
+
+
+def _time_in_child(lib, N, J, G, M, K, frames):
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import json, sys; sys.path.insert(0, %r); from paper_1701_08361_gb300 import tune as T; "
+            "ms, path = T.measure(%d, %d, dict(G=%d, exec_mode=0, cluster_cs=0), %d, %d, frames=%d); "
+            "print(json.dumps(dict(ms=ms, path=list(path))))" % (root, N, J, G, M, K, frames))
+    env = dict(os.environ, NLINV_LIB=lib)
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        return None, r.stderr.strip().splitlines()[-1:] or ["failed"]
+    return json.loads(r.stdout.strip().splitlines()[-1])["ms"], None
+
+
+def compile_sweep(N, J, M=7, K=10, G=None, frames=6, db=DB_PATH, write=True, workdir=None, variants=None):
+    """Build and time every compile variant (compile_variants) for an N x N
+    image with J channels; returns (and records under the GPU's name) the
+    times and the fastest variant."""
+    import concurrent.futures as cf
+    import tempfile
+    from . import build as B
+    G = 2 * N if G is None else G
+    vs = variants if variants is not None else compile_variants(N, G)
+    work = workdir or tempfile.mkdtemp(prefix="nlinv_sweep_")
+    per = max(1, (os.cpu_count() or 2) // max(1, len(vs)))
+
+    def build_one(v):
+        lib = os.path.join(work, f"lib_{v['name']}.so")
+        B.build(force=True, extra=v["flags"], sizes=[v["grid"]], lib=lib, obj=os.path.join(work, v["name"]),
+                workers=per)
+        return lib
+
+    with cf.ThreadPoolExecutor(max_workers=len(vs)) as ex:
+        libs = list(ex.map(build_one, vs))
+    rows = []
+    for v, lib in zip(vs, libs):
+        ms, err = _time_in_child(lib, N, J, G, M, K, frames)
+        rows.append(dict(name=v["name"], tw=v["grid"][3], eu=v["eu"], pminb=v["pminb"],
+                         ms_per_frame=None if ms is None else round(ms, 4), error=err))
+    ok = [r for r in rows if r["ms_per_frame"] is not None]
+    best = min(ok, key=lambda r: r["ms_per_frame"]) if ok else None
+    rec = dict(pick=best, variants=rows, frames_timed=frames, G=G,
+               when=time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()))
+    if write and db:
+        data = _load(db)
+        data.setdefault(gpu_name(), {})[_key(N, J, M, K) + f"_G{G}_compile"] = rec
+        with open(db, "w") as f:
+            json.dump(data, f, indent=1, sort_keys=True)
+    return rec
+
+
 def main():
     ap = argparse.ArgumentParser(description="time NLINV frames per grid and execution path, keep the fastest")
     ap.add_argument("--N", type=int, required=True)
@@ -152,8 +258,13 @@ def main():
     ap.add_argument("--gamma", type=float, nargs=2, default=(1.0, 2.0))
     ap.add_argument("--frames", type=int, default=6)
     ap.add_argument("--db", default=DB_PATH)
+    ap.add_argument("--compile", action="store_true",
+                    help="sweep the compile-time knobs of the G = 2N grid instead of grids and paths")
     a = ap.parse_args()
-    rec = tune(a.N, a.J, a.M, a.K, tuple(a.gamma), a.db, frames=a.frames)
+    if a.compile:
+        rec = compile_sweep(a.N, a.J, a.M, a.K, frames=a.frames, db=a.db)
+    else:
+        rec = tune(a.N, a.J, a.M, a.K, tuple(a.gamma), a.db, frames=a.frames)
     print(json.dumps(rec))
 
 

@@ -75,6 +75,38 @@ def test_batch_mixes_grid_sizes_and_channel_counts():
         assert rel(to_np(d["x_out"]), ref.flat()) <= TOL
 
 
+def test_batch_graph_replays_new_inputs_frame_counts_and_alpha0():
+    """The per-phase batch runs from CUDA graphs captured once per frame count
+    (and again after nlinv_set_alpha0) that read the frames' pointers from a
+    device table: replays with other inputs and outputs, another frame count
+    and a changed alpha_0 all match the oracle."""
+    from paper_1701_08361_gb300 import nlinv as L
+    N, J, M, K = 32, 3, 3, 6
+    g = O.Geometry(N=N, J=J)
+    frames = cart_frames(N, J, 7, seed=300)
+    P = frames[0][1]
+    plan = make_plan(N, J, psf=P, max_batch=3, newton_steps=M, cg_iters=K)   # default: CUDA graph
+    assert L.nlinv_plan_path(plan)[0] == 4
+
+    def run(idx, alpha0):
+        prm = O.Params(newton_steps=M, cg_iters=K, alpha0=alpha0)
+        descs = []
+        for f in idx:
+            xo = torch.empty(plan.nx, dtype=torch.complex64, device="cuda")
+            descs.append(dict(plan=plan, Y=to_dev(frames[f][0]), turn=0, x_prev=None, x_out=xo))
+        L.nlinv_batch(descs)
+        assert L.nlinv_sync(plan) == 0
+        for f, d in zip(idx, descs):
+            ref = O.nlinv_frame(frames[f][0], P, O.XVec.initial(g), O.XVec.initial(g), g, prm)
+            assert rel(to_np(d["x_out"]), ref.flat()) <= TOL, (idx, f, alpha0)
+
+    run([0, 1, 2], 1.0)      # captures the 3-frame sequence
+    run([3, 4, 5], 1.0)      # replays it on other buffers
+    run([6, 0], 1.0)         # a second graph (2 frames)
+    L.nlinv_set_alpha0(plan, 0.5)
+    run([1, 2, 3], 0.5)      # recaptured with the new alpha_n
+
+
 # radial stream of the schedule tests: 8 frames N=128, 4 coils, 13 spokes,
 # 5 turns; frames 0..2 in order, then 3 in flight (Eq. (10) with o = 3).  At
 # N=64 the same trajectory sits on the FP32 floor of the 1e-3 bar (FP32
