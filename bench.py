@@ -54,7 +54,8 @@ def source_hash() -> str:
 
 
 def profiled_traffic(kernel):
-    """DRAM read + write bytes per launch of `kernel` from the record of the
+    """DRAM read + write bytes per launch of `kernel` (for "frame_phases":
+    per frame, the sum over the frame's phase kernels) from the record of the
     last ncu capture (profiles/traffic.json: kernel, source hash, bytes), or
     None when there is none or the kernel sources changed since it was taken."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
@@ -318,7 +319,8 @@ def run_ours(args):
         "latency_ms": {"p50": round(statistics.median(lat), 4), "min": round(lat[0], 4)},
         "roofline": {"bound": "alu", "achieved": round(achieved, 3),
                      "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
-                     "frac": round(achieved / fp32_peak, 4), "traffic": profiled_traffic(["", "", "k_frame", "k_frame_cl", ""][path]),
+                     "frac": round(achieved / fp32_peak, 4), "traffic": profiled_traffic({1: "frame_phases", 2: "k_frame", 3: "k_frame_cl",
+                                                                  4: "frame_phases"}[path]),
                      "kernel": kernel_name,
                      "peak_source": "FP32: %d SMs x 128 lanes x 2 flop x sm_max_mhz (%s)" % (sm_count(), pk_src)},
         "hbm": {"achieved_gbs": round(hbm, 1), "peak_gbs": pk["hbm_gbs"],
@@ -391,7 +393,7 @@ def unfused_own_kernels(Yall, Ps, args):
     M, C = CFG["M"], CFG["CG"]
     return {"value": round(nf / (ms / 1e3), 2), "unit": "frames/s", "frames": nf,
             "kind": "own kernels, one launch per fused phase (exec_mode 1), one frame at a time",
-            "launches_per_frame": 1 + M * (5 + 5 * C) + 2 + 1}
+            "launches_per_frame": 2 + M * (5 + 4 * C + (1 if C > 0 else 0)) + 2 + 1}
 
 
 # ------------------------------------------- batched uneven frames (C3)
