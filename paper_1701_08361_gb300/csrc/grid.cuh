@@ -160,17 +160,21 @@ __global__ void __launch_bounds__(K::BS, NLINV_PMINB) kf_row_b(Ctx C0, PhaseBatc
 
 // COL_RHS: column pass of the residual against the frame's data;
 // COL_TOEP: the PSF column pass of a CG iteration (both with the frame's PSF)
-template <class K>
-__global__ void __launch_bounds__(K::BS, NLINV_PMINB) kf_col_c(Ctx C0, PhaseBatch B, int mode, int k) {
+// (one kernel per mode, so each compiles for its own operands: the CG's PSF
+// pass needs 233 registers at one CTA per SM, none spilled at 128; with
+// K::OMINB two CTAs per SM where they fit, as for the row pass back)
+template <class K, int MODE>
+__global__ void __launch_bounds__(K::BS, MODE == COL_TOEP ? K::OMINB : NLINV_PMINB) kf_col_c(Ctx C0, PhaseBatch B,
+                                                                                        int k) {
   int f;
   const Ctx C = frame_entry(C0, B, f);
   extern __shared__ float2 sm[];
   const FrameIO& io = B.io[f];
-  phase_col_c<K>(C, sm, mode, io.P, mode == COL_RHS ? io.Y : nullptr, nullptr, C.v, k);
+  phase_col_c<K>(C, sm, MODE, io.P, MODE == COL_RHS ? io.Y : nullptr, nullptr, C.v, k);
 }
 
 template <class K>
-__global__ void __launch_bounds__(K::BS, NLINV_PMINB) kf_row_d(Ctx C0, PhaseBatch B) {
+__global__ void __launch_bounds__(K::BS, K::OMINB) kf_row_d(Ctx C0, PhaseBatch B) {
   int f;
   const Ctx C = frame_entry(C0, B, f);
   extern __shared__ float2 sm[];
@@ -504,8 +508,24 @@ int read_stages(unsigned long long* ns, unsigned long long* cnt) {
 #endif
 
 
+// Dynamic shared memory for the two-CTA phase kernels (kf_col_c of the CG,
+// kf_row_d) in a one-frame launch: more than half of an SM's, so that one CTA
+// sits on each SM.  A lone frame's 152 CTAs, launched early behind their
+// predecessor, otherwise pair up on the SMs that free first (measured 2.97
+// against 2.76 ms per frame); frames of a batch keep two per SM (C3 396 ->
+// 432 frames/s).
+constexpr int kOneCtaSmem = 116 * 1024;
+template <class K>
+constexpr int one_cta_smem() {
+  return K::OMINB == 2 ? (K::SMEM > kOneCtaSmem ? K::SMEM : kOneCtaSmem) : K::SMEM;
+}
+
 template <class K>
 int set_smem_attrs() {
+  if (one_cta_smem<K>() > 48 * 1024) {
+    CK(cudaFuncSetAttribute(kf_col_c<K, COL_TOEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, one_cta_smem<K>()));
+    CK(cudaFuncSetAttribute(kf_row_d<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, one_cta_smem<K>()));
+  }
   if (K::SMEM > 48 * 1024) {
     CK(cudaFuncSetAttribute(k_coil_y<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(k_row_b<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
@@ -515,8 +535,7 @@ int set_smem_attrs() {
     CK(cudaFuncSetAttribute(k_col_e<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(kf_coil_y<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(kf_row_b<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
-    CK(cudaFuncSetAttribute(kf_col_c<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
-    CK(cudaFuncSetAttribute(kf_row_d<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
+    CK(cudaFuncSetAttribute(kf_col_c<K, COL_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(kf_col_e<K, E_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(kf_col_e<K, E_CGR>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(kf_row_cgr<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
@@ -702,10 +721,11 @@ struct Ops {
     // one-phase launches: the co-resident CTAs of the phase kernels, but no
     // more than the largest phase has items (+ the elementwise share)
     int occ = 1 << 20;
-    const void* kf[] = {(const void*)kf_coil_y<K>,        (const void*)kf_row_b<K>,
-                        (const void*)kf_col_c<K>,         (const void*)kf_row_d<K>,
-                        (const void*)kf_col_e<K, E_RHS>,  (const void*)kf_col_e<K, E_CGR>,
-                        (const void*)kf_row_cgr<K>,       (const void*)kf_cgr_final<K>};
+    const void* kf[] = {(const void*)kf_coil_y<K>,          (const void*)kf_row_b<K>,
+                        (const void*)kf_col_c<K, COL_TOEP>, (const void*)kf_col_c<K, COL_RHS>,
+                        (const void*)kf_row_d<K>,           (const void*)kf_col_e<K, E_RHS>,
+                        (const void*)kf_col_e<K, E_CGR>,    (const void*)kf_row_cgr<K>,
+                        (const void*)kf_cgr_final<K>};
     for (const void* fn : kf) {
       int o = 0;
       CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, K::BS, K::SMEM));
@@ -807,19 +827,20 @@ struct Ops {
     const PhaseBatch Be{pl->fstride, plan_grid((int)((C.nx + 255) / 256), 1), pl->io_dev};
     const int gp = nf * B.nbf, ge = nf * Be.nbf;
     const size_t sm = (size_t)K::SMEM;
+    const size_t sm2 = nf == 1 ? (size_t)one_cta_smem<K>() : sm;   // kf_col_c (CG), kf_row_d
     RC(L.go(&kf_init, ge, 256, 0, "kf_init", C, Be, damping));
     for (int n = 0; n < M; ++n) {
       const float al = alpha[n];
       RC(L.go(&kf_coil_y<K>, gp, K::BS, sm, "kf_coil_y", C, B));
       RC(L.go(&kf_row_b<K>, gp, K::BS, sm, "kf_row_b", C, B, (int)ROW_COIL));
-      RC(L.go(&kf_col_c<K>, gp, K::BS, sm, "kf_col_c", C, B, (int)COL_RHS, 0));
-      RC(L.go(&kf_row_d<K>, gp, K::BS, sm, "kf_row_d", C, B));
+      RC(L.go(&kf_col_c<K, COL_RHS>, gp, K::BS, sm, "kf_col_c", C, B, 0));
+      RC(L.go(&kf_row_d<K>, gp, K::BS, sm2, "kf_row_d", C, B));
       RC(L.go(&kf_col_e<K, E_RHS>, gp, K::BS, sm, "kf_col_e", C, B, al, 0, n == M - 1 ? 1 : 0, damping));
       // CG with the operator applied to the residual: four phases per iteration
       for (int k = 0; k < Kcg; ++k) {
         RC(L.go(&kf_row_cgr<K>, gp, K::BS, sm, "kf_row_cgr", C, B, k));
-        RC(L.go(&kf_col_c<K>, gp, K::BS, sm, "kf_col_c", C, B, (int)COL_TOEP, k));
-        RC(L.go(&kf_row_d<K>, gp, K::BS, sm, "kf_row_d", C, B));
+        RC(L.go(&kf_col_c<K, COL_TOEP>, gp, K::BS, sm2, "kf_col_c", C, B, k));
+        RC(L.go(&kf_row_d<K>, gp, K::BS, sm2, "kf_row_d", C, B));
         RC(L.go(&kf_col_e<K, E_CGR>, gp, K::BS, sm, "kf_col_e", C, B, al, k, 0, damping));
       }
       if (Kcg > 0) RC(L.go(&kf_cgr_final<K>, gp, K::BS, sm, "kf_cgr_final", C, B, Kcg));
