@@ -67,12 +67,15 @@ __global__ void __launch_bounds__(K::BS, K::OMINB) k_row_deapod(Ctx C0, const fl
   phase_row_deapod<K>(C, sm, dap, scale, v);
 }
 
-template <class K>
-__global__ void __launch_bounds__(K::BS, K::OMINB) k_col_c(Ctx C0, int mode, const float* P, const float2* Yin,
-                                                 float2* zout, float2* vio, int k) {
+// the operator column passes, one kernel per mode (each compiles for its own
+// operands: at two CTAs per SM the register cap otherwise spills the modes
+// that need fewer)
+template <class K, int MODE>
+__global__ void __launch_bounds__(K::BS, K::OMINB) k_col_c(Ctx C0, const float* P, const float2* Yin,
+                                                           float2* zout, float2* vio, int k) {
   const Ctx C = phase_entry(C0);
   extern __shared__ float2 sm[];
-  phase_col_c<K>(C, sm, mode, P, Yin, zout, vio, k);
+  phase_col_c<K>(C, sm, MODE, P, Yin, zout, vio, k);
 }
 
 template <class K>
@@ -83,19 +86,14 @@ __global__ void __launch_bounds__(K::BS, K::OMINB) k_row_d(Ctx C0, const float2*
   phase_row_d<K>(C, sm, rho, win, sout, kbout);
 }
 
-template <class K>
-__global__ void __launch_bounds__(K::BS, K::OMINB) k_col_e(Ctx C0, int mode, float alpha, int k, const float2* kbin,
-                                                 const float2* sin, const float2* p_old, float2* p_new,
-                                                 float2* out, float2* hout, int slot) {
+template <class K, int MODE>
+__global__ void __launch_bounds__(K::BS, K::OMINB) k_col_e(Ctx C0, float alpha, int k, const float2* kbin,
+                                                           const float2* sin, const float2* p_old, float2* p_new,
+                                                           float2* out, float2* hout, int slot) {
   const Ctx C = phase_entry(C0);
   extern __shared__ float2 sm[];
   __shared__ float2 sred[32];
-  switch (mode) {
-    case E_CG: phase_col_e<K, E_CG>(C, sm, sred, alpha, k, kbin, sin, p_old, p_new, out, hout, slot); break;
-    case E_RHS: phase_col_e<K, E_RHS>(C, sm, sred, alpha, k, kbin, sin, p_old, p_new, out, hout, slot); break;
-    case E_DFH: phase_col_e<K, E_DFH>(C, sm, sred, alpha, k, kbin, sin, p_old, p_new, out, hout, slot); break;
-    default: phase_col_e<K, E_NORMAL>(C, sm, sred, alpha, k, kbin, sin, p_old, p_new, out, hout, slot);
-  }
+  phase_col_e<K, MODE>(C, sm, sred, alpha, k, kbin, sin, p_old, p_new, out, hout, slot);
 }
 
 // ------------------------------------------ frame-indexed phase kernels
@@ -530,9 +528,12 @@ int set_smem_attrs() {
     CK(cudaFuncSetAttribute(k_coil_y<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(k_row_b<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(k_row_deapod<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
-    CK(cudaFuncSetAttribute(k_col_c<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
+    CK(cudaFuncSetAttribute(k_col_c<K, COL_TOEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
+    CK(cudaFuncSetAttribute(k_col_c<K, COL_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
+    CK(cudaFuncSetAttribute(k_col_c<K, COL_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(k_row_d<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
-    CK(cudaFuncSetAttribute(k_col_e<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
+    CK(cudaFuncSetAttribute(k_col_e<K, E_DFH>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
+    CK(cudaFuncSetAttribute(k_col_e<K, E_NORMAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(kf_coil_y<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(kf_row_b<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(kf_col_c<K, COL_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
@@ -650,7 +651,13 @@ struct Launch {
   int col_c(int mode, const float* P, const float2* Yin, float2* zout, float2* vio, int k = 0) const {
     const Ctx& C = pl->C;
     const int g = plan_grid(C.J * ((C.G + K::TW - 1) / K::TW), 1);
-    return go(&k_col_c<K>, pick(g), K::BS, (size_t)K::SMEM, "k_col_c", C, mode, P, Yin, zout, vio, k);
+    const size_t sm = (size_t)K::SMEM;
+    switch (mode) {
+      case COL_TOEP: return go(&k_col_c<K, COL_TOEP>, pick(g), K::BS, sm, "k_col_c", C, P, Yin, zout, vio, k);
+      case COL_FWD: return go(&k_col_c<K, COL_FWD>, pick(g), K::BS, sm, "k_col_c", C, P, Yin, zout, vio, k);
+      case COL_INV: return go(&k_col_c<K, COL_INV>, pick(g), K::BS, sm, "k_col_c", C, P, Yin, zout, vio, k);
+      default: return NLINV_EINVAL;
+    }
   }
   int row_d(const float2* rho, const float2* win, float2* sout, float2* kbout) const {
     const Ctx& C = pl->C;
@@ -662,7 +669,16 @@ struct Launch {
     const Ctx& C = pl->C;
     const int items = C.J * ((C.Gc + K::TW - 1) / K::TW);
     const int g = plan_grid(items, (C.N * C.N + K::BS - 1) / K::BS);
-    return go(&k_col_e<K>, pick(g), K::BS, (size_t)K::SMEM, "k_col_e", C, mode, alpha, k, kbin, sin, p_old, p_new, out, hout, slot);
+    const size_t sm = (size_t)K::SMEM;
+    switch (mode) {
+      case E_DFH:
+        return go(&k_col_e<K, E_DFH>, pick(g), K::BS, sm, "k_col_e", C, alpha, k, kbin, sin, p_old, p_new, out, hout,
+                  slot);
+      case E_NORMAL:
+        return go(&k_col_e<K, E_NORMAL>, pick(g), K::BS, sm, "k_col_e", C, alpha, k, kbin, sin, p_old, p_new, out,
+                  hout, slot);
+      default: return NLINV_EINVAL;
+    }
   }
   // coil maps c_j = W^-1 c^_j of x^ into the plan's c buffer
   int coils(const float2* xhat) const {
