@@ -182,8 +182,8 @@ __global__ void __launch_bounds__(K::BS, K::OMINB) kf_row_d(Ctx C0, PhaseBatch B
 // E_RHS: the Newton right-hand side r_0 (the last step regularised towards
 // damping * x_last when `last` and the frame has one) and H r_0;
 // E_CGR: w_k = A r_k, the partials of Re<r_k, w_k> and |r_k|^2, and H w_k
-template <class K, int MODE>
-__global__ void __launch_bounds__(K::BS, NLINV_PMINB) kf_col_e(Ctx C0, PhaseBatch B, float alpha, int k,
+template <class K, int MODE, int MB = NLINV_PMINB>
+__global__ void __launch_bounds__(K::BS, MB) kf_col_e(Ctx C0, PhaseBatch B, float alpha, int k,
                                                                int last, float damping) {
   int f;
   const Ctx C = frame_entry(C0, B, f);
@@ -199,8 +199,8 @@ __global__ void __launch_bounds__(K::BS, NLINV_PMINB) kf_col_e(Ctx C0, PhaseBatc
 }
 
 // the row pass of r_k, with step k-1's update (phases_cgr.cuh)
-template <class K>
-__global__ void __launch_bounds__(K::BS, NLINV_PMINB) kf_row_cgr(Ctx C0, PhaseBatch B, int k) {
+template <class K, int MB = NLINV_PMINB>
+__global__ void __launch_bounds__(K::BS, MB) kf_row_cgr(Ctx C0, PhaseBatch B, int k) {
   int f;
   const Ctx C = frame_entry(C0, B, f);
   extern __shared__ float2 sm[];
@@ -540,6 +540,8 @@ int set_smem_attrs() {
     CK(cudaFuncSetAttribute(kf_col_e<K, E_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(kf_col_e<K, E_CGR>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(kf_row_cgr<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
+    CK(cudaFuncSetAttribute(kf_col_e<K, E_CGR, K::OMINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
+    CK(cudaFuncSetAttribute(kf_row_cgr<K, K::OMINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(kf_cgr_final<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(k_frame<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(k_batch<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
@@ -854,10 +856,16 @@ struct Ops {
       RC(L.go(&kf_col_e<K, E_RHS>, gp, K::BS, sm, "kf_col_e", C, B, al, 0, n == M - 1 ? 1 : 0, damping));
       // CG with the operator applied to the residual: four phases per iteration
       for (int k = 0; k < Kcg; ++k) {
-        RC(L.go(&kf_row_cgr<K>, gp, K::BS, sm, "kf_row_cgr", C, B, k));
+        if (nf > 1)
+          RC(L.go(&kf_row_cgr<K, K::OMINB>, gp, K::BS, sm, "kf_row_cgr", C, B, k));
+        else
+          RC(L.go(&kf_row_cgr<K>, gp, K::BS, sm, "kf_row_cgr", C, B, k));
         RC(L.go(&kf_col_c<K, COL_TOEP>, gp, K::BS, sm2, "kf_col_c", C, B, k));
         RC(L.go(&kf_row_d<K>, gp, K::BS, sm2, "kf_row_d", C, B));
-        RC(L.go(&kf_col_e<K, E_CGR>, gp, K::BS, sm, "kf_col_e", C, B, al, k, 0, damping));
+        if (nf > 1)
+          RC(L.go(&kf_col_e<K, E_CGR, K::OMINB>, gp, K::BS, sm, "kf_col_e", C, B, al, k, 0, damping));
+        else
+          RC(L.go(&kf_col_e<K, E_CGR>, gp, K::BS, sm, "kf_col_e", C, B, al, k, 0, damping));
       }
       if (Kcg > 0) RC(L.go(&kf_cgr_final<K>, gp, K::BS, sm, "kf_cgr_final", C, B, Kcg));
     }
