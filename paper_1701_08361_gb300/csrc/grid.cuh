@@ -135,8 +135,8 @@ __global__ void kf_init(Ctx C0, PhaseBatch B, float damping) {
 }
 
 // the coil part of x^_n through W^-1 along y
-template <class K>
-__global__ void __launch_bounds__(K::BS, NLINV_PMINB) kf_coil_y(Ctx C0, PhaseBatch B) {
+template <class K, int MB = NLINV_PMINB>
+__global__ void __launch_bounds__(K::BS, MB) kf_coil_y(Ctx C0, PhaseBatch B) {
   int f;
   const Ctx C = frame_entry(C0, B, f);
   extern __shared__ float2 sm[];
@@ -145,8 +145,8 @@ __global__ void __launch_bounds__(K::BS, NLINV_PMINB) kf_coil_y(Ctx C0, PhaseBat
 
 // ROW_COIL: coil maps and rho c_j rows through the padded row FFT;
 // ROW_COILONLY: the coil maps alone
-template <class K>
-__global__ void __launch_bounds__(K::BS, NLINV_PMINB) kf_row_b(Ctx C0, PhaseBatch B, int mode) {
+template <class K, int MB = NLINV_PMINB>
+__global__ void __launch_bounds__(K::BS, MB) kf_row_b(Ctx C0, PhaseBatch B, int mode) {
   int f;
   const Ctx C = frame_entry(C0, B, f);
   extern __shared__ float2 sm[];
@@ -536,13 +536,15 @@ int set_smem_attrs() {
     CK(cudaFuncSetAttribute(k_col_e<K, E_NORMAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(kf_coil_y<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(kf_row_b<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
+    CK(cudaFuncSetAttribute(kf_coil_y<K, K::OMINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
+    CK(cudaFuncSetAttribute(kf_row_b<K, K::OMINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
+    CK(cudaFuncSetAttribute(kf_cgr_final<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(kf_col_c<K, COL_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(kf_col_e<K, E_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(kf_col_e<K, E_CGR>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(kf_row_cgr<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(kf_col_e<K, E_CGR, K::OMINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(kf_row_cgr<K, K::OMINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
-    CK(cudaFuncSetAttribute(kf_cgr_final<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(k_frame<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
     CK(cudaFuncSetAttribute(k_batch<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM));
   }
@@ -849,8 +851,13 @@ struct Ops {
     RC(L.go(&kf_init, ge, 256, 0, "kf_init", C, Be, damping));
     for (int n = 0; n < M; ++n) {
       const float al = alpha[n];
-      RC(L.go(&kf_coil_y<K>, gp, K::BS, sm, "kf_coil_y", C, B));
-      RC(L.go(&kf_row_b<K>, gp, K::BS, sm, "kf_row_b", C, B, (int)ROW_COIL));
+      if (nf > 1) {
+        RC(L.go(&kf_coil_y<K, K::OMINB>, gp, K::BS, sm, "kf_coil_y", C, B));
+        RC(L.go(&kf_row_b<K, K::OMINB>, gp, K::BS, sm, "kf_row_b", C, B, (int)ROW_COIL));
+      } else {
+        RC(L.go(&kf_coil_y<K>, gp, K::BS, sm, "kf_coil_y", C, B));
+        RC(L.go(&kf_row_b<K>, gp, K::BS, sm, "kf_row_b", C, B, (int)ROW_COIL));
+      }
       RC(L.go(&kf_col_c<K, COL_RHS>, gp, K::BS, sm, "kf_col_c", C, B, 0));
       RC(L.go(&kf_row_d<K>, gp, K::BS, sm2, "kf_row_d", C, B));
       RC(L.go(&kf_col_e<K, E_RHS>, gp, K::BS, sm, "kf_col_e", C, B, al, 0, n == M - 1 ? 1 : 0, damping));
@@ -867,7 +874,7 @@ struct Ops {
         else
           RC(L.go(&kf_col_e<K, E_CGR>, gp, K::BS, sm, "kf_col_e", C, B, al, k, 0, damping));
       }
-      if (Kcg > 0) RC(L.go(&kf_cgr_final<K>, gp, K::BS, sm, "kf_cgr_final", C, B, Kcg));
+      if (Kcg > 0) RC(L.go(&kf_cgr_final<K>, gp, K::BS, 0, "kf_cgr_final", C, B, Kcg));   // no dynamic smem
     }
     RC(L.go(&kf_coil_y<K>, gp, K::BS, sm, "kf_coil_y", C, B));
     RC(L.go(&kf_row_b<K>, gp, K::BS, sm, "kf_row_b", C, B, (int)ROW_COILONLY));
