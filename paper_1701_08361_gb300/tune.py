@@ -146,8 +146,9 @@ def tuned_params(N, J, M=7, K=10, gamma=(1.0, 2.0), db=DB_PATH, measure_if_missi
 # ------------------------------------------------ compile-time knobs
 # Per compiled grid the tile width TW (columns of a column item, rows of a row
 # item), the elements per thread and round of the elementwise parts
-# (NLINV_EU) and the CTAs per SM the frame-indexed phase kernels are compiled
-# for (NLINV_PMINB) are fixed when the library is built.  compile_sweep
+# (NLINV_EU), the CTAs per SM the frame-indexed phase kernels are compiled
+# for (NLINV_PMINB) and the fewest CTAs a phase leaves to its elementwise part
+# (NLINV_ELEM_CTAS) are fixed when the library is built.  compile_sweep
 # builds one library per variant (only this grid's unit, all variants in
 # parallel, each in its own object folder), times each in a child process on
 # the default execution path and records every time and the fastest.
@@ -175,26 +176,34 @@ def built_in_knob(name):
     return int(m.group(1))
 
 
-def compile_variants(N, G=None, tws=(8, 12, 16), eus=(2, 4, 8), pminbs=(1, 2)):
+# the -D knobs the sweep varies (besides the tile width) and their candidates
+KNOBS = {"NLINV_EU": (2, 4, 8), "NLINV_PMINB": (1, 2), "NLINV_ELEM_CTAS": (16, 32, 64)}
+
+
+def compile_variants(N, G=None, tws=(8, 12, 16), knobs=None):
     """Variants of the compiled grid for (G, N) (G = 2N by default): the
-    built-in one, each tile width in `tws`, each EU in `eus` and each PMINB in
-    `pminbs` (one knob changed at a time).  Returns dicts with the grid tuple
-    (G1, G2, N, TW, MINB) and the nvcc -D flags."""
+    built-in one, then one knob changed at a time -- each tile width in `tws`
+    and each candidate of every -D knob in `knobs` (default KNOBS).  Returns
+    dicts with the grid tuple (G1, G2, N, TW, MINB), the knob values and the
+    nvcc -D flags."""
     from . import build as B
     G = 2 * N if G is None else G
+    knobs = KNOBS if knobs is None else knobs
     base = [t for t in B.grid_sizes() if t[0] * t[1] == G and t[2] == N]
     if not base:
         raise ValueError(f"no compiled grid for G={G}, N={N}")
     g1, g2, n, tw0, mb = base[0]
-    eu0, pm0 = built_in_knob("NLINV_EU"), built_in_knob("NLINV_PMINB")
-    out = [dict(grid=(g1, g2, n, tw0, mb), eu=eu0, pminb=pm0)]
-    out += [dict(grid=(g1, g2, n, tw, mb), eu=eu0, pminb=pm0) for tw in tws if tw != tw0]
-    out += [dict(grid=(g1, g2, n, tw0, mb), eu=eu, pminb=pm0) for eu in eus if eu != eu0]
-    out += [dict(grid=(g1, g2, n, tw0, mb), eu=eu0, pminb=pm) for pm in pminbs if pm != pm0]
+    k0 = {k: built_in_knob(k) for k in knobs}
+    out = [dict(grid=(g1, g2, n, tw0, mb), knobs=dict(k0))]
+    out += [dict(grid=(g1, g2, n, tw, mb), knobs=dict(k0)) for tw in tws if tw != tw0]
+    for k, cands in knobs.items():
+        out += [dict(grid=(g1, g2, n, tw0, mb), knobs=dict(k0, **{k: v})) for v in cands if v != k0[k]]
     out = [v for v in out if _fits(*v["grid"])]
+    short = {"NLINV_EU": "eu", "NLINV_PMINB": "pm", "NLINV_ELEM_CTAS": "ec"}
     for v in out:
-        v["flags"] = [f"-DNLINV_EU={v['eu']}", f"-DNLINV_PMINB={v['pminb']}"]
-        v["name"] = "tw{}_eu{}_pm{}".format(v["grid"][3], v["eu"], v["pminb"])
+        v["flags"] = [f"-D{k}={x}" for k, x in sorted(v["knobs"].items())]
+        v["name"] = "tw{}_".format(v["grid"][3]) + "_".join(
+            "{}{}".format(short.get(k, k.lower()), x) for k, x in sorted(v["knobs"].items()))
     return out
 
 
@@ -235,7 +244,7 @@ def compile_sweep(N, J, M=7, K=10, G=None, frames=6, db=DB_PATH, write=True, wor
     rows = []
     for v, lib in zip(vs, libs):
         ms, err = _time_in_child(lib, N, J, G, M, K, frames)
-        rows.append(dict(name=v["name"], tw=v["grid"][3], eu=v["eu"], pminb=v["pminb"],
+        rows.append(dict(name=v["name"], tw=v["grid"][3], knobs=v["knobs"],
                          ms_per_frame=None if ms is None else round(ms, 4), error=err))
     ok = [r for r in rows if r["ms_per_frame"] is not None]
     best = min(ok, key=lambda r: r["ms_per_frame"]) if ok else None

@@ -161,6 +161,26 @@ def test_degenerate_iteration_counts(M, K, mode):
     assert rel(x, ref.flat()) <= TOL
 
 
+@pytest.mark.parametrize("N,J,M,K", [(20, 2, 1, 8), (20, 2, 5, 8), (32, 3, 2, 8)])
+@pytest.mark.parametrize("exec_mode", [0, 1])
+def test_cg_reaching_the_rounding_floor_is_not_a_breakdown(N, J, M, K, exec_mode):
+    """Small Cartesian frames whose CG converges to the FP32 rounding floor
+    within a few iterations: the per-phase path's CG (the operator applied to
+    the residual) stops there instead of reporting a breakdown, and the frame
+    still matches the oracle."""
+    from paper_1701_08361_gb300 import nlinv as L
+    Y, P = S.cartesian_frame(N, J, seed=100, sigma=1e-3, frame=0)[:2]
+    g = O.Geometry(N=N, J=J)
+    plan = make_plan(N, J, psf=P, newton_steps=M, cg_iters=K, exec_mode=exec_mode)
+    x = torch.empty(plan.nx, dtype=torch.complex64, device="cuda")
+    L.nlinv_frame(plan, to_dev(Y), 0, None, x)
+    assert L.nlinv_sync(plan) == 0
+    ref = O.nlinv_frame(Y, P, O.XVec.initial(g), O.XVec.initial(g), g, O.Params(newton_steps=M, cg_iters=K))
+    e = rel(to_np(x), ref.flat())
+    print(f"N={N} J={J} M={M} K={K} mode={exec_mode}: rel L2 vs FP64 {e:.2e}")
+    assert e <= TOL
+
+
 @pytest.mark.parametrize("N,J,Gc,cs", [(160, 10, 0, 0), (64, 4, 0, 0), (20, 3, 0, 0), (32, 4, 16, 0),
                                        (128, 8, 0, 8), (128, 8, 0, 0), (64, 4, 0, 6)])
 def test_cluster_kernel_matches_oracle_and_grid_kernel(N, J, Gc, cs):

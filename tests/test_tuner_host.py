@@ -24,12 +24,12 @@ def test_fit_check_rejects_what_cfg_rejects():
 def test_variants_change_one_knob(N):
     vs = T.compile_variants(N)
     base = vs[0]
-    assert (base["eu"], base["pminb"]) == (T.built_in_knob("NLINV_EU"), T.built_in_knob("NLINV_PMINB"))
+    assert base["knobs"] == {k: T.built_in_knob(k) for k in T.KNOBS}
     assert base["grid"] in B.grid_sizes()
     names = [v["name"] for v in vs]
     assert len(set(names)) == len(names)
     for v in vs[1:]:
-        diff = (v["grid"][3] != base["grid"][3]) + (v["eu"] != base["eu"]) + (v["pminb"] != base["pminb"])
+        diff = (v["grid"][3] != base["grid"][3]) + sum(v["knobs"][k] != base["knobs"][k] for k in T.KNOBS)
         assert diff == 1, v
         assert v["grid"][:3] == base["grid"][:3] and v["grid"][4] == base["grid"][4]
 
