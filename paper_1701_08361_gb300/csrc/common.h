@@ -133,6 +133,7 @@ struct nlinv_plan_s {
   // phase kernels read, and the phase sequences captured into CUDA graphs
   // (one per frame count and alpha_0)
   int phase_grid = 0;
+  int colc_grid = 0;          // CTAs per frame of the CG's PSF column pass (no partial sums)
   nlinv::FrameIO* io_dev = nullptr;
   cudaStream_t gcap = nullptr;
   struct PhaseGraph {

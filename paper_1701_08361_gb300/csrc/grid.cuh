@@ -756,6 +756,17 @@ struct Ops {
     if (pg > most) pg = most;
     if (pg > kMaxPart) pg = kMaxPart;
     pl->phase_grid = pg;
+    // the CG's PSF column pass deposits and reads no partial sums, so it may
+    // run its own CTA count: one CTA per item as far as the co-resident CTAs
+    // allow (at C2, 270 items in one round at two CTAs per SM instead of two
+    // rounds of 152)
+    int oc = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oc, kf_col_c<K, COL_TOEP>, K::BS, K::SMEM));
+    const int citems = pl->J * ((pl->G + K::TW - 1) / K::TW);
+    int cg = oc * pl->nsm;
+    if (cg > citems) cg = citems;
+    if (cg < pg) cg = pg;
+    pl->colc_grid = cg;
     if (pg <= 0) return NLINV_ECUDA;
     if (pl->prm.exec_mode == 3) {
       RC(pick_cluster<K>(pl));
@@ -845,9 +856,11 @@ struct Ops {
     Launch<K> L{pl, st, 0, pdl};
     const PhaseBatch B{pl->fstride, pl->phase_grid, pl->io_dev};
     const PhaseBatch Be{pl->fstride, plan_grid((int)((C.nx + 255) / 256), 1), pl->io_dev};
-    const int gp = nf * B.nbf, ge = nf * Be.nbf;
+    const PhaseBatch Bc{pl->fstride, pl->colc_grid, pl->io_dev};
+    const int gp = nf * B.nbf, ge = nf * Be.nbf, gc = nf * Bc.nbf;
     const size_t sm = (size_t)K::SMEM;
-    const size_t sm2 = nf == 1 ? (size_t)one_cta_smem<K>() : sm;   // kf_col_c (CG), kf_row_d
+    const size_t sm2 = nf == 1 ? (size_t)one_cta_smem<K>() : sm;   // kf_row_d (and kf_col_c at 1 CTA per frame SM)
+    const size_t smc = (nf == 1 && Bc.nbf <= pl->nsm) ? sm2 : sm;
     RC(L.go(&kf_init, ge, 256, 0, "kf_init", C, Be, damping));
     for (int n = 0; n < M; ++n) {
       const float al = alpha[n];
@@ -867,7 +880,7 @@ struct Ops {
           RC(L.go(&kf_row_cgr<K, K::OMINB>, gp, K::BS, sm, "kf_row_cgr", C, B, k));
         else
           RC(L.go(&kf_row_cgr<K>, gp, K::BS, sm, "kf_row_cgr", C, B, k));
-        RC(L.go(&kf_col_c<K, COL_TOEP>, gp, K::BS, sm2, "kf_col_c", C, B, k));
+        RC(L.go(&kf_col_c<K, COL_TOEP>, gc, K::BS, smc, "kf_col_c", C, Bc, k));
         RC(L.go(&kf_row_d<K>, gp, K::BS, sm2, "kf_row_d", C, B));
         if (nf > 1)
           RC(L.go(&kf_col_e<K, E_CGR, K::OMINB>, gp, K::BS, sm, "kf_col_e", C, B, al, k, 0, damping));
