@@ -532,16 +532,17 @@ def high_channel_c4(args):
 
 # ------------------------------------ differentiable unrolled NLINV (C5)
 def differentiable_c5(args):
-    """A batch of 8 frames of the real-time stream's size (N=160 / 320 grid,
-    10 channels, 13 spokes, 7 x 10) through the torch.autograd.Function:
-    forward (nlinv_batch) and the hand-written backward (per frame, per
-    Newton step recomputed from its checkpoint) for L = Re<g, x^_M>, with
-    gradients w.r.t. the gridded data and alpha_0.  Time per training step."""
+    """A batch of 8 frames (--c5-batch) of the real-time stream's size
+    (N=160 / 320 grid, 10 channels, 13 spokes, 7 x 10) through the
+    torch.autograd.Function: forward (nlinv_batch) and the hand-written
+    backward (per frame: one forward sweep recording every Newton step's CG,
+    then the reverse sweep) for L = Re<g, x^_M>, with gradients w.r.t. the
+    gridded data and alpha_0.  Time per training step."""
     import torch
     from paper_1701_08361_gb300 import nlinv as L
     from paper_1701_08361_gb300 import autograd as AG
     dev = torch.device("cuda")
-    N, J, U, B = CFG["N"], CFG["J"], CFG["U"], 8
+    N, J, U, B = CFG["N"], CFG["J"], CFG["U"], args.c5_batch
     G = 2 * N
     p = L.nlinv_default_params(N, J)
     p.n_turns = U
@@ -595,8 +596,8 @@ def differentiable_c5(args):
     return {"value": round(B / (ms / 1e3), 2), "unit": "frames/s (forward + backward)",
             "ms_per_step": round(ms, 3), "wall_ms_per_step": round(wall, 3), "forward_ms": round(fwd, 3),
             "backward_ms": round(ms - fwd, 3), "batch": B, "steps": args.c5_steps,
-            "workload": "8 frames N=160 / 320^2 grid, 10 channels, 13 spokes, 7x10 unrolled; "
-                        "d/dY and d/dalpha_0 of Re<g, x^_M> through torch.autograd"}
+            "workload": "%d frames N=160 / 320^2 grid, 10 channels, 13 spokes, 7x10 unrolled; "
+                        "d/dY and d/dalpha_0 of Re<g, x^_M> through torch.autograd" % B}
 
 
 # --------------------------------------------------- CPU oracle baseline
@@ -781,6 +782,7 @@ def main():
     ap.add_argument("--c3-groups", type=int, default=4)
     ap.add_argument("--c4-frames", type=int, default=3)
     ap.add_argument("--c5-steps", type=int, default=1)
+    ap.add_argument("--c5-batch", type=int, default=8, help="frames per C5 step (8: the configuration)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -327,7 +327,7 @@ int nlinv_set_alpha0(nlinv_plan_t plan, double alpha0);
  * computed, with the data-dependent step lengths).  A forward sweep records
  * every Newton step (checkpoint x^_n, residual, the CG vectors p_k, q_k, r_k)
  * in the workspace and the reverse sweep reads that record: per frame
- * (M + 1 + M (3 K + 1) + 13) n_x + (M + 2) J G^2 complex64 values, ~0.24 GB
+ * (M + 1 + M (3 K + 1) + 13) n_x + (M + 2) J G^2 + J N^2 complex64 values, ~0.24 GB
  * at N = 160, J = 10, G = 320, M = 7, K = 10.  With gbar = dL/dx^_M (device [n_x]; for
  * complex vectors the gradient of a real L is dL/dRe + i dL/dIm):
  *   Ybar_out       device [J][G][G] complex64: dL/dY

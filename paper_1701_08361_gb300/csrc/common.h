@@ -205,10 +205,14 @@ struct GridOps {
 // of view, tile width TW and MINB CTAs per SM (Cfg in phases.cuh); one
 // grid.cu unit each.  G = 2N for the twofold grids; the others are grids
 // G = 2 gamma N of Eq. (8) with gamma > 1 (radix 3, 5 and 7 splits).  A unit
-// left out of a build leaves its grid unsupported (weak reference).
+// left out of a build leaves its grid unsupported (weak reference).  The
+// tile widths are measured picks (tune.py): 12 at 320 and 16 at 512 for one
+// frame at a time, 8 at 384 (192-thread CTAs, two per SM) for frames in
+// flight together (the 384^2 / 16-channel class of the batched workload:
+// 493 -> 522 frames/s over the three classes).
 #define NLINV_GRIDS(X)                                                                               \
   X(4, 4, 8, 16, 2) X(4, 6, 12, 16, 2) X(4, 10, 20, 16, 2) X(8, 8, 32, 16, 2) X(8, 16, 64, 16, 2)   \
-  X(16, 16, 128, 16, 2) X(16, 20, 160, 12, 1) X(16, 24, 192, 16, 1) X(16, 32, 256, 16, 1)          \
+  X(16, 16, 128, 16, 2) X(16, 20, 160, 12, 1) X(16, 24, 192, 8, 1) X(16, 32, 256, 16, 1)          \
   X(4, 14, 20, 16, 2) X(6, 9, 20, 16, 2) X(8, 9, 24, 16, 2) X(16, 28, 160, 16, 1)                  \
   X(16, 30, 160, 16, 1) X(18, 27, 160, 16, 1) X(16, 32, 160, 16, 1) X(20, 28, 160, 16, 1)          \
   X(16, 24, 128, 16, 1)

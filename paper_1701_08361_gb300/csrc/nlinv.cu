@@ -1377,14 +1377,23 @@ struct GradOps {
   // The plan's coil-map buffer holds W^-1 of lin's coil part when
   // coils_at == lin.  lin is the Newton step's checkpoint x^_n, which is not
   // written while it is the linearisation point; maps of any other point
-  // (a buffer that may change between calls) are never reused.
+  // (a buffer that may change between calls) are never reused.  With `alt`
+  // (a view whose coil-map buffer is a scratch array) the maps of other
+  // points go there, so lin's maps survive them.
+  const nlinv_plan_s* alt = nullptr;
   const float2* lin = nullptr;
   mutable const float2* coils_at = nullptr;
-  // whether the coil buffer already holds the maps of w; updates the record
+  // the view whose coil buffer serves point w
+  const nlinv_plan_s* at(const float2* w) const { return (w != nullptr && w == lin) || !alt ? pl : alt; }
+  // whether that coil buffer already holds the maps of w; updates the record
   bool coils_ready(const float2* w) const {
-    const bool ready = w != nullptr && w == lin && coils_at == lin;
-    coils_at = (w == lin) ? lin : nullptr;
-    return ready;
+    if (w != nullptr && w == lin) {
+      const bool ready = coils_at == lin;
+      coils_at = lin;
+      return ready;
+    }
+    if (!alt) coils_at = nullptr;   // the plan's buffer is about to hold another point's maps
+    return false;
   }
 
   int grid(long long n) const {
@@ -1428,14 +1437,19 @@ struct GradOps {
     return NLINV_OK;
   }
   // z = DF(x)[d]
-  int DF(const float2* x, const float2* d, float2* z) const { return ops->DF(pl, st, x, d, z, coils_ready(x)); }
+  int DF(const float2* x, const float2* d, float2* z) const {
+    const bool r = coils_ready(x);
+    return ops->DF(at(x), st, x, d, z, r);
+  }
   // out = DF(w)^H z
   int DFH(const float2* w, const float2* z, float2* out) const {
-    return ops->DFH(pl, st, w, z, out, coils_ready(w));
+    const bool r = coils_ready(w);
+    return ops->DFH(at(w), st, w, z, out, r);
   }
   // out = (DF(x)^H P DF(x) + alpha) d
   int normal(const float2* x, const float2* d, double alpha, float2* out) const {
-    return ops->normal(pl, st, x, d, P, alpha, out, coils_ready(x));
+    const bool r = coils_ready(x);
+    return ops->normal(at(x), st, x, d, P, alpha, out, r);
   }
   int psf(float2* z, float s) const {
     k_psf_scale<<<grid(nk), 256, 0, st>>>(pl->J, pl->G, z, P, s);
@@ -1456,6 +1470,7 @@ struct GradOps {
 struct GradWS {
   float2 *ck, *b, *z, *zt, *zt2, *tp, *tq, *tr, *xb, *xbn, *pbar, *rbar, *qbar, *pb, *t0, *t1, *t2, *xref,
       *xrefbar, *xcg;
+  float2* cscr;   // coil maps [J][N][N] of points other than the linearisation point
   double *part, *sc;
   size_t vn = 0;                             // elements of one vector slot (256-byte aligned)
   size_t spq = 0, sr = 0, sz = 0, ssc = 0;   // elements between two Newton steps' tapes / z / scalars
@@ -1479,6 +1494,7 @@ size_t grad_ws_bytes(const nlinv_plan_s* pl) {
   const size_t vb = align_up(nx * sizeof(float2)), kb = align_up(nk * sizeof(float2));
   const size_t kt = Kc > 0 ? Kc : 1;   // p_k and q_k tapes (one vector even without CG)
   return vb * ((M + 1) + (size_t)M * (2 * kt + Kc + 1) + 13) + (M + 2) * kb +
+         align_up((size_t)pl->J * pl->N * pl->N * sizeof(float2)) +
          align_up((size_t)kMaxDots * kDotBlocks * sizeof(double)) +
          align_up((size_t)M * VjpSlots(Kc).total * sizeof(double));
 }
@@ -1516,6 +1532,8 @@ void grad_ws_carve(const nlinv_plan_s* pl, char* p, GradWS& w) {
   p += kb;
   w.zt2 = (float2*)p;
   p += kb;
+  w.cscr = (float2*)p;
+  p += align_up((size_t)pl->J * pl->N * pl->N * sizeof(float2));
   w.part = (double*)p;
   p += align_up((size_t)kMaxDots * kDotBlocks * sizeof(double));
   w.sc = (double*)p;
@@ -1579,6 +1597,12 @@ int vjp_issue(const nlinv_plan_s* view, cudaStream_t st, const GradWS& w, const 
   const int M = prm.newton_steps, Kc = prm.cg_iters;
   const VjpSlots S(Kc);
   GradOps O{view, st, P, view->nx, (long long)view->J * view->G * view->G, w.part, grid_ops(view->G, view->N)};
+  // coil maps of points other than x^_n (the reverse steps' DF^H at q-bar,
+  // p and b-bar) go to a scratch array, so x^_n's maps are built once per
+  // Newton step
+  nlinv_plan_s alt(*view);
+  alt.C.c = w.cscr;
+  O.alt = &alt;
   const long long nx = O.nx, nk = O.nk;
   const int nfill = M * S.total;
   k_fill<<<(nfill + 255) / 256, 256, 0, st>>>(w.sc, nfill, 0.0);
