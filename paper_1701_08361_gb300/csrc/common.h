@@ -134,6 +134,7 @@ struct nlinv_plan_s {
   // (one per frame count and alpha_0)
   int phase_grid = 0;
   int colc_grid = 0;          // CTAs per frame of the CG's PSF column pass (no partial sums)
+  bool dense = false;         // a lone frame has work for two CTAs per SM (runs like a batch)
   nlinv::FrameIO* io_dev = nullptr;
   cudaStream_t gcap = nullptr;
   struct PhaseGraph {
@@ -206,13 +207,15 @@ struct GridOps {
 // grid.cu unit each.  G = 2N for the twofold grids; the others are grids
 // G = 2 gamma N of Eq. (8) with gamma > 1 (radix 3, 5 and 7 splits).  A unit
 // left out of a build leaves its grid unsupported (weak reference).  The
-// tile widths are measured picks (tune.py): 12 at 320 and 16 at 512 for one
-// frame at a time, 8 at 384 (192-thread CTAs, two per SM) for frames in
+// tile widths are measured picks (tune.py and the bench): 12 at 320 for one
+// frame at a time; 8 at 384 (192-thread CTAs, two per SM) for frames in
 // flight together (the 384^2 / 16-channel class of the batched workload:
-// 493 -> 522 frames/s over the three classes).
+// 493 -> 522 frames/s over the three classes); 8 at 512, where a 64-channel
+// frame is dense enough to run like a batch (26.0 against 27.2 ms per frame
+// with 16-wide tiles at one CTA per SM).
 #define NLINV_GRIDS(X)                                                                               \
   X(4, 4, 8, 16, 2) X(4, 6, 12, 16, 2) X(4, 10, 20, 16, 2) X(8, 8, 32, 16, 2) X(8, 16, 64, 16, 2)   \
-  X(16, 16, 128, 16, 2) X(16, 20, 160, 12, 1) X(16, 24, 192, 8, 1) X(16, 32, 256, 16, 1)          \
+  X(16, 16, 128, 16, 2) X(16, 20, 160, 12, 1) X(16, 24, 192, 8, 1) X(16, 32, 256, 8, 1)           \
   X(4, 14, 20, 16, 2) X(6, 9, 20, 16, 2) X(8, 9, 24, 16, 2) X(16, 28, 160, 16, 1)                  \
   X(16, 30, 160, 16, 1) X(18, 27, 160, 16, 1) X(16, 32, 160, 16, 1) X(20, 28, 160, 16, 1)          \
   X(16, 24, 128, 16, 1)

@@ -752,6 +752,12 @@ struct Ops {
       occ = o < occ ? o : occ;
     }
     const int most = pl->J * ((pl->G + K::TW - 1) / K::TW) + kElemCTAs;
+    // a frame whose row passes alone have items for two rounds of two CTAs
+    // per SM runs its phases like a batch: the two-CTA variants and twice
+    // the CTAs per frame
+    const int ritems = pl->J * ((pl->N + K::TW - 1) / K::TW);
+    pl->dense = K::OMINB == 2 && ritems >= 4 * K::OMINB * pl->nsm;
+    if (pl->dense) occ = K::OMINB;
     int pg = occ * pl->nsm;
     if (pg > most) pg = most;
     if (pg > kMaxPart) pg = kMaxPart;
@@ -859,12 +865,13 @@ struct Ops {
     const PhaseBatch Bc{pl->fstride, pl->colc_grid, pl->io_dev};
     const int gp = nf * B.nbf, ge = nf * Be.nbf, gc = nf * Bc.nbf;
     const size_t sm = (size_t)K::SMEM;
-    const size_t sm2 = nf == 1 ? (size_t)one_cta_smem<K>() : sm;   // kf_row_d (and kf_col_c at 1 CTA per frame SM)
-    const size_t smc = (nf == 1 && Bc.nbf <= pl->nsm) ? sm2 : sm;
+    const bool two = nf > 1 || pl->dense;   // the two-CTA variants
+    const size_t sm2 = two ? sm : (size_t)one_cta_smem<K>();   // kf_row_d (and kf_col_c at 1 CTA per SM)
+    const size_t smc = (!two && Bc.nbf <= pl->nsm) ? sm2 : sm;
     RC(L.go(&kf_init, ge, 256, 0, "kf_init", C, Be, damping));
     for (int n = 0; n < M; ++n) {
       const float al = alpha[n];
-      if (nf > 1) {
+      if (two) {
         RC(L.go(&kf_coil_y<K, K::OMINB>, gp, K::BS, sm, "kf_coil_y", C, B));
         RC(L.go(&kf_row_b<K, K::OMINB>, gp, K::BS, sm, "kf_row_b", C, B, (int)ROW_COIL));
       } else {
@@ -876,13 +883,13 @@ struct Ops {
       RC(L.go(&kf_col_e<K, E_RHS>, gp, K::BS, sm, "kf_col_e", C, B, al, 0, n == M - 1 ? 1 : 0, damping));
       // CG with the operator applied to the residual: four phases per iteration
       for (int k = 0; k < Kcg; ++k) {
-        if (nf > 1)
+        if (two)
           RC(L.go(&kf_row_cgr<K, K::OMINB>, gp, K::BS, sm, "kf_row_cgr", C, B, k));
         else
           RC(L.go(&kf_row_cgr<K>, gp, K::BS, sm, "kf_row_cgr", C, B, k));
         RC(L.go(&kf_col_c<K, COL_TOEP>, gc, K::BS, smc, "kf_col_c", C, Bc, k));
         RC(L.go(&kf_row_d<K>, gp, K::BS, sm2, "kf_row_d", C, B));
-        if (nf > 1)
+        if (two)
           RC(L.go(&kf_col_e<K, E_CGR, K::OMINB>, gp, K::BS, sm, "kf_col_e", C, B, al, k, 0, damping));
         else
           RC(L.go(&kf_col_e<K, E_CGR>, gp, K::BS, sm, "kf_col_e", C, B, al, k, 0, damping));
