@@ -225,7 +225,14 @@ int nlinv_apply_normal_static(int N, int J, int Gc, double w_a, double w_l,
 /* One NLINV frame (Eqs. 2-3): M Newton steps from x^_0 = x_prev, each
  *   (DF^H P DF + alpha_n I) delta = DF^H (Y - P F^(x^_n)) - alpha_n (x^_n - x_ref)
  * solved by cg_iters CG iterations from zero, x^_{n+1} = x^_n + delta,
- * alpha_n = alpha0 q^n, x_ref = damping * x_prev.
+ * alpha_n = alpha0 q^n, x_ref = damping * x_prev.  The per-phase paths
+ * (exec_mode 0, 1, 4) run the CG with the operator applied to the residual
+ * (one reduction point per iteration; the same iterates as the textbook CG
+ * in exact arithmetic) and stop a Newton step's CG once |r_k|^2 falls to
+ * 1e-8 |r_0|^2 and its step length is no longer positive (rounding floor);
+ * the persistent kernels (exec_mode 2, 3) run the textbook CG.  A step
+ * length that is not positive above that floor is a breakdown:
+ * NLINV_ENUMERIC from nlinv_sync.
  * Y: device complex64 [J][G][G]; turn selects the PSF; x_prev: device [n_x]
  * or NULL (rho = 1, c^ = 0: the first frame of Sec. 3.3); x_out: device
  * [n_x] (may alias x_prev); rho_out: device [N][N] or NULL; img_out: device
