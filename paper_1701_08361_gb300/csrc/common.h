@@ -135,6 +135,8 @@ struct nlinv_plan_s {
   int phase_grid = 0;
   int colc_grid = 0;          // CTAs per frame of the CG's PSF column pass (no partial sums)
   bool dense = false;         // a lone frame has work for two CTAs per SM (runs like a batch)
+  int op_minb = 1;            // CTAs per SM of the operator kernels (Cfg::OMINB)
+  int op_grid = 0;            // cap on the CTAs of an operator launch (0: one per item)
   nlinv::FrameIO* io_dev = nullptr;
   cudaStream_t gcap = nullptr;
   struct PhaseGraph {

@@ -614,7 +614,7 @@ struct Launch {
   cudaStream_t st;
   int fixed = 0;   // if > 0: every launch uses this many CTAs (CG reductions need equal counts)
   bool pdl = false;   // launch with programmatic dependent launch (see phase_entry)
-  int pick(int g) const { return fixed > 0 ? fixed : g; }
+  int pick(int g) const { return fixed > 0 ? fixed : (pl->op_grid > 0 && g > pl->op_grid ? pl->op_grid : g); }
   template <class... KArgs, class... Args>
   int go(void (*kern)(KArgs...), int grid, int block, size_t smem, const char* what, Args... args) const {
     if (!pdl) {
@@ -762,6 +762,7 @@ struct Ops {
     if (pg > most) pg = most;
     if (pg > kMaxPart) pg = kMaxPart;
     pl->phase_grid = pg;
+    pl->op_minb = K::OMINB;
     // the CG's PSF column pass deposits and reads no partial sums, so it may
     // run its own CTA count: one CTA per item as far as the co-resident CTAs
     // allow (at C2, 270 items in one round at two CTAs per SM instead of two

@@ -1786,6 +1786,10 @@ extern "C" int nlinv_batch_vjp(nlinv_plan_t pl, int nframes, const void* const* 
       }
       nlinv_plan_s view(*pl);
       view.C = frame_ctx(pl->C, (size_t)f * pl->fstride);
+      // frames' reverse passes run side by side: each operator launch takes
+      // its share of two waves of resident CTAs (one CTA per item when alone;
+      // 8 frames: C5 backward 60.4 -> 55.9 ms)
+      view.op_grid = nframes > 1 ? (2 * pl->op_minb * pl->nsm + nframes - 1) / nframes : 0;
       GradWS w;
       grad_ws_carve(pl, wbase + wsb * f, w);
       CK(cudaStreamBeginCapture(sf, cudaStreamCaptureModeThreadLocal));
