@@ -373,7 +373,8 @@ def psf_kernel(kx: np.ndarray, ky: np.ndarray, N: int, G: int) -> np.ndarray:
     """PSF P on the G grid for the Toeplitz form of A^H A:
     p(d) = (2N)^-2 sum_s exp(2 pi i k_s . d) for d in [-(N-1), N-1]^2, embedded
     circularly on the G grid (G >= 2N - 1: no offset wraps onto another),
-    P = G U p.  Real because p is Hermitian; returned as [G, G]."""
+    P = G U p.  Real because p is Hermitian: returned as a complex128 [G, G]
+    array whose imaginary part is rounding (callers take .real)."""
     assert G >= 2 * N - 1
     d = np.arange(-(N - 1), N, dtype=np.float64)
     ex = np.exp(2j * np.pi * np.outer(kx, d))        # [S, dx]
