@@ -68,15 +68,19 @@ def candidates(N, J, M=7, K=10, gamma=(1.0, 2.0)):
     return out
 
 
-def measure(N, J, cand, M=7, K=10, frames=6, warmup=2, spokes=13, seed=5):
-    """Median ms per frame of a stream of frames with the candidate's plan.
-    The work of a frame does not depend on the data (fixed Newton and CG
-    counts), so the gridded data are seeded random values and the PSF comes
-    from a radial trajectory of `spokes` spokes on the candidate's grid."""
+def measure(N, J, cand, M=7, K=10, frames=6, warmup=2, spokes=13, seed=5, batch=1):
+    """Median ms per frame of a stream of frames with the candidate's plan
+    (batch > 1: `batch` frames in flight per nlinv_batch call, the call's time
+    divided by `batch`).  The work of a frame does not depend on the data
+    (fixed Newton and CG counts), so the gridded data are seeded random values
+    and the PSF comes from a radial trajectory of `spokes` spokes on the
+    candidate's grid."""
     from synth import radial_trajectory
     dev = torch.device("cuda")
     G = cand["G"]
-    plan = L.nlinv_plan(_params(N, J, M, K, G, cand["exec_mode"], cand["cluster_cs"]))
+    prm = _params(N, J, M, K, G, cand["exec_mode"], cand["cluster_cs"])
+    prm.max_batch = max(1, batch)
+    plan = L.nlinv_plan(prm)
     kx, ky = radial_trajectory(N, spokes, 5, 0)
     L.nlinv_psf(plan, 0, torch.tensor(np.stack([kx, ky], 1), dtype=torch.float64, device=dev))
     gen = torch.Generator(device=dev)
@@ -85,11 +89,19 @@ def measure(N, J, cand, M=7, K=10, frames=6, warmup=2, spokes=13, seed=5):
     x = torch.empty(plan.nx, dtype=torch.complex64, device=dev)
     st = torch.cuda.current_stream()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(frames)]
+    if batch > 1:
+        xs = torch.empty((batch, plan.nx), dtype=torch.complex64, device=dev)
+        L.nlinv_frame(plan, Y, 0, None, x)
+        descs = [dict(plan=plan, Y=Y, turn=0, x_prev=x, x_out=xs[f]) for f in range(batch)]
+        run = lambda: L.nlinv_batch(descs)
+    else:
+        run = lambda: L.nlinv_frame(plan, Y, 0, x, x)
+        L.nlinv_frame(plan, Y, 0, None, x)
     for n in range(warmup):
-        L.nlinv_frame(plan, Y, 0, None if n == 0 else x, x)
+        run()
     for n in range(frames):
         ev[n][0].record(st)
-        L.nlinv_frame(plan, Y, 0, x, x)
+        run()
         ev[n][1].record(st)
     torch.cuda.synchronize()
     rc = L.nlinv_sync(plan)
@@ -97,7 +109,7 @@ def measure(N, J, cand, M=7, K=10, frames=6, warmup=2, spokes=13, seed=5):
     plan.close()
     if rc != 0:
         raise L.NlinvError(rc, "tune.measure")
-    return statistics.median(a.elapsed_time(b) for a, b in ev), path
+    return statistics.median(a.elapsed_time(b) for a, b in ev) / max(1, batch), path
 
 
 def _load(db):
@@ -207,13 +219,13 @@ def compile_variants(N, G=None, tws=(8, 12, 16), knobs=None):
     return out
 
 
-def _time_in_child(lib, N, J, G, M, K, frames):
+def _time_in_child(lib, N, J, G, M, K, frames, batch=1):
     import subprocess
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     code = ("import json, sys; sys.path.insert(0, %r); from paper_1701_08361_gb300 import tune as T; "
-            "ms, path = T.measure(%d, %d, dict(G=%d, exec_mode=0, cluster_cs=0), %d, %d, frames=%d); "
-            "print(json.dumps(dict(ms=ms, path=list(path))))" % (root, N, J, G, M, K, frames))
+            "ms, path = T.measure(%d, %d, dict(G=%d, exec_mode=0, cluster_cs=0), %d, %d, frames=%d, batch=%d); "
+            "print(json.dumps(dict(ms=ms, path=list(path))))" % (root, N, J, G, M, K, frames, batch))
     env = dict(os.environ, NLINV_LIB=lib)
     r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
     if r.returncode != 0:
@@ -221,7 +233,8 @@ def _time_in_child(lib, N, J, G, M, K, frames):
     return json.loads(r.stdout.strip().splitlines()[-1])["ms"], None
 
 
-def compile_sweep(N, J, M=7, K=10, G=None, frames=6, db=DB_PATH, write=True, workdir=None, variants=None):
+def compile_sweep(N, J, M=7, K=10, G=None, frames=6, db=DB_PATH, write=True, workdir=None, variants=None,
+                  batch=1):
     """Build and time every compile variant (compile_variants) for an N x N
     image with J channels; returns (and records under the GPU's name) the
     times and the fastest variant."""
@@ -243,16 +256,16 @@ def compile_sweep(N, J, M=7, K=10, G=None, frames=6, db=DB_PATH, write=True, wor
         libs = list(ex.map(build_one, vs))
     rows = []
     for v, lib in zip(vs, libs):
-        ms, err = _time_in_child(lib, N, J, G, M, K, frames)
+        ms, err = _time_in_child(lib, N, J, G, M, K, frames, batch)
         rows.append(dict(name=v["name"], tw=v["grid"][3], knobs=v["knobs"],
                          ms_per_frame=None if ms is None else round(ms, 4), error=err))
     ok = [r for r in rows if r["ms_per_frame"] is not None]
     best = min(ok, key=lambda r: r["ms_per_frame"]) if ok else None
-    rec = dict(pick=best, variants=rows, frames_timed=frames, G=G,
+    rec = dict(pick=best, variants=rows, frames_timed=frames, G=G, batch=batch,
                when=time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()))
     if write and db:
         data = _load(db)
-        data.setdefault(gpu_name(), {})[_key(N, J, M, K) + f"_G{G}_compile"] = rec
+        data.setdefault(gpu_name(), {})[_key(N, J, M, K) + f"_G{G}_compile" + (f"_b{batch}" if batch > 1 else "")] = rec
         with open(db, "w") as f:
             json.dump(data, f, indent=1, sort_keys=True)
     return rec
@@ -267,11 +280,12 @@ def main():
     ap.add_argument("--gamma", type=float, nargs=2, default=(1.0, 2.0))
     ap.add_argument("--frames", type=int, default=6)
     ap.add_argument("--db", default=DB_PATH)
+    ap.add_argument("--batch", type=int, default=1, help="frames in flight per call (compile sweep)")
     ap.add_argument("--compile", action="store_true",
                     help="sweep the compile-time knobs of the G = 2N grid instead of grids and paths")
     a = ap.parse_args()
     if a.compile:
-        rec = compile_sweep(a.N, a.J, a.M, a.K, frames=a.frames, db=a.db)
+        rec = compile_sweep(a.N, a.J, a.M, a.K, frames=a.frames, db=a.db, batch=a.batch)
     else:
         rec = tune(a.N, a.J, a.M, a.K, tuple(a.gamma), a.db, frames=a.frames)
     print(json.dumps(rec))
